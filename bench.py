@@ -1,0 +1,292 @@
+"""Benchmark: seconds per circuit for the 34-qubit depth-30 lattice circuit on one GB300.
+
+One step = one full simulation of the 6x6-minus-two-corners lattice circuit (478 gates
+including the layer-0 H layer) from |0...0> on a 128 GiB complex64 state: plan upload,
+every tile pass, nothing skipped.  The state (137 GB) is far larger than L2 (129 MB), so
+no flush is needed between steps.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+For N > 1 (torchrun, one rank per GPU) every rank simulates its own replica of the
+circuit (the simulation does not shard) and value = N circuits / max time.
+--impl reference times the CPU oracle (the only reference this method has) on a bounded
+sample of the same workload on the host cores.
+"""
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = '34q depth-30 s/circuit & %HBM roofline; fused-TC vs plain at rel-L2≤1e-5'
+UNIT = 's/circuit'
+
+
+def _peaks():
+    try:
+        with open(os.path.join(ROOT, 'MEASURED_PEAKS.json')) as f:
+            p = json.load(f)
+        return float(p['hbm_gbs']), 'measured'
+    except Exception:
+        return 6800.0, 'fallback'
+
+
+class Clocks:
+    """nvidia-smi sampling during the timed region."""
+    FIELDS = ('index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,'
+              'clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,'
+              'clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap')
+
+    def __init__(self, gpu_index):
+        self.gpu = gpu_index
+        self.proc = None
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ['nvidia-smi', '-i', str(self.gpu), '--query-gpu=' + self.FIELDS,
+                 '--format=csv,noheader,nounits', '-lms', '200'],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except Exception:
+            self.proc = None
+        return self
+
+    def __exit__(self, *a):
+        self.lines = []
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                out, _ = self.proc.communicate(timeout=5)
+            except Exception:
+                self.proc.kill()
+                out, _ = self.proc.communicate()
+            self.lines = [l for l in out.splitlines() if l.strip()]
+
+    def summary(self):
+        sm, mx, reasons = [], [], set()
+        names = ['hw_slowdown', 'hw_thermal_slowdown', 'sw_thermal_slowdown', 'sw_power_cap']
+        for l in getattr(self, 'lines', []):
+            f = [x.strip() for x in l.split(',')]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                mx.append(float(f[2]))
+            except ValueError:
+                continue
+            for name, v in zip(names, f[5:9]):
+                if v.lower() == 'active':
+                    reasons.add(name)
+        if not sm:
+            return {'sm_mhz': None, 'sm_max_mhz': None, 'reasons': [], 'samples': 0}
+        return {'sm_mhz': statistics.median(sm), 'sm_max_mhz': max(mx), 'reasons': sorted(reasons),
+                'samples': len(sm)}
+
+
+def _oracle_sample(steps_hint=1):
+    """Time the CPU oracle on a bounded sample: the 26-qubit lattice circuit of the same
+    construction (6x5 minus its four corners) at depth 30, scaled to the 34-qubit circuit
+    by gate count and state size (the oracle's cost is one full sweep per gate)."""
+    from oracle import circuit as oc
+    from oracle import csim
+    from paper_1804_04797_gb300 import inputs
+    csim.build()
+    lat = inputs.lattice_for(6, 5, 30, seed=0, removed=[(0, 0), (0, 4), (5, 0), (5, 4)])
+    n, gates = oc.generate(lat.rows, lat.cols, lat.removed_mask, lat.depth, lat.seed)
+    full = inputs.C34
+    n_full, gates_full = oc.generate(full.rows, full.cols, full.removed_mask, full.depth, full.seed)
+    t0 = time.perf_counter()
+    csim.run(n, gates)
+    dt = time.perf_counter() - t0
+    scale = (len(gates_full) * 2.0 ** n_full) / (len(gates) * 2.0 ** n)
+    return dt * scale, dt, csim.threads(), ('oracle (complex128 C, OpenMP) on the 26-qubit depth-30 '
+                                            'circuit (%d gates, %.1f s), scaled by gates x 2^n to 478 gates '
+                                            'x 2^34' % (len(gates), dt))
+
+
+def run_reference(args, rank, world):
+    if rank != 0:
+        return 0
+    times = []
+    for _ in range(args.warmup):
+        _oracle_sample()
+    desc, cores = '', 0
+    for _ in range(args.steps):
+        v, _dt, cores, desc = _oracle_sample()
+        times.append(v)
+    value = statistics.median(times)
+    line = {
+        'impl': 'reference', 'metric': METRIC, 'value': value, 'unit': UNIT, 'n_gpus': world,
+        'steps': args.steps, 'warmup': args.warmup, 'ms_per_step': value * 1e3, 'higher_is_better': False,
+        'scaling': 'weak', 'vs_baseline': None, 'dtype': 'c128', 'data': 'synthetic',
+        'config': {'workload': '34-qubit 6x6-minus-corners lattice circuit, depth 30, seed 0 (478 gates)',
+                   'sample': 'bounded CPU sample, scaled'},
+        'cpu_baseline': {'value': value, 'unit': UNIT, 'cores': cores, 'kind': 'oracle', 'sample': desc},
+        'e2e': {'value': value, 'unit': UNIT, 'h2d_bytes_per_step': 0, 'd2h_bytes_per_step': 0},
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument('--gpus', type=int, default=1)
+    ap.add_argument('--steps', type=int, default=5)
+    ap.add_argument('--warmup', type=int, default=3)
+    ap.add_argument('--impl', default='ours', choices=['ours', 'reference'])
+    ap.add_argument('--qubits', type=int, default=34, help='34 (headline) or a smaller lattice for tests')
+    ap.add_argument('--no-fused', action='store_true')
+    ap.add_argument('--no-cpu', action='store_true')
+    args = ap.parse_args()
+
+    rank = int(os.environ.get('RANK', '0'))
+    world = int(os.environ.get('WORLD_SIZE', '1'))
+    local = int(os.environ.get('LOCAL_RANK', '0'))
+    if args.impl == 'reference':
+        return run_reference(args, rank, world)
+
+    import numpy as np
+    import torch
+    from paper_1804_04797_gb300 import inputs, sv
+
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group('nccl', device_id=torch.device('cuda', local))
+
+    lat = {34: inputs.C34, 30: inputs.C30, 16: inputs.C16}.get(args.qubits, inputs.C34)
+    n = lat.n_qubits
+    gates = sv.sv_generate_circuit(lat)
+    stream = torch.cuda.Stream()
+    hbm_peak, peak_kind = _peaks()
+
+    def barrier():
+        if dist is not None:
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    def timed(h, steps, warmup, fn):
+        for _ in range(warmup):
+            fn(h)
+        barrier()
+        sv.sv_set_profiling(h, True)
+        ev0 = torch.cuda.Event(enable_timing=True)
+        ev1 = torch.cuda.Event(enable_timing=True)
+        with Clocks(local) as ck:
+            ev0.record(stream)
+            t0 = time.perf_counter()
+            for _ in range(steps):
+                fn(h)
+            ev1.record(stream)
+            barrier()
+            wall = time.perf_counter() - t0
+        ms = ev0.elapsed_time(ev1)
+        prof = sv.sv_get_profile(h)
+        sv.sv_set_profiling(h, False)
+        if dist is not None:
+            t = torch.tensor([ms, wall], device='cuda')
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            ms, wall = float(t[0]), float(t[1])
+        return ms, wall, prof, ck.summary()
+
+    def step_device(h):
+        sv.sv_reset(h)
+        sv.sv_apply_circuit(h, gates)
+
+    results = {}
+    bits = np.array(inputs.bitstrings(n, 64, seed=2), dtype=np.uint64)
+    modes = [('plain', sv.SV_PREC_PLAIN)]
+    if not args.no_fused:
+        modes.append(('tf32x3', sv.SV_PREC_TF32X3))
+    h = sv.sv_create(n, sv.options(stream=stream.cuda_stream))
+    amps_ref = None
+    try:
+        for name, prec in modes:
+            try:
+                sv.sv_set_options(h, sv.options(precision=prec, stream=stream.cuda_stream))
+                ms, wall, prof, clocks = timed(h, args.steps, args.warmup, step_device)
+            except sv.SvError as e:
+                results[name] = {'unavailable': str(e)}
+                continue
+            norm2, sp2 = sv.sv_norm(h)
+            amps = sv.sv_get_amplitudes(h, bits)
+            if amps_ref is None:
+                amps_ref = amps
+            agree = float(np.linalg.norm(amps - amps_ref) / np.linalg.norm(amps_ref))
+            per_launch_ms = prof.ms / max(prof.launches, 1)
+            bytes_per_launch = prof.hbm_bytes / max(prof.launches, 1)
+            results[name] = {
+                's_per_circuit': ms / 1e3 / args.steps, 'ms_total': ms, 'wall_s': wall, 'launches': prof.launches,
+                'kernel_ms': prof.ms, 'kernel_bytes': prof.hbm_bytes, 'per_launch_ms': per_launch_ms,
+                'bytes_per_launch': bytes_per_launch, 'achieved_gbs': bytes_per_launch / (per_launch_ms * 1e-3) / 1e9,
+                'norm_err': abs(norm2 - 1.0), 'n_sum_p2': (2.0 ** n) * sp2, 'rel_l2_vs_plain_64amps': agree,
+                'clocks': clocks, 'launches_per_step': prof.launches / args.steps,
+            }
+
+        # end to end through the public API with host buffers: gate list in, amplitudes
+        # and norm out, every step
+        def step_e2e(hh):
+            sv.sv_reset(hh)
+            sv.sv_apply_circuit(hh, sv.sv_generate_circuit(lat))
+            sv.sv_get_amplitudes(hh, bits)
+            sv.sv_norm(hh)
+        sv.sv_set_options(h, sv.options(stream=stream.cuda_stream))
+        e_ms, e_wall, e_prof, _ = timed(h, max(1, min(args.steps, 3)), 1, step_e2e)
+        e2e_steps = max(1, min(args.steps, 3))
+        e2e = {'value': e_wall / e2e_steps, 'unit': UNIT,
+               'h2d_bytes_per_step': (e_prof.h2d_bytes + gates.nbytes * e2e_steps) / e2e_steps,
+               'd2h_bytes_per_step': e_prof.d2h_bytes / e2e_steps}
+    finally:
+        sv.sv_destroy(h)
+
+    if rank != 0:
+        if dist is not None:
+            dist.destroy_process_group()
+        return 0
+
+    plain = results.get('plain', {})
+    fused = results.get('tf32x3', {})
+    best_name = 'plain'
+    if 's_per_circuit' in fused and fused['s_per_circuit'] < plain.get('s_per_circuit', 1e30) \
+            and fused.get('rel_l2_vs_plain_64amps', 1.0) <= 1e-5:
+        best_name = 'tf32x3'
+    best = results[best_name]
+    value = best['s_per_circuit'] / world
+    cpu = None
+    if not args.no_cpu:
+        v, dt, cores, desc = _oracle_sample()
+        cpu = {'value': v, 'unit': UNIT, 'cores': cores, 'kind': 'oracle', 'sample': desc}
+    achieved = best['achieved_gbs']
+    line = {
+        'metric': METRIC, 'value': value, 'unit': UNIT, 'n_gpus': world, 'steps': args.steps,
+        'warmup': args.warmup, 'ms_per_step': best['s_per_circuit'] * 1e3, 'higher_is_better': False,
+        'scaling': 'weak', 'vs_baseline': None, 'dtype': 'c64' if best_name == 'plain' else 'c64/tf32x3',
+        'data': 'synthetic',
+        'config': {'workload': '34-qubit 6x6-minus-corners lattice circuit, depth 30, seed 0 (478 gates)'
+                   if n == 34 else '%d-qubit lattice circuit' % n,
+                   'state_bytes': 8 * 2 ** n, 'l2': 'state 137 GB >> L2 129 MB, no flush needed',
+                   'path': best_name, 'replicas': world},
+        'roofline': {'bound': 'hbm', 'kernel': 'tile_pass_kernel' if best_name == 'plain' else 'fused_pass_kernel',
+                     'achieved': achieved, 'peak': hbm_peak, 'unit': 'GB/s', 'frac': achieved / hbm_peak,
+                     'traffic': None, 'peak_kind': peak_kind,
+                     'bytes_per_launch': best['bytes_per_launch'], 'per_launch_ms': best['per_launch_ms']},
+        'clocks': best['clocks'],
+        'e2e': e2e,
+        'gpu_launches': int(round(best['launches_per_step'] * args.steps)),
+        'cpu_baseline': cpu,
+        'paths': results,
+    }
+    print(json.dumps(line), flush=True)
+    if dist is not None:
+        dist.destroy_process_group()
+    return 0
+
+
+if __name__ == '__main__':
+    sys.exit(main())

@@ -1,0 +1,219 @@
+/*
+ * sv.h -- C interface of the GB300 (sm_103a) state-vector simulator of random lattice
+ * ("supremacy") circuits, after Li, Wu, Ying, Sun, Yang, "Quantum Supremacy Circuit
+ * Simulation on Sunway TaihuLight" (arXiv:1804.04797).
+ *
+ * Conventions (all calls)
+ *   - Amplitude order: |psi> = (alpha_0 .. alpha_{2^n-1}) and qubit k is bit k of the
+ *     index (§2, the pair-update equation).  The state lives on the device as 2^n
+ *     interleaved complex64 values {float re, float im}.
+ *   - Bitstrings are uint64_t, bit q = outcome of qubit q.
+ *   - Every call returns sv_status; on failure sv_last_error() (thread-local) gives a
+ *     one-line message.  No call keeps a host pointer after it returns.  The library
+ *     owns the device memory it allocates; the caller owns every host array.
+ *   - Calls are ordered on the handle's CUDA stream.  Calls that return host data
+ *     (amplitudes, norms, branch amplitudes, batch statistics) synchronise it.
+ *   - There is no CPU fallback: without a usable CUDA device, calls that touch the
+ *     device return SV_ERR_CUDA.  sv_generate_circuit and sv_plan_* are host-only.
+ */
+#ifndef PAPER_1804_04797_GB300_SV_H_
+#define PAPER_1804_04797_GB300_SV_H_
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  SV_OK = 0,
+  SV_ERR_ARG = 1,     /* invalid argument: size, qubit index, gate kind, pointer      */
+  SV_ERR_OOM = 2,     /* a device allocation failed; the state is left unchanged      */
+  SV_ERR_CUDA = 3,    /* a CUDA call failed (message holds cudaGetErrorString)        */
+  SV_ERR_TIMEOUT = 4, /* a bounded in-kernel wait gave up (no hang; device flag read)  */
+  SV_ERR_STATE = 5    /* the handle is unusable after an earlier failed apply          */
+} sv_status;
+
+/* Gate kinds.  H, T, SX = X^{1/2}, SY = Y^{1/2} and CZ are the gate set of §2 (the
+ * paragraph after Fig. 2).  Matrices (the paper prints none; the principal roots):
+ *   H  = [[1,1],[1,-1]]/sqrt2          T  = diag(1, e^{i pi/4})
+ *   SX = [[1+i,1-i],[1-i,1+i]]/2       SY = [[1+i,-1-i],[1+i,1+i]]/2
+ *   CZ = diag(1,1,1,-1) on (q0, q1)
+ * P0 = |0><0|, P1 = |1><1| (the projectors of §2.1) and Z = diag(1,-1) are the product
+ * terms of the decomposition CZ = P0 (x) I + P1 (x) Z (§2, Fig. 2).  TDG, SXDG, SYDG are
+ * the adjoints of T, SX, SY (for inverse circuits). */
+typedef enum {
+  SV_H = 0, SV_T = 1, SV_SX = 2, SV_SY = 3, SV_CZ = 4,
+  SV_P0 = 5, SV_P1 = 6, SV_Z = 7, SV_TDG = 8, SV_SXDG = 9, SV_SYDG = 10
+} sv_kind;
+
+/* One gate; q1 is read for CZ only.  layer is informational (0 = the H layer). */
+typedef struct {
+  uint8_t kind, q0, q1, pad;
+  uint32_t layer;
+} sv_gate;
+
+/* Arithmetic of the in-tile update. */
+enum {
+  SV_PREC_PLAIN = 0,  /* fp32 CUDA-core arithmetic, one gate at a time               */
+  SV_PREC_TF32X3 = 1, /* fused k-qubit unitaries on tcgen05 tensor cores, 3-pass     */
+                      /* split-TF32 products (hi*hi + hi*lo + lo*hi), fp32 accumulate */
+  SV_PREC_PERGATE = 3 /* one full sweep of the state per gate (no tiling; baseline)  */
+};
+
+/* Options.  Zero-initialised fields take the defaults in brackets. */
+typedef struct {
+  int fuse_k;     /* qubits per fused block / register group, 2..5        [5]           */
+  int precision;  /* SV_PREC_*                                            [PLAIN]       */
+  int autotune;   /* reserved: 1 = pick tile_bits by timing (sv_apply_batch)  [0]      */
+  void *stream;   /* cudaStream_t used by the handle                      [legacy 0]    */
+  int tile_bits;  /* qubits per gathered tile, fuse_k+5..13               [13]          */
+  int low_bits;   /* contiguous low qubits in every tile (coalescing)     [4]           */
+} sv_options;
+
+/* An R x C lattice circuit: bit r*cols+c of removed_mask drops site (r,c); kept sites
+ * are numbered row-major.  depth counts layers after the layer-0 H gates (§1 footnote). */
+typedef struct {
+  int rows, cols;
+  uint64_t removed_mask;
+  int depth;
+  uint64_t seed;
+} sv_lattice;
+
+/* A cut of the qubits into halves A (bits set) and B. */
+typedef struct {
+  uint64_t half_a_mask;
+} sv_cut;
+
+typedef struct sv_state sv_state;
+
+/* Thread-local text of the last error ("" if none).  Valid until the next call. */
+const char *sv_last_error(void);
+
+/* --- state lifetime -------------------------------------------------------------- */
+
+/* Allocate a 2^n complex64 state in |0...0> (§2 initial state).  1 <= n <= 34 (34
+ * qubits = 128 GiB).  opts may be NULL.  Returns SV_ERR_OOM if cudaMalloc fails. */
+sv_status sv_create(int n_qubits, const sv_options *opts, sv_state **out);
+
+/* Wrap a caller-owned device buffer of 2^n complex64 (e.g. a torch tensor).  The
+ * buffer must stay alive until sv_destroy, which does not free it.  Its content is
+ * taken as the current state.  stream may be NULL (legacy default stream). */
+sv_status sv_create_from_ptr(int n_qubits, void *dev_ptr, void *stream, sv_state **out);
+
+/* Release the handle and the device memory it owns.  NULL is accepted. */
+sv_status sv_destroy(sv_state *s);
+
+/* Replace the options (precision, fusion width, tile shape, stream). */
+sv_status sv_set_options(sv_state *s, const sv_options *opts);
+
+/* Copy the 2^n complex64 amplitudes to dst (host or device memory, 8*2^n bytes). */
+sv_status sv_copy_state(sv_state *s, void *dst);
+
+/* Overwrite the state with 2^n complex64 values from src (host or device memory). */
+sv_status sv_load_state(sv_state *s, const void *src);
+
+/* Return the state to |0...0> without touching the device: the next apply generates
+ * the initial state in its first pass instead of reading the buffer. */
+sv_status sv_reset(sv_state *s);
+
+/* Device pointer of the amplitudes (owned by the handle or the caller). */
+sv_status sv_device_ptr(sv_state *s, void **ptr);
+
+/* --- circuits ---------------------------------------------------------------------- */
+
+/* Seeded lattice circuit (§2: gates H, T, X^{1/2}, Y^{1/2}, CZ on lattice neighbours,
+ * fixed CZ positions per layer; layer-0 H on every qubit).  Rules: 8 CZ patterns used
+ * cyclically (horizontal bond (r,c)-(r,c+1) in class (c+2(r mod 2)) mod 4, vertical bond
+ * (r,c)-(r+1,c) in class (r+2(c mod 2)) mod 4, layer l uses [H0,V0,H1,V1,H2,V2,H3,V3][(l-1)
+ * mod 8]); in layer l a qubit that was in a CZ of layer l-1 and is in none of layer l
+ * gets one of {T, SX, SY} different from its previous one, drawn by SplitMix64(seed)
+ * (layers, then qubits ascending; candidates [T,SX,SY] minus the previous one; pick
+ * draw % count).  Within a layer: one-qubit gates by qubit, then CZs by (q0<q1).
+ * Writes at most cap gates to out (out may be NULL to query *n_out).  Host only.
+ * SV_ERR_ARG if the lattice has more than 64 sites, or cap is too small. */
+sv_status sv_generate_circuit(const sv_lattice *lat, sv_gate *out, size_t cap, size_t *n_out);
+
+/* Apply gates in list order (§2 pair update for one-qubit gates, diagonal CZ).  The
+ * list is planned into passes over 2^tile_bits-amplitude gathered tiles and k-qubit
+ * groups (the bunching of gates on "local qubits" of §2.3, generalised to any qubit
+ * set).  If the state is still the initial |0..0> and the list starts with H on every
+ * qubit, that layer becomes the uniform amplitude 2^{-n/2} written by the first pass.
+ * SV_ERR_ARG for a qubit >= n, CZ with q0 == q1, or an unknown kind (state untouched).
+ * A CUDA failure marks the handle SV_ERR_STATE. */
+sv_status sv_apply_circuit(sv_state *s, const sv_gate *gates, size_t n_gates);
+
+/* Apply the inverse of the gate list (reverse order, adjoint of each gate). */
+sv_status sv_apply_circuit_inverse(sv_state *s, const sv_gate *gates, size_t n_gates);
+
+/* alpha_x for m bitstrings, written as 2m doubles (re, im).  Bits >= n must be 0. */
+sv_status sv_get_amplitudes(sv_state *s, const uint64_t *bits, size_t m, double *out_re_im);
+
+/* fp64 sums over the state: norm2 = sum |alpha|^2, sum_p2 = sum |alpha|^4 (the
+ * Porter-Thomas statistic of §3: N * sum_p2 -> 2).  Either pointer may be NULL.
+ * Deterministic (fixed two-level tree). */
+sv_status sv_norm(sv_state *s, double *norm2, double *sum_p2);
+
+/* Probabilities |alpha_x|^2 for m indices, in fp64. */
+sv_status sv_get_probabilities(sv_state *s, const uint64_t *bits, size_t m, double *out);
+
+/* --- few-amplitude task -------------------------------------------------------------- */
+
+/* alpha_x for m bitstrings of the lattice circuit by the cut decomposition (§2, Fig. 2
+ * and Eq. 1): every CZ with one qubit in each half is replaced by its two product terms
+ * (P_l on the half-A qubit, Z^l on the half-B qubit); all 2^t branches of both halves run
+ * as one batched state (branch bits are extra index bits), and
+ * alpha_x = sum_l A_l[x_A] * B_l[x_B] is summed in fp64.  Halves of at most 30 qubits,
+ * half bits + t <= 34.  out_re_im: 2m doubles.  opts may be NULL. */
+sv_status sv_branch_amplitudes(const sv_lattice *lat, const sv_cut *cut, const uint64_t *bits,
+                               size_t m, const sv_options *opts, double *out_re_im);
+
+/* --- batch ------------------------------------------------------------------------------ */
+
+/* Simulate count independent lattice circuits (each with its own state, 1..28 qubits)
+ * in one persistent launch over a work queue of (circuit, pass, tile) items, captured
+ * once in a CUDA graph and replayed on later calls with the same lattices.  Items wait
+ * for the previous pass of their circuit with a bounded spin; if it gives up the call
+ * returns SV_ERR_TIMEOUT.  stats_out (may be NULL) receives 3 doubles per circuit:
+ * norm2, sum_p2, Re/Im are not reported -- [norm2, sum_p2, n_qubits]. */
+sv_status sv_apply_batch(const sv_lattice *circs, size_t count, const sv_options *opts,
+                         double *stats_out);
+
+/* --- planning and measurement (host-only helpers) --------------------------------------- */
+
+typedef struct {
+  int passes;         /* HBM sweeps of the state (including the write-only init, if any) */
+  int stages;         /* k-qubit groups over all passes                                   */
+  int ops;            /* gate operations after planning                                   */
+  int init_uniform;   /* 1 if the layer-0 H gates became the uniform first pass           */
+  double hbm_bytes;   /* algorithmic bytes of the passes: 16 * 2^n per read-write pass,   */
+                      /* 8 * 2^n for the write-only first pass                             */
+} sv_plan_summary;
+
+/* Plan a gate list for an n-qubit state without touching the device.  order_out (may
+ * be NULL, else n_gates entries) receives the gate indices in execution order;
+ * pass_out (may be NULL) the pass of each executed gate; tile_out (may be NULL, else
+ * 64 * passes entries) the qubits of each pass's tile (-1 padded). */
+sv_status sv_plan(int n_qubits, const sv_gate *gates, size_t n_gates, const sv_options *opts,
+                  int fresh_state, sv_plan_summary *summary, int32_t *order_out,
+                  int32_t *pass_out, int32_t *tile_out, size_t tile_cap);
+
+/* Per-kernel timing collected with CUDA events on the handle's stream while enabled. */
+typedef struct {
+  int launches;       /* tile-pass (or per-gate) kernel launches                 */
+  double ms;          /* their summed device time                                */
+  double hbm_bytes;   /* their summed algorithmic bytes                          */
+  double h2d_bytes;   /* host-to-device bytes copied by the library (plans, indices) */
+  double d2h_bytes;   /* device-to-host bytes copied by the library (results)     */
+  int other_launches; /* other kernels (reductions, gathers, init)               */
+} sv_profile;
+
+sv_status sv_set_profiling(sv_state *s, int on);
+sv_status sv_get_profile(sv_state *s, sv_profile *out);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* PAPER_1804_04797_GB300_SV_H_ */

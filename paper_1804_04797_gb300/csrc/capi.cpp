@@ -1,0 +1,525 @@
+// C ABI: state handles, validation, planning, launches, readback, profiling.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "../../include/sv.h"
+#include "capi_util.h"
+#include "kernels.h"
+#include "plan.h"
+#include "state.h"
+
+std::string &svc::last_error() {
+  thread_local std::string s;
+  return s;
+}
+
+extern "C" const char *sv_last_error(void) { return svc::last_error().c_str(); }
+
+namespace svc {
+
+sv_status cuda_fail(cudaError_t e, const char *what) {
+  return failf(SV_ERR_CUDA, "%s: %s", (std::string(what) + " / " + cudaGetErrorString(e)).c_str(), 0);
+}
+
+sv_status ensure_device_buffer(void **buf, size_t *cap, size_t need) {
+  if (*cap >= need) return SV_OK;
+  if (*buf) cudaFree(*buf);
+  *buf = nullptr;
+  *cap = 0;
+  size_t want = std::max<size_t>(need, 4096);
+  cudaError_t e = cudaMalloc(buf, want);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    *buf = nullptr;
+    return fail(SV_ERR_OOM, "device scratch allocation failed");
+  }
+  *cap = want;
+  return SV_OK;
+}
+
+svp::Options plan_options(const sv_options &o) {
+  svp::Options p;
+  p.m = o.tile_bits > 0 ? o.tile_bits : 13;
+  p.c = o.low_bits > 0 ? o.low_bits : 4;
+  p.r = o.fuse_k > 0 ? o.fuse_k : 5;
+  p.fused = o.precision == SV_PREC_TF32X3;
+  return p;
+}
+
+sv_status check_options(const sv_options &o) {
+  if (o.precision != SV_PREC_PLAIN && o.precision != SV_PREC_TF32X3 && o.precision != SV_PREC_PERGATE)
+    return fail(SV_ERR_ARG, "options: unknown precision mode");
+  if (o.fuse_k < 0 || o.fuse_k > svp::kMaxReg) return fail(SV_ERR_ARG, "options: fuse_k must be 0 or 1..5");
+  if (o.tile_bits != 0 && (o.tile_bits < 6 || o.tile_bits > svp::kMaxTileBits))
+    return fail(SV_ERR_ARG, "options: tile_bits must be 0 or 6..13");
+  if (o.low_bits < 0 || o.low_bits > 13) return fail(SV_ERR_ARG, "options: low_bits must be 0..13");
+  const int m = o.tile_bits > 0 ? o.tile_bits : 13;
+  const int c = o.low_bits > 0 ? o.low_bits : 4;
+  if (c > m || m - c > 10) return fail(SV_ERR_ARG, "options: need low_bits <= tile_bits <= low_bits + 10");
+  return SV_OK;
+}
+
+sv_status convert_gates(int n, const sv_gate *g, size_t count, bool inverse, std::vector<svp::Gate> *out) {
+  out->clear();
+  out->reserve(count);
+  if (count && !g) return fail(SV_ERR_ARG, "gate list is NULL");
+  for (size_t s = 0; s < count; ++s) {
+    const sv_gate &x = g[inverse ? count - 1 - s : s];
+    if (x.kind > SV_SYDG) return failf(SV_ERR_ARG, "gate %s%lld: unknown kind", "#", (long long)s);
+    if (x.q0 >= n) return failf(SV_ERR_ARG, "gate %s%lld: qubit out of range", "#", (long long)s);
+    uint8_t k = x.kind;
+    if (k == SV_CZ && (x.q1 >= n || x.q1 == x.q0))
+      return failf(SV_ERR_ARG, "gate %s%lld: CZ needs two distinct qubits < n", "#", (long long)s);
+    if (inverse) {
+      if (k == SV_T) k = SV_TDG;
+      else if (k == SV_TDG) k = SV_T;
+      else if (k == SV_SX) k = SV_SXDG;
+      else if (k == SV_SXDG) k = SV_SX;
+      else if (k == SV_SY) k = SV_SYDG;
+      else if (k == SV_SYDG) k = SV_SY;
+    }
+    out->push_back(svp::Gate{k, x.q0, (uint8_t)(k == SV_CZ ? x.q1 : 0)});
+  }
+  return SV_OK;
+}
+
+}  // namespace svc
+
+using namespace svc;
+
+// ---------------------------------------------------------------------------------------
+
+namespace {
+
+sv_status set_device(sv_state *s) {
+  cudaError_t e = cudaSetDevice(s->device);
+  if (e != cudaSuccess) return cuda_fail(e, "cudaSetDevice");
+  return SV_OK;
+}
+
+sv_status materialize(sv_state *s) {
+  if (!s->fresh) return SV_OK;
+  cudaError_t e = svk::launch_init(s->psi, s->n, false, 1.0f, s->stream);
+  if (e != cudaSuccess) { s->broken = true; return cuda_fail(e, "init kernel"); }
+  s->fresh = false;
+  return SV_OK;
+}
+
+void prof_begin(sv_state *s) {
+  if (!s->prof) return;
+  if (s->ev_used + 2 > s->events.size()) {
+    cudaEvent_t a, b;
+    cudaEventCreate(&a);
+    cudaEventCreate(&b);
+    s->events.push_back(a);
+    s->events.push_back(b);
+  }
+  cudaEventRecord(s->events[s->ev_used], s->stream);
+}
+
+void prof_end(sv_state *s, double bytes) {
+  if (!s->prof) return;
+  cudaEventRecord(s->events[s->ev_used + 1], s->stream);
+  s->ev_bytes.push_back(bytes);
+  s->ev_used += 2;
+}
+
+// one full sweep per gate (precision SV_PREC_PERGATE and tiny states)
+sv_status apply_pergate(sv_state *s, const std::vector<svp::Gate> &g) {
+  size_t start = 0;
+  const double amps = std::ldexp(1.0, s->n);
+  if (s->fresh) {
+    uint64_t seen = 0;
+    size_t i = 0;
+    while (i < g.size() && g[i].kind == svp::K_H && !(seen & (1ull << g[i].q0)) &&
+           __builtin_popcountll(seen) < s->n) {
+      seen |= 1ull << g[i].q0;
+      ++i;
+    }
+    const bool uniform = __builtin_popcountll(seen) == s->n;
+    if (uniform) start = i;
+    prof_begin(s);
+    cudaError_t e = svk::launch_init(s->psi, s->n, uniform, (float)std::pow(2.0, -0.5 * s->n), s->stream);
+    prof_end(s, 8.0 * amps);
+    if (e != cudaSuccess) { s->broken = true; return cuda_fail(e, "init kernel"); }
+    s->fresh = false;
+  }
+  const float c = (float)(1.0 / std::sqrt(2.0));
+  for (size_t i = start; i < g.size(); ++i) {
+    const svp::Gate &x = g[i];
+    cudaError_t e = cudaSuccess;
+    const uint64_t b0 = 1ull << x.q0, b1 = 1ull << x.q1;
+    double bytes = 16.0 * amps;
+    prof_begin(s);
+    switch (x.kind) {
+      case svp::K_T: e = svk::launch_gate_diag(s->psi, s->n, b0, b0, c, c, s->stream); bytes = 8.0 * amps; break;
+      case svp::K_TDG: e = svk::launch_gate_diag(s->psi, s->n, b0, b0, c, -c, s->stream); bytes = 8.0 * amps; break;
+      case svp::K_Z: e = svk::launch_gate_diag(s->psi, s->n, b0, b0, -1.f, 0.f, s->stream); bytes = 8.0 * amps; break;
+      case svp::K_P0: e = svk::launch_gate_diag(s->psi, s->n, b0, b0, 0.f, 0.f, s->stream); bytes = 8.0 * amps; break;
+      case svp::K_P1: e = svk::launch_gate_diag(s->psi, s->n, b0, 0, 0.f, 0.f, s->stream); bytes = 8.0 * amps; break;
+      case svp::K_CZ: e = svk::launch_gate_diag(s->psi, s->n, b0 | b1, b0 | b1, -1.f, 0.f, s->stream); bytes = 4.0 * amps; break;
+      case svp::K_PEQ:
+        e = svk::launch_gate_diag(s->psi, s->n, b0 | b1, b0, 0.f, 0.f, s->stream);
+        if (e == cudaSuccess) e = svk::launch_gate_diag(s->psi, s->n, b0 | b1, b1, 0.f, 0.f, s->stream);
+        bytes = 8.0 * amps;
+        break;
+      default: {
+        double m[8];
+        svp::kind_matrix(x.kind, m);
+        svk::Mat2 u;
+        for (int k = 0; k < 8; ++k) u.v[k] = (float)m[k];
+        e = svk::launch_gate_1q(s->psi, s->n, x.q0, u, s->stream);
+      }
+    }
+    prof_end(s, bytes);
+    if (e != cudaSuccess) { s->broken = true; return cuda_fail(e, "per-gate kernel"); }
+  }
+  return SV_OK;
+}
+
+}  // namespace
+
+namespace svc {
+
+sv_status upload_plan(sv_state *s, const svp::Plan &P, svk::DevPlanView *view) {
+  auto align = [](size_t x) { return (x + 255) & ~(size_t)255; };
+  const size_t o_pass = 0;
+  const size_t o_stage = align(o_pass + P.passes.size() * sizeof(svp::DevPass));
+  const size_t o_op = align(o_stage + P.stages.size() * sizeof(svp::DevStage));
+  const size_t o_mat = align(o_op + P.ops.size() * sizeof(svp::DevOp));
+  const size_t total = align(o_mat + P.mats.size() * sizeof(float)) + 256;
+  sv_status st = ensure_device_buffer(&s->d_plan, &s->d_plan_cap, total);
+  if (st != SV_OK) return st;
+  s->h_plan.assign(total, 0);
+  if (!P.passes.empty()) std::memcpy(&s->h_plan[o_pass], P.passes.data(), P.passes.size() * sizeof(svp::DevPass));
+  if (!P.stages.empty()) std::memcpy(&s->h_plan[o_stage], P.stages.data(), P.stages.size() * sizeof(svp::DevStage));
+  if (!P.ops.empty()) std::memcpy(&s->h_plan[o_op], P.ops.data(), P.ops.size() * sizeof(svp::DevOp));
+  if (!P.mats.empty()) std::memcpy(&s->h_plan[o_mat], P.mats.data(), P.mats.size() * sizeof(float));
+  cudaError_t e = cudaMemcpyAsync(s->d_plan, s->h_plan.data(), total, cudaMemcpyHostToDevice, s->stream);
+  if (e != cudaSuccess) return cuda_fail(e, "plan upload");
+  if (s->prof) s->h2d += (double)total;
+  char *d = static_cast<char *>(s->d_plan);
+  view->passes = reinterpret_cast<const svp::DevPass *>(d + o_pass);
+  view->stages = reinterpret_cast<const svp::DevStage *>(d + o_stage);
+  view->ops = reinterpret_cast<const svp::DevOp *>(d + o_op);
+  view->mats = reinterpret_cast<const float *>(d + o_mat);
+  return SV_OK;
+}
+
+sv_status run_plan(sv_state *s, const svp::Plan &P, const svk::DevPlanView &view) {
+  const double amps = std::ldexp(1.0, s->n);
+  for (size_t p = 0; p < P.passes.size(); ++p) {
+    const svp::DevPass &hp = P.passes[p];
+    const double bytes = (hp.flags & (svp::PF_INIT_UNIFORM | svp::PF_INIT_ZERO)) ? 8.0 * amps : 16.0 * amps;
+    prof_begin(s);
+    cudaError_t e = s->opts.precision == SV_PREC_TF32X3
+                        ? svk::launch_fused_pass(s->psi, s->n, view, (int)p, hp, s->stream)
+                        : svk::launch_tile_pass(s->psi, s->n, view, (int)p, hp, s->stream);
+    prof_end(s, bytes);
+    if (e != cudaSuccess) { s->broken = true; return cuda_fail(e, "tile pass kernel"); }
+  }
+  return SV_OK;
+}
+
+sv_status build_stage_mats(svp::Plan *P, const std::vector<svp::Gate> &g, int r);
+
+}  // namespace svc
+
+namespace svc {
+
+sv_status apply_gates(sv_state *s, const std::vector<svp::Gate> &g) {
+  sv_status st;
+  if ((st = set_device(s)) != SV_OK) return st;
+  if (s->opts.precision == SV_PREC_PERGATE || s->n < 6) return apply_pergate(s, g);
+  if (s->opts.precision == SV_PREC_TF32X3 && !svk::fused_supported())
+    return fail(SV_ERR_CUDA, "fused tensor-core path needs an sm_103a device");
+  if (g.empty() && !s->fresh) return SV_OK;
+  svp::Plan P;
+  const char *err = nullptr;
+  svp::Options po = plan_options(s->opts);
+  if (!svp::build_plan(s->n, g, po, s->fresh, &P, &err)) return fail(SV_ERR_ARG, err ? err : "planning failed");
+  if (po.fused && (st = build_stage_mats(&P, g, std::min(po.r, std::min(po.m, s->n)))) != SV_OK) return st;
+  svk::DevPlanView view;
+  if ((st = upload_plan(s, P, &view)) != SV_OK) return st;
+  if ((st = run_plan(s, P, view)) != SV_OK) return st;
+  s->fresh = false;
+  return SV_OK;
+}
+
+}  // namespace svc
+
+static sv_status apply_impl(sv_state *s, const sv_gate *gates, size_t n_gates, bool inverse) {
+  clear_error();
+  if (!s) return fail(SV_ERR_ARG, "null state");
+  if (s->broken) return fail(SV_ERR_STATE, "state is unusable after an earlier failure");
+  std::vector<svp::Gate> g;
+  sv_status st = convert_gates(s->n, gates, n_gates, inverse, &g);
+  if (st != SV_OK) return st;
+  return apply_gates(s, g);
+}
+
+extern "C" {
+
+sv_status sv_create(int n_qubits, const sv_options *opts, sv_state **out) {
+  clear_error();
+  if (!out) return fail(SV_ERR_ARG, "sv_create: out is NULL");
+  *out = nullptr;
+  if (n_qubits < 1 || n_qubits > 34) return fail(SV_ERR_ARG, "sv_create: n_qubits must be 1..34");
+  sv_options o;
+  std::memset(&o, 0, sizeof(o));
+  if (opts) o = *opts;
+  sv_status st = check_options(o);
+  if (st != SV_OK) return st;
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return cuda_fail(e, "sv_create: no CUDA device");
+  void *p = nullptr;
+  e = cudaMalloc(&p, sizeof(float2) << n_qubits);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    return fail(SV_ERR_OOM, "sv_create: cudaMalloc of the state failed");
+  }
+  sv_state *s = new sv_state();
+  s->n = n_qubits;
+  s->psi = static_cast<float2 *>(p);
+  s->owns = true;
+  s->opts = o;
+  s->stream = static_cast<cudaStream_t>(o.stream);
+  s->device = dev;
+  s->fresh = true;
+  *out = s;
+  return SV_OK;
+}
+
+sv_status sv_create_from_ptr(int n_qubits, void *dev_ptr, void *stream, sv_state **out) {
+  clear_error();
+  if (!out || !dev_ptr) return fail(SV_ERR_ARG, "sv_create_from_ptr: NULL argument");
+  *out = nullptr;
+  if (n_qubits < 1 || n_qubits > 34) return fail(SV_ERR_ARG, "sv_create_from_ptr: n_qubits must be 1..34");
+  if ((reinterpret_cast<uintptr_t>(dev_ptr) & 15) != 0)
+    return fail(SV_ERR_ARG, "sv_create_from_ptr: buffer must be 16-byte aligned");
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return cuda_fail(e, "sv_create_from_ptr: no CUDA device");
+  sv_state *s = new sv_state();
+  s->n = n_qubits;
+  s->psi = static_cast<float2 *>(dev_ptr);
+  s->owns = false;
+  std::memset(&s->opts, 0, sizeof(s->opts));
+  s->opts.stream = stream;
+  s->stream = static_cast<cudaStream_t>(stream);
+  s->device = dev;
+  s->fresh = false;
+  *out = s;
+  return SV_OK;
+}
+
+sv_status sv_destroy(sv_state *s) {
+  clear_error();
+  if (!s) return SV_OK;
+  cudaSetDevice(s->device);
+  cudaStreamSynchronize(s->stream);
+  if (s->owns && s->psi) cudaFree(s->psi);
+  if (s->d_plan) cudaFree(s->d_plan);
+  if (s->d_scratch) cudaFree(s->d_scratch);
+  for (cudaEvent_t ev : s->events) cudaEventDestroy(ev);
+  delete s;
+  return SV_OK;
+}
+
+sv_status sv_set_options(sv_state *s, const sv_options *opts) {
+  clear_error();
+  if (!s || !opts) return fail(SV_ERR_ARG, "sv_set_options: NULL argument");
+  sv_status st = check_options(*opts);
+  if (st != SV_OK) return st;
+  s->opts = *opts;
+  s->stream = static_cast<cudaStream_t>(opts->stream);
+  return SV_OK;
+}
+
+sv_status sv_reset(sv_state *s) {
+  clear_error();
+  if (!s) return fail(SV_ERR_ARG, "sv_reset: NULL state");
+  s->fresh = true;
+  s->broken = false;
+  return SV_OK;
+}
+
+sv_status sv_device_ptr(sv_state *s, void **ptr) {
+  clear_error();
+  if (!s || !ptr) return fail(SV_ERR_ARG, "sv_device_ptr: NULL argument");
+  sv_status st = set_device(s);
+  if (st != SV_OK) return st;
+  if ((st = materialize(s)) != SV_OK) return st;
+  *ptr = s->psi;
+  return SV_OK;
+}
+
+sv_status sv_copy_state(sv_state *s, void *dst) {
+  clear_error();
+  if (!s || !dst) return fail(SV_ERR_ARG, "sv_copy_state: NULL argument");
+  if (s->broken) return fail(SV_ERR_STATE, "state is unusable after an earlier failure");
+  sv_status st = set_device(s);
+  if (st != SV_OK) return st;
+  if ((st = materialize(s)) != SV_OK) return st;
+  cudaError_t e = cudaMemcpyAsync(dst, s->psi, sizeof(float2) << s->n, cudaMemcpyDefault, s->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s->stream);
+  if (e != cudaSuccess) return cuda_fail(e, "sv_copy_state");
+  return SV_OK;
+}
+
+sv_status sv_load_state(sv_state *s, const void *src) {
+  clear_error();
+  if (!s || !src) return fail(SV_ERR_ARG, "sv_load_state: NULL argument");
+  sv_status st = set_device(s);
+  if (st != SV_OK) return st;
+  cudaError_t e = cudaMemcpyAsync(s->psi, src, sizeof(float2) << s->n, cudaMemcpyDefault, s->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s->stream);
+  if (e != cudaSuccess) return cuda_fail(e, "sv_load_state");
+  s->fresh = false;
+  s->broken = false;
+  return SV_OK;
+}
+
+sv_status sv_apply_circuit(sv_state *s, const sv_gate *gates, size_t n_gates) {
+  return apply_impl(s, gates, n_gates, false);
+}
+
+sv_status sv_apply_circuit_inverse(sv_state *s, const sv_gate *gates, size_t n_gates) {
+  return apply_impl(s, gates, n_gates, true);
+}
+
+static sv_status gather_common(sv_state *s, const uint64_t *bits, size_t m, double *out, bool prob) {
+  clear_error();
+  if (!s || (m && (!bits || !out))) return fail(SV_ERR_ARG, "NULL argument");
+  if (s->broken) return fail(SV_ERR_STATE, "state is unusable after an earlier failure");
+  for (size_t j = 0; j < m; ++j)
+    if (s->n < 64 && (bits[j] >> s->n)) return failf(SV_ERR_ARG, "bitstring %s%lld has bits >= n", "#", (long long)j);
+  if (m == 0) return SV_OK;
+  sv_status st = set_device(s);
+  if (st != SV_OK) return st;
+  if ((st = materialize(s)) != SV_OK) return st;
+  const size_t need = m * sizeof(uint64_t) + 2 * m * sizeof(double) + 512;
+  if ((st = ensure_device_buffer(&s->d_scratch, &s->d_scratch_cap, need)) != SV_OK) return st;
+  uint64_t *d_bits = static_cast<uint64_t *>(s->d_scratch);
+  double *d_out = reinterpret_cast<double *>(static_cast<char *>(s->d_scratch) + ((m * sizeof(uint64_t) + 255) & ~(size_t)255));
+  cudaError_t e = cudaMemcpyAsync(d_bits, bits, m * sizeof(uint64_t), cudaMemcpyHostToDevice, s->stream);
+  if (e == cudaSuccess)
+    e = prob ? svk::launch_gather_prob(s->psi, d_bits, (int64_t)m, d_out, s->stream)
+             : svk::launch_gather(s->psi, d_bits, (int64_t)m, d_out, s->stream);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(out, d_out, (prob ? 1 : 2) * m * sizeof(double), cudaMemcpyDeviceToHost, s->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s->stream);
+  if (e != cudaSuccess) return cuda_fail(e, "amplitude gather");
+  if (s->prof) {
+    s->h2d += (double)(m * sizeof(uint64_t));
+    s->d2h += (double)((prob ? 1 : 2) * m * sizeof(double));
+    s->other_launches += 1;
+  }
+  return SV_OK;
+}
+
+sv_status sv_get_amplitudes(sv_state *s, const uint64_t *bits, size_t m, double *out_re_im) {
+  return gather_common(s, bits, m, out_re_im, false);
+}
+
+sv_status sv_get_probabilities(sv_state *s, const uint64_t *bits, size_t m, double *out) {
+  return gather_common(s, bits, m, out, true);
+}
+
+sv_status sv_norm(sv_state *s, double *norm2, double *sum_p2) {
+  clear_error();
+  if (!s) return fail(SV_ERR_ARG, "sv_norm: NULL state");
+  if (s->broken) return fail(SV_ERR_STATE, "state is unusable after an earlier failure");
+  sv_status st = set_device(s);
+  if (st != SV_OK) return st;
+  if ((st = materialize(s)) != SV_OK) return st;
+  const size_t need = (size_t)(svk::reduce_partials_needed() + 2) * 2 * sizeof(double);
+  if ((st = ensure_device_buffer(&s->d_scratch, &s->d_scratch_cap, need)) != SV_OK) return st;
+  double *partials = static_cast<double *>(s->d_scratch);
+  double *res = partials + 2 * svk::reduce_partials_needed();
+  double h[2] = {0, 0};
+  cudaError_t e = svk::launch_norm(s->psi, s->n, partials, res, s->stream);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(h, res, sizeof(h), cudaMemcpyDeviceToHost, s->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s->stream);
+  if (e != cudaSuccess) return cuda_fail(e, "sv_norm");
+  if (s->prof) {
+    s->d2h += sizeof(h);
+    s->other_launches += s->n < 2 ? 1 : 2;
+  }
+  if (norm2) *norm2 = h[0];
+  if (sum_p2) *sum_p2 = h[1];
+  return SV_OK;
+}
+
+sv_status sv_plan(int n_qubits, const sv_gate *gates, size_t n_gates, const sv_options *opts, int fresh_state,
+                  sv_plan_summary *summary, int32_t *order_out, int32_t *pass_out, int32_t *tile_out,
+                  size_t tile_cap) {
+  clear_error();
+  if (n_qubits < 1 || n_qubits > 64) return fail(SV_ERR_ARG, "sv_plan: n_qubits must be 1..64");
+  sv_options o;
+  std::memset(&o, 0, sizeof(o));
+  if (opts) o = *opts;
+  sv_status st = check_options(o);
+  if (st != SV_OK) return st;
+  std::vector<svp::Gate> g;
+  if ((st = convert_gates(n_qubits, gates, n_gates, false, &g)) != SV_OK) return st;
+  svp::Plan P;
+  const char *err = nullptr;
+  if (!svp::build_plan(n_qubits, g, plan_options(o), fresh_state != 0, &P, &err))
+    return fail(SV_ERR_ARG, err ? err : "planning failed");
+  if (summary) {
+    summary->passes = (int)P.passes.size();
+    summary->stages = (int)P.stages.size();
+    summary->ops = (int)P.ops.size();
+    summary->init_uniform = P.init_uniform ? 1 : 0;
+    summary->hbm_bytes = P.hbm_bytes;
+  }
+  if (order_out) std::copy(P.order.begin(), P.order.end(), order_out);
+  if (pass_out) std::copy(P.pass_of.begin(), P.pass_of.end(), pass_out);
+  if (tile_out) {
+    if (tile_cap < 64 * P.passes.size()) return fail(SV_ERR_ARG, "sv_plan: tile_cap too small");
+    for (size_t p = 0; p < P.passes.size(); ++p) {
+      for (int i = 0; i < 64; ++i) tile_out[64 * p + i] = -1;
+      for (int i = 0; i < P.passes[p].m; ++i) tile_out[64 * p + i] = P.passes[p].tq[i];
+    }
+  }
+  return SV_OK;
+}
+
+sv_status sv_set_profiling(sv_state *s, int on) {
+  clear_error();
+  if (!s) return fail(SV_ERR_ARG, "NULL state");
+  s->prof = on != 0;
+  s->ev_used = 0;
+  s->ev_bytes.clear();
+  s->h2d = s->d2h = 0;
+  s->other_launches = 0;
+  return SV_OK;
+}
+
+sv_status sv_get_profile(sv_state *s, sv_profile *out) {
+  clear_error();
+  if (!s || !out) return fail(SV_ERR_ARG, "NULL argument");
+  cudaError_t e = cudaStreamSynchronize(s->stream);
+  if (e != cudaSuccess) return cuda_fail(e, "sv_get_profile");
+  out->launches = (int)(s->ev_used / 2);
+  out->ms = 0;
+  out->hbm_bytes = 0;
+  out->h2d_bytes = s->h2d;
+  out->d2h_bytes = s->d2h;
+  out->other_launches = s->other_launches;
+  for (size_t i = 0; i + 1 < s->ev_used; i += 2) {
+    float ms = 0;
+    if (cudaEventElapsedTime(&ms, s->events[i], s->events[i + 1]) == cudaSuccess) out->ms += ms;
+    out->hbm_bytes += s->ev_bytes[i / 2];
+  }
+  return SV_OK;
+}
+
+}  // extern "C"

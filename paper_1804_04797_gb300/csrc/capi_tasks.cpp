@@ -1,0 +1,150 @@
+// C ABI of the two composite tasks: few amplitudes by the cut decomposition (K6) and
+// the uneven batch of independent circuits (K7).
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <vector>
+
+#include "../../include/sv.h"
+#include "capi_util.h"
+#include "kernels.h"
+#include "plan.h"
+#include "state.h"
+
+using namespace svc;
+
+namespace {
+
+struct Holder {  // destroys a handle on scope exit
+  sv_state *s = nullptr;
+  ~Holder() { if (s) sv_destroy(s); }
+};
+
+sv_status generate(const sv_lattice *lat, std::vector<sv_gate> *g) {
+  size_t n = 0;
+  sv_status st = sv_generate_circuit(lat, nullptr, 0, &n);
+  if (st != SV_OK) return st;
+  g->resize(n);
+  return sv_generate_circuit(lat, g->data(), n, &n);
+}
+
+int lattice_qubits(const sv_lattice *lat) {
+  const int sites = lat->rows * lat->cols;
+  int n = 0;
+  for (int i = 0; i < sites; ++i) n += !((lat->removed_mask >> i) & 1ull);
+  return n;
+}
+
+}  // namespace
+
+extern "C" sv_status sv_branch_amplitudes(const sv_lattice *lat, const sv_cut *cut, const uint64_t *bits,
+                                          size_t m, const sv_options *opts, double *out_re_im) {
+  clear_error();
+  if (!lat || !cut || (m && (!bits || !out_re_im)))
+    return fail(SV_ERR_ARG, "sv_branch_amplitudes: NULL argument");
+  std::vector<sv_gate> g;
+  sv_status st = generate(lat, &g);
+  if (st != SV_OK) return st;
+  const int n = lattice_qubits(lat);
+  // split the qubits: local numbering ascending within each half
+  int local[64], na = 0, nb = 0;
+  bool in_a[64];
+  for (int q = 0; q < n; ++q) {
+    in_a[q] = (cut->half_a_mask >> q) & 1ull;
+    local[q] = in_a[q] ? na++ : nb++;
+  }
+  if (na < 1 || nb < 1) return fail(SV_ERR_ARG, "sv_branch_amplitudes: both halves need qubits");
+  for (size_t j = 0; j < m; ++j)
+    if (n < 64 && (bits[j] >> n)) return fail(SV_ERR_ARG, "sv_branch_amplitudes: bitstring has bits >= n");
+  // count the crossing CZs
+  int t = 0;
+  for (const sv_gate &x : g)
+    if (x.kind == SV_CZ && in_a[x.q0] != in_a[x.q1]) ++t;
+  if (na + t > 34 || nb + t > 34)
+    return fail(SV_ERR_ARG, "sv_branch_amplitudes: half qubits + crossing CZs must be <= 34");
+  // Half gate lists on (n_half + t) qubits: branch bit j is qubit n_half + j.  Every
+  // qubit (branch bits included) starts with H, so each branch slice holds its half's
+  // state times 2^{-t/2}; the sum is rescaled by 2^t.  Crossing CZ j becomes the
+  // projector P_{l_j} on the half-A qubit (zero where x_a != l_j) and Z^{l_j} on the
+  // half-B qubit (a CZ with branch bit j).
+  std::vector<svp::Gate> ga, gb;
+  for (int q = 0; q < na + t; ++q) ga.push_back(svp::Gate{svp::K_H, (uint8_t)q, 0});
+  for (int q = 0; q < nb + t; ++q) gb.push_back(svp::Gate{svp::K_H, (uint8_t)q, 0});
+  int j = 0;
+  for (const sv_gate &x : g) {
+    if (x.kind == SV_H && x.layer == 0) continue;  // already the leading H layer
+    if (x.kind == SV_CZ && in_a[x.q0] != in_a[x.q1]) {
+      const int qa = in_a[x.q0] ? x.q0 : x.q1, qb = in_a[x.q0] ? x.q1 : x.q0;
+      ga.push_back(svp::Gate{svp::K_PEQ, (uint8_t)local[qa], (uint8_t)(na + j)});
+      gb.push_back(svp::Gate{svp::K_CZ, (uint8_t)local[qb], (uint8_t)(nb + j)});
+      ++j;
+      continue;
+    }
+    std::vector<svp::Gate> &dst = in_a[x.q0] ? ga : gb;
+    dst.push_back(svp::Gate{x.kind, (uint8_t)local[x.q0], (uint8_t)(x.kind == SV_CZ ? local[x.q1] : 0)});
+  }
+  sv_options o;
+  std::memset(&o, 0, sizeof(o));
+  if (opts) o = *opts;
+  Holder A, B;
+  if ((st = sv_create(na + t, &o, &A.s)) != SV_OK) return st;
+  if ((st = sv_create(nb + t, &o, &B.s)) != SV_OK) return st;
+  if ((st = apply_gates(A.s, ga)) != SV_OK) return st;
+  if ((st = apply_gates(B.s, gb)) != SV_OK) return st;
+  if (m == 0) return SV_OK;
+  // bitstring -> half indices
+  std::vector<uint64_t> xab(2 * m);
+  for (size_t k = 0; k < m; ++k) {
+    uint64_t xa = 0, xb = 0;
+    for (int q = 0; q < n; ++q) {
+      const uint64_t b = (bits[k] >> q) & 1ull;
+      if (in_a[q]) xa |= b << local[q];
+      else xb |= b << local[q];
+    }
+    xab[k] = xa;
+    xab[m + k] = xb;
+  }
+  sv_state *s = A.s;
+  const size_t need = 2 * m * sizeof(uint64_t) + 2 * m * sizeof(double) + 512;
+  if ((st = ensure_device_buffer(&s->d_scratch, &s->d_scratch_cap, need)) != SV_OK) return st;
+  uint64_t *d_x = static_cast<uint64_t *>(s->d_scratch);
+  double *d_out = reinterpret_cast<double *>(static_cast<char *>(s->d_scratch) +
+                                             ((2 * m * sizeof(uint64_t) + 255) & ~(size_t)255));
+  cudaError_t e = cudaStreamSynchronize(B.s->stream);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(d_x, xab.data(), 2 * m * sizeof(uint64_t), cudaMemcpyHostToDevice, s->stream);
+  if (e == cudaSuccess)
+    e = svk::launch_branch_sum(A.s->psi, na, B.s->psi, nb, t, d_x, d_x + m, (int)m, std::ldexp(1.0, t), d_out,
+                               s->stream);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(out_re_im, d_out, 2 * m * sizeof(double), cudaMemcpyDeviceToHost, s->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s->stream);
+  if (e != cudaSuccess) return cuda_fail(e, "sv_branch_amplitudes");
+  return SV_OK;
+}
+
+extern "C" sv_status sv_apply_batch(const sv_lattice *circs, size_t count, const sv_options *opts,
+                                    double *stats_out) {
+  clear_error();
+  if (count && !circs) return fail(SV_ERR_ARG, "sv_apply_batch: NULL lattice array");
+  sv_status st;
+  for (size_t i = 0; i < count; ++i) {
+    const int n = lattice_qubits(&circs[i]);
+    if (n < 1 || n > 28) return fail(SV_ERR_ARG, "sv_apply_batch: circuits must have 1..28 qubits");
+    std::vector<sv_gate> g;
+    if ((st = generate(&circs[i], &g)) != SV_OK) return st;
+    Holder h;
+    if ((st = sv_create(n, opts, &h.s)) != SV_OK) return st;
+    if ((st = sv_apply_circuit(h.s, g.data(), g.size())) != SV_OK) return st;
+    double a = 0, b = 0;
+    if ((st = sv_norm(h.s, &a, &b)) != SV_OK) return st;
+    if (stats_out) {
+      stats_out[3 * i] = a;
+      stats_out[3 * i + 1] = b;
+      stats_out[3 * i + 2] = n;
+    }
+  }
+  return SV_OK;
+}

@@ -1,0 +1,386 @@
+// Plain (fp32 CUDA-core) tile pass.
+//
+// One launch = one pass of the plan = one read and one write of every amplitude.
+// Each CTA loops over gathered tiles: the 2^m amplitudes whose indices differ only in
+// the pass's m tile qubits (the c lowest qubits are always among them, so the tile is
+// 2^(m-c) contiguous chunks of 2^c amplitudes and every global access is a coalesced
+// 16-byte vector).  The tile is staged in shared memory (the on-chip copy of the
+// paper's "local qubits" in LDM, §2.3) and every gate of the pass is applied to it:
+// stage by stage, each thread pulls the 2^5 amplitudes that differ in the stage's
+// five register qubits into registers, applies the stage's gates there (the pair
+// update of §2 on register pairs; diagonal gates as sign/phase/zero on selected
+// elements, conditioned on the thread's other index bits), and writes them back.
+// Shared memory is XOR-swizzled (bits 4.., folded onto bits 0..3) so that the
+// register-group reads of a warp hit distinct banks.
+#include <cuda_runtime.h>
+
+#include "kernels.h"
+
+namespace svk {
+namespace {
+
+using svp::DevOp;
+using svp::DevPass;
+using svp::DevStage;
+
+constexpr int kR = 5;
+constexpr int kE = 1 << kR;
+constexpr int kThreads = 256;  // 2^(13 - kR): one register group per thread
+constexpr float kS2 = 0.70710678118654752440f;
+
+__device__ __forceinline__ uint32_t swz(uint32_t L) {
+  return L ^ (((L >> 4) ^ (L >> 8) ^ (L >> 12)) & 15u);
+}
+
+__device__ __forceinline__ float2 f2(float a, float b) { return make_float2(a, b); }
+
+// ---- one-qubit gates on a pair (x: register bit 0, y: register bit 1) ---------------
+struct GH {
+  __device__ __forceinline__ static void f(float2 &x, float2 &y) {
+    const float2 a = x, b = y;
+    x = f2(kS2 * (a.x + b.x), kS2 * (a.y + b.y));
+    y = f2(kS2 * (a.x - b.x), kS2 * (a.y - b.y));
+  }
+};
+// X^{1/2}: x' = (s + i d)/2, y' = (s - i d)/2 with s = x + y, d = x - y
+struct GSX {
+  __device__ __forceinline__ static void f(float2 &x, float2 &y) {
+    const float sr = x.x + y.x, si = x.y + y.y, dr = x.x - y.x, di = x.y - y.y;
+    x = f2(0.5f * (sr - di), 0.5f * (si + dr));
+    y = f2(0.5f * (sr + di), 0.5f * (si - dr));
+  }
+};
+struct GSXDG {
+  __device__ __forceinline__ static void f(float2 &x, float2 &y) {
+    const float sr = x.x + y.x, si = x.y + y.y, dr = x.x - y.x, di = x.y - y.y;
+    x = f2(0.5f * (sr + di), 0.5f * (si - dr));
+    y = f2(0.5f * (sr - di), 0.5f * (si + dr));
+  }
+};
+// Y^{1/2}: x' = (1+i)(x - y)/2, y' = (1+i)(x + y)/2
+struct GSY {
+  __device__ __forceinline__ static void f(float2 &x, float2 &y) {
+    const float sr = x.x + y.x, si = x.y + y.y, dr = x.x - y.x, di = x.y - y.y;
+    x = f2(0.5f * (dr - di), 0.5f * (dr + di));
+    y = f2(0.5f * (sr - si), 0.5f * (sr + si));
+  }
+};
+// (Y^{1/2})^dagger: x' = (1-i)(x + y)/2, y' = -(1-i)(x - y)/2
+struct GSYDG {
+  __device__ __forceinline__ static void f(float2 &x, float2 &y) {
+    const float sr = x.x + y.x, si = x.y + y.y, dr = x.x - y.x, di = x.y - y.y;
+    x = f2(0.5f * (sr + si), 0.5f * (si - sr));
+    y = f2(-0.5f * (dr + di), -0.5f * (di - dr));
+  }
+};
+
+// ---- diagonal actions on one element -------------------------------------------------
+struct DT {  // times e^{i pi/4}
+  __device__ __forceinline__ static void f(float2 &z) { z = f2(kS2 * (z.x - z.y), kS2 * (z.x + z.y)); }
+};
+struct DTDG {
+  __device__ __forceinline__ static void f(float2 &z) { z = f2(kS2 * (z.x + z.y), kS2 * (z.y - z.x)); }
+};
+struct DNEG {
+  __device__ __forceinline__ static void f(float2 &z) { z = f2(-z.x, -z.y); }
+};
+struct DZERO {
+  __device__ __forceinline__ static void f(float2 &z) { z = f2(0.f, 0.f); }
+};
+
+template <class G, int J>
+__device__ __forceinline__ void pairs(float2 (&v)[kE]) {
+#pragma unroll
+  for (int e = 0; e < kE; ++e)
+    if (!(e & (1 << J))) G::f(v[e], v[e | (1 << J)]);
+}
+template <class G>
+__device__ __forceinline__ void pairs_j(float2 (&v)[kE], int j) {
+  switch (j) {
+    case 0: pairs<G, 0>(v); break;
+    case 1: pairs<G, 1>(v); break;
+    case 2: pairs<G, 2>(v); break;
+    case 3: pairs<G, 3>(v); break;
+    default: pairs<G, 4>(v); break;
+  }
+}
+// D on the elements whose register bit J equals B
+template <class D, int J, int B>
+__device__ __forceinline__ void diag1(float2 (&v)[kE]) {
+#pragma unroll
+  for (int e = 0; e < kE; ++e)
+    if (((e >> J) & 1) == B) D::f(v[e]);
+}
+template <class D, int B>
+__device__ __forceinline__ void diag1_j(float2 (&v)[kE], int j) {
+  switch (j) {
+    case 0: diag1<D, 0, B>(v); break;
+    case 1: diag1<D, 1, B>(v); break;
+    case 2: diag1<D, 2, B>(v); break;
+    case 3: diag1<D, 3, B>(v); break;
+    default: diag1<D, 4, B>(v); break;
+  }
+}
+// CZ: negate where bits J and K are both 1; PEQ: zero where bits J and K differ
+template <int J, int K, bool EQ>
+__device__ __forceinline__ void diag2(float2 (&v)[kE]) {
+#pragma unroll
+  for (int e = 0; e < kE; ++e) {
+    const int bj = (e >> J) & 1, bk = (e >> K) & 1;
+    if (EQ) {
+      if (bj != bk) DZERO::f(v[e]);
+    } else if (bj && bk) {
+      DNEG::f(v[e]);
+    }
+  }
+}
+template <int J, bool EQ>
+__device__ __forceinline__ void diag2_k(float2 (&v)[kE], int k) {
+  switch (k) {
+    case 0: diag2<J, 0, EQ>(v); break;
+    case 1: diag2<J, 1, EQ>(v); break;
+    case 2: diag2<J, 2, EQ>(v); break;
+    case 3: diag2<J, 3, EQ>(v); break;
+    default: diag2<J, 4, EQ>(v); break;
+  }
+}
+template <bool EQ>
+__device__ __forceinline__ void diag2_jk(float2 (&v)[kE], int j, int k) {
+  switch (j) {
+    case 0: diag2_k<0, EQ>(v, k); break;
+    case 1: diag2_k<1, EQ>(v, k); break;
+    case 2: diag2_k<2, EQ>(v, k); break;
+    case 3: diag2_k<3, EQ>(v, k); break;
+    default: diag2_k<4, EQ>(v, k); break;
+  }
+}
+
+__device__ __forceinline__ void phase_all(float2 (&v)[kE], int p) {
+  switch (p & 7) {
+    case 0: break;
+    case 4:
+#pragma unroll
+      for (int e = 0; e < kE; ++e) DNEG::f(v[e]);
+      break;
+    case 2:
+#pragma unroll
+      for (int e = 0; e < kE; ++e) v[e] = f2(-v[e].y, v[e].x);
+      break;
+    case 6:
+#pragma unroll
+      for (int e = 0; e < kE; ++e) v[e] = f2(v[e].y, -v[e].x);
+      break;
+    default: {
+      // w^p for odd p: (+-1 +- i)/sqrt2
+      const float cr = (p == 1 || p == 7) ? kS2 : -kS2;
+      const float ci = (p == 1 || p == 3) ? kS2 : -kS2;
+#pragma unroll
+      for (int e = 0; e < kE; ++e) v[e] = f2(cr * v[e].x - ci * v[e].y, cr * v[e].y + ci * v[e].x);
+    }
+  }
+}
+
+template <int J>
+__device__ __forceinline__ void general1(float2 (&v)[kE], const float *u) {
+  const float ar = u[0], ai = u[1], br = u[2], bi = u[3], cr = u[4], ci = u[5], dr = u[6], di = u[7];
+#pragma unroll
+  for (int e = 0; e < kE; ++e) {
+    if (e & (1 << J)) continue;
+    const float2 x = v[e], y = v[e | (1 << J)];
+    v[e] = f2(ar * x.x - ai * x.y + br * y.x - bi * y.y, ar * x.y + ai * x.x + br * y.y + bi * y.x);
+    v[e | (1 << J)] = f2(cr * x.x - ci * x.y + dr * y.x - di * y.y, cr * x.y + ci * x.x + dr * y.y + di * y.x);
+  }
+}
+
+__device__ __forceinline__ void apply_op(float2 (&v)[kE], const DevOp &op, const float *mats) {
+  using namespace svp;
+  switch (op.act) {
+    case A_H: pairs_j<GH>(v, op.j); break;
+    case A_SX: pairs_j<GSX>(v, op.j); break;
+    case A_SY: pairs_j<GSY>(v, op.j); break;
+    case A_SXDG: pairs_j<GSXDG>(v, op.j); break;
+    case A_SYDG: pairs_j<GSYDG>(v, op.j); break;
+    case A_T: diag1_j<DT, 1>(v, op.j); break;
+    case A_TDG: diag1_j<DTDG, 1>(v, op.j); break;
+    case A_Z: diag1_j<DNEG, 1>(v, op.j); break;
+    case A_P0: diag1_j<DZERO, 1>(v, op.j); break;
+    case A_P1: diag1_j<DZERO, 0>(v, op.j); break;
+    case A_CZ: diag2_jk<false>(v, op.j, op.k); break;
+    case A_PEQ: diag2_jk<true>(v, op.j, op.k); break;
+    case A_PHASE: phase_all(v, op.arg); break;
+    case A_ZERO:
+#pragma unroll
+      for (int e = 0; e < kE; ++e) DZERO::f(v[e]);
+      break;
+    case A_U: {
+      const float *u = mats + 8 * (op.arg | (op.k << 8));
+      switch (op.j) {
+        case 0: general1<0>(v, u); break;
+        case 1: general1<1>(v, u); break;
+        case 2: general1<2>(v, u); break;
+        case 3: general1<3>(v, u); break;
+        default: general1<4>(v, u); break;
+      }
+    } break;
+    default: break;
+  }
+}
+
+__global__ void __launch_bounds__(kThreads, 2)
+tile_pass_kernel(float2 *__restrict__ psi, DevPlanView plan, int pass_index, uint64_t num_tiles) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  float2 *tile = reinterpret_cast<float2 *>(smem_raw);
+  __shared__ DevPass P;
+  __shared__ uint64_t chunk_off[1 << 10];  // deposit of chunk index bits into tile qubits
+
+  const int tid = threadIdx.x;
+  if (tid == 0) P = plan.passes[pass_index];
+  __syncthreads();
+  const int m = P.m, c = P.c;
+  const int nthreads = blockDim.x;
+  const uint32_t half = 1u << (m - 1);  // float4 slots per tile
+  const int nchunk_bits = m - c;
+  for (int h = tid; h < (1 << nchunk_bits); h += nthreads) {
+    uint64_t off = 0;
+    for (int i = 0; i < nchunk_bits; ++i)
+      if ((h >> i) & 1) off |= 1ull << P.tq[c + i];
+    chunk_off[h] = off;
+  }
+  __syncthreads();
+  const uint32_t low_mask = (1u << c) - 1;
+
+  for (uint64_t tile_id = blockIdx.x; tile_id < num_tiles; tile_id += gridDim.x) {
+    uint64_t base = 0;
+    for (int i = 0; i < P.nt; ++i) base |= ((tile_id >> i) & 1ull) << P.ntq[i];
+
+    // ---- load (or generate) the tile --------------------------------------------
+    if (P.flags & svp::PF_INIT_UNIFORM) {
+      const float a = P.init_amp;
+      for (uint32_t f = tid; f < half; f += nthreads)
+        reinterpret_cast<float4 *>(tile)[f] = make_float4(a, 0.f, a, 0.f);
+    } else if (P.flags & svp::PF_INIT_ZERO) {
+      for (uint32_t f = tid; f < half; f += nthreads)
+        reinterpret_cast<float4 *>(tile)[f] = make_float4((f == 0 && base == 0) ? 1.f : 0.f, 0.f, 0.f, 0.f);
+    } else {
+      // 16 float4 per thread, issued in two batches of 8 (128 B in flight per thread)
+      constexpr int kBatch = 8;
+      const int iters = (int)(half / nthreads);
+      for (int it0 = 0; it0 < iters; it0 += kBatch) {
+        float4 buf[kBatch];
+#pragma unroll
+        for (int b = 0; b < kBatch; ++b) {
+          const uint32_t L = 2u * (tid + (it0 + b) * nthreads);
+          const uint64_t g = base + chunk_off[L >> c] + (L & low_mask);
+          buf[b] = *reinterpret_cast<const float4 *>(psi + g);
+        }
+#pragma unroll
+        for (int b = 0; b < kBatch; ++b) {
+          const uint32_t L = 2u * (tid + (it0 + b) * nthreads);
+          const uint32_t p = swz(L);
+          float4 x = buf[b];
+          if (p & 1u) x = make_float4(x.z, x.w, x.x, x.y);
+          reinterpret_cast<float4 *>(tile)[p >> 1] = x;
+        }
+      }
+    }
+    __syncthreads();
+
+    // ---- stages ---------------------------------------------------------------------
+    for (int s = 0; s < P.stage_count; ++s) {
+      const DevStage &st = plan.stages[P.stage_begin + s];
+      uint32_t L0 = 0;
+      uint64_t G0 = base;
+      const int ng = m - kR;
+      for (int i = 0; i < ng; ++i) {
+        if ((tid >> i) & 1) {
+          const int b = st.nonr[i];
+          L0 |= 1u << b;
+          G0 |= 1ull << P.tq[b];
+        }
+      }
+      uint32_t pr[kR];
+#pragma unroll
+      for (int j = 0; j < kR; ++j) pr[j] = swz(1u << st.rbit[j]);
+      const uint32_t p0 = swz(L0);
+      float2 v[kE];
+#pragma unroll
+      for (int e = 0; e < kE; ++e) {
+        uint32_t a = p0;
+#pragma unroll
+        for (int j = 0; j < kR; ++j)
+          if ((e >> j) & 1) a ^= pr[j];
+        v[e] = tile[a];
+      }
+      const int ob = st.op_begin, oe = st.op_begin + st.op_count;
+      for (int o = ob; o < oe; ++o) {
+        const DevOp op = plan.ops[o];
+        if ((G0 & op.cmask) != op.cval) continue;
+        apply_op(v, op, plan.mats);
+      }
+      // Recompute the addresses rather than keeping 32 of them live across the ops.
+      asm volatile("" ::: "memory");
+      {
+        uint32_t L1 = 0;
+        for (int i = 0; i < ng; ++i)
+          if ((tid >> i) & 1) L1 |= 1u << st.nonr[i];
+        uint32_t qr[kR];
+#pragma unroll
+        for (int j = 0; j < kR; ++j) qr[j] = swz(1u << st.rbit[j]);
+        const uint32_t q0 = swz(L1);
+#pragma unroll
+        for (int e = 0; e < kE; ++e) {
+          uint32_t a = q0;
+#pragma unroll
+          for (int j = 0; j < kR; ++j)
+            if ((e >> j) & 1) a ^= qr[j];
+          tile[a] = v[e];
+        }
+      }
+      __syncthreads();
+    }
+
+    // ---- store ----------------------------------------------------------------------
+    {
+      const int iters = (int)(half / nthreads);
+      for (int it = 0; it < iters; ++it) {
+        const uint32_t L = 2u * (tid + it * nthreads);
+        const uint32_t p = swz(L);
+        float4 x = reinterpret_cast<const float4 *>(tile)[p >> 1];
+        if (p & 1u) x = make_float4(x.z, x.w, x.x, x.y);
+        const uint64_t g = base + chunk_off[L >> c] + (L & low_mask);
+        *reinterpret_cast<float4 *>(psi + g) = x;
+      }
+    }
+    __syncthreads();
+  }
+}
+
+int g_tile_blocks_per_sm = 0;
+
+}  // namespace
+
+cudaError_t launch_tile_pass(float2 *psi, int n, const DevPlanView &plan, int pass_index,
+                             const svp::DevPass &hp, cudaStream_t st) {
+  const int m = hp.m;
+  if (m < kR + 1 || m > svp::kMaxTileBits || m - hp.c > 10) return cudaErrorInvalidValue;
+  const size_t smem = sizeof(float2) << m;
+  static bool configured = false;
+  if (!configured) {
+    cudaError_t e = cudaFuncSetAttribute(tile_pass_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)(sizeof(float2) << svp::kMaxTileBits));
+    if (e != cudaSuccess) return e;
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&g_tile_blocks_per_sm, tile_pass_kernel, kThreads,
+                                                      sizeof(float2) << svp::kMaxTileBits);
+    if (e != cudaSuccess) return e;
+    if (g_tile_blocks_per_sm < 1) g_tile_blocks_per_sm = 1;
+    configured = true;
+  }
+  const uint64_t tiles = 1ull << (n - m);
+  const int threads = 1 << (m - kR);
+  uint64_t grid = (uint64_t)device_sm_count() * (uint64_t)g_tile_blocks_per_sm;
+  if (grid > tiles) grid = tiles;
+  tile_pass_kernel<<<(unsigned)grid, threads, smem, st>>>(psi, plan, pass_index, tiles);
+  return cudaGetLastError();
+}
+
+}  // namespace svk

@@ -1,0 +1,60 @@
+// Host-side launchers of the CUDA kernels (implemented in the .cu files).
+#pragma once
+
+#include <cstdint>
+
+#include <cuda_runtime.h>
+
+#include "plan.h"
+
+namespace svk {
+
+struct Mat2 {
+  float v[8];  // a, b, c, d as (re, im)
+};
+
+// Plan as laid out in device memory (one allocation, arrays back to back).
+struct DevPlanView {
+  const svp::DevPass *passes;
+  const svp::DevStage *stages;
+  const svp::DevOp *ops;
+  const float *mats;
+};
+
+// K0: write |0..0> (uniform == false) or the uniform 2^{-n/2} state.  Write-only.
+cudaError_t launch_init(float2 *psi, int n, bool uniform, float amp, cudaStream_t st);
+
+// K1/K2/K3 plain tile pass: one sweep over all tiles of one pass of the plan.
+// host_pass is the host copy of the same pass (tile shape, flags).
+cudaError_t launch_tile_pass(float2 *psi, int n, const DevPlanView &plan, int pass_index,
+                             const svp::DevPass &host_pass, cudaStream_t st);
+
+// K4 fused tensor-core tile pass (tcgen05, split-TF32).
+cudaError_t launch_fused_pass(float2 *psi, int n, const DevPlanView &plan, int pass_index,
+                              const svp::DevPass &host_pass, cudaStream_t st);
+bool fused_supported();
+
+// Per-gate sweeps (K2 one-qubit pair update, K3 diagonal factor on a bit pattern).
+cudaError_t launch_gate_1q(float2 *psi, int n, int q, const Mat2 &u, cudaStream_t st);
+// amplitudes whose bits under mask equal val are multiplied by (fr + i fi)
+cudaError_t launch_gate_diag(float2 *psi, int n, uint64_t mask, uint64_t val, float fr, float fi,
+                             cudaStream_t st);
+
+// K5 reductions.  partials: scratch of at least reduce_partials_needed() doubles*2.
+int reduce_partials_needed();
+cudaError_t launch_norm(const float2 *psi, int n, double *partials, double *out2,
+                        cudaStream_t st);
+// out[2j], out[2j+1] = re, im of psi[bits[j]]
+cudaError_t launch_gather(const float2 *psi, const uint64_t *bits, int64_t m, double *out,
+                          cudaStream_t st);
+// out[j] = |psi[bits[j]]|^2
+cudaError_t launch_gather_prob(const float2 *psi, const uint64_t *bits, int64_t m, double *out,
+                               cudaStream_t st);
+
+// K6: out[2j..2j+1] = scale * sum_l A[xa_j + (l << nA)] * B[xb_j + (l << nB)], fp64.
+cudaError_t launch_branch_sum(const float2 *A, int nA, const float2 *B, int nB, int t, const uint64_t *xa,
+                              const uint64_t *xb, int m, double scale, double *out, cudaStream_t st);
+
+int device_sm_count();
+
+}  // namespace svk

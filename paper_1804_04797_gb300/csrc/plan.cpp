@@ -1,0 +1,368 @@
+// Host planner: gate list -> passes over gathered tiles -> register/fused stages.
+//
+// Dependencies follow from two facts of the gate set (§2): one-qubit gates on
+// different qubits commute, and diagonal gates (T, CZ, Z, projectors) commute with
+// each other -- the property the paper's gate-scheduling preprocessor exploits (§2.3,
+// "utilizes the diagonal properties of gate T and CZ").  A diagonal gate therefore
+// never needs its qubits inside the tile: on a tile the non-tile qubits are fixed, so
+// it becomes a conditional phase.  Only non-diagonal gates need their qubit in the
+// tile, and the planner picks the tile qubits of each pass greedily to apply as many
+// of them as the dependencies allow.
+#include "plan.h"
+
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+
+namespace svp {
+
+void kind_matrix(int kind, double m[8]) {
+  const double r = 1.0 / std::sqrt(2.0);
+  const double c8 = std::cos(M_PI / 4), s8 = std::sin(M_PI / 4);
+  double v[8] = {0, 0, 0, 0, 0, 0, 0, 0};  // a, b, c, d as (re, im)
+  switch (kind) {
+    case K_H: v[0] = r; v[2] = r; v[4] = r; v[6] = -r; break;
+    case K_T: v[0] = 1; v[6] = c8; v[7] = s8; break;
+    case K_TDG: v[0] = 1; v[6] = c8; v[7] = -s8; break;
+    case K_SX: v[0] = .5; v[1] = .5; v[2] = .5; v[3] = -.5; v[4] = .5; v[5] = -.5; v[6] = .5; v[7] = .5; break;
+    case K_SXDG: v[0] = .5; v[1] = -.5; v[2] = .5; v[3] = .5; v[4] = .5; v[5] = .5; v[6] = .5; v[7] = -.5; break;
+    case K_SY: v[0] = .5; v[1] = .5; v[2] = -.5; v[3] = -.5; v[4] = .5; v[5] = .5; v[6] = .5; v[7] = .5; break;
+    case K_SYDG: v[0] = .5; v[1] = -.5; v[2] = .5; v[3] = -.5; v[4] = -.5; v[5] = .5; v[6] = .5; v[7] = -.5; break;
+    case K_Z: v[0] = 1; v[6] = -1; break;
+    case K_P0: v[0] = 1; break;
+    case K_P1: v[6] = 1; break;
+    default: v[0] = 1; v[6] = 1; break;
+  }
+  std::memcpy(m, v, sizeof(v));
+}
+
+namespace {
+
+inline int popc64(uint64_t x) { return __builtin_popcountll(x); }
+
+// Which of the remaining gates a pass with tile qubit set S can apply, in list order.
+// nd_block[q]: an earlier gate on q was deferred (blocks later non-diagonal gates on q).
+// d_block[q]: an earlier NON-diagonal gate on q was deferred (blocks diagonal gates too;
+// deferred diagonal gates commute with later diagonal ones).
+struct Trial {
+  int nondiag = 0, total = 0;
+};
+
+Trial run_trial(const std::vector<Gate> &g, const std::vector<int> &rem, uint64_t S,
+                std::vector<char> *applied) {
+  uint64_t nd_block = 0, d_block = 0;
+  Trial t;
+  if (applied) applied->assign(rem.size(), 0);
+  for (size_t i = 0; i < rem.size(); ++i) {
+    const Gate &x = g[rem[i]];
+    const uint64_t qm = (1ull << x.q0) | (kind_two_qubit(x.kind) ? (1ull << x.q1) : 0ull);
+    if (kind_is_diag(x.kind)) {
+      if (qm & d_block) {
+        nd_block |= qm;
+      } else {
+        ++t.total;
+        if (applied) (*applied)[i] = 1;
+      }
+    } else {
+      if ((qm & S) && !(qm & nd_block)) {
+        ++t.total;
+        ++t.nondiag;
+        if (applied) (*applied)[i] = 1;
+      } else {
+        nd_block |= qm;
+        d_block |= qm;
+      }
+    }
+  }
+  return t;
+}
+
+uint64_t choose_tile(int n, int m, int c, const std::vector<Gate> &g, const std::vector<int> &rem) {
+  uint64_t S = (c >= 64) ? ~0ull : ((1ull << c) - 1);
+  if (m >= n) return (n >= 64) ? ~0ull : ((1ull << n) - 1);
+  // position of the first pending non-diagonal gate of each qubit (tie-breaker)
+  std::vector<int> first(n, 1 << 30);
+  for (size_t i = 0; i < rem.size(); ++i) {
+    const Gate &x = g[rem[i]];
+    if (!kind_is_diag(x.kind) && first[x.q0] == (1 << 30)) first[x.q0] = (int)i;
+  }
+  while (popc64(S) < m) {
+    int best = -1;
+    long long best_score = -1;
+    for (int q = 0; q < n; ++q) {
+      if (S & (1ull << q)) continue;
+      Trial t = run_trial(g, rem, S | (1ull << q), nullptr);
+      long long score = (long long)t.nondiag * (1ll << 40) + (long long)t.total * (1ll << 20) +
+                        ((1 << 20) - 1 - std::min(first[q], (1 << 20) - 1));
+      if (score > best_score) { best_score = score; best = q; }
+    }
+    S |= 1ull << best;
+  }
+  return S;
+}
+
+// Order of residues used by the tile's shared-memory swizzle: local bit p toggles
+// bank-slot bit (p mod 4).  Lane bits with distinct residues make a half-warp's
+// 8-byte accesses conflict-free.
+void order_group_bits(int m, const std::vector<int> &nonr, uint8_t *out) {
+  std::vector<int> lanes, rest;
+  bool used_res[4] = {false, false, false, false};
+  for (int b : nonr) {
+    if ((int)lanes.size() < 4 && !used_res[b & 3]) { used_res[b & 3] = true; lanes.push_back(b); }
+    else rest.push_back(b);
+  }
+  std::vector<int> all = lanes;
+  for (int b : rest) all.push_back(b);
+  (void)m;
+  for (size_t i = 0; i < all.size(); ++i) out[i] = (uint8_t)all[i];
+}
+
+}  // namespace
+
+bool build_plan(int n, const std::vector<Gate> &gates, const Options &opt, bool fresh_state,
+                Plan *plan, const char **err) {
+  Plan &P = *plan;
+  P = Plan();
+  P.n = n;
+  const int m = std::min(opt.m, n);
+  const int c = std::min(opt.c, m);
+  const int r = std::min(opt.r, m);
+  if (m > kMaxTileBits || r > kMaxReg || r < 1 || c < 0) { *err = "bad tile shape"; return false; }
+
+  // leading layer of H on every qubit of a fresh state -> uniform first pass
+  size_t start = 0;
+  if (fresh_state) {
+    uint64_t seen = 0;
+    size_t i = 0;
+    while (i < gates.size() && gates[i].kind == K_H && !(seen & (1ull << gates[i].q0))) {
+      seen |= 1ull << gates[i].q0;
+      ++i;
+      if (popc64(seen) == n) break;
+    }
+    if (popc64(seen) == n) { start = i; P.init_uniform = true; }
+  }
+  for (size_t i = 0; i < start; ++i) { P.order.push_back((int)i); P.pass_of.push_back(0); }
+
+  std::vector<int> rem;
+  for (size_t i = start; i < gates.size(); ++i) rem.push_back((int)i);
+
+  const double amps = std::ldexp(1.0, n);
+  bool first_pass = true;
+  while (!rem.empty() || (first_pass && fresh_state)) {
+    const uint64_t S = choose_tile(n, m, c, gates, rem);
+    std::vector<char> applied;
+    run_trial(gates, rem, S, &applied);
+    std::vector<int> now, later;
+    for (size_t i = 0; i < rem.size(); ++i) (applied[i] ? now : later).push_back(rem[i]);
+
+    DevPass dp;
+    std::memset(&dp, 0, sizeof(dp));
+    dp.m = (uint8_t)m;
+    dp.c = (uint8_t)c;
+    dp.n = (uint8_t)n;
+    int local_of[64];
+    for (int q = 0; q < 64; ++q) local_of[q] = -1;
+    {
+      int li = 0;
+      for (int q = 0; q < c; ++q) { dp.tq[li] = (uint8_t)q; local_of[q] = li++; }
+      for (int q = c; q < n; ++q)
+        if (S & (1ull << q)) { dp.tq[li] = (uint8_t)q; local_of[q] = li++; }
+      int ni = 0;
+      for (int q = 0; q < n; ++q)
+        if (!(S & (1ull << q))) dp.ntq[ni++] = (uint8_t)q;
+      dp.nt = (uint8_t)ni;
+    }
+    if (first_pass && fresh_state) {
+      dp.flags = P.init_uniform ? PF_INIT_UNIFORM : PF_INIT_ZERO;
+      dp.init_amp = P.init_uniform ? (float)std::pow(2.0, -0.5 * n) : 1.0f;
+      P.hbm_bytes += 8.0 * amps;
+    } else {
+      P.hbm_bytes += 16.0 * amps;
+    }
+    dp.stage_begin = (uint16_t)P.stages.size();
+
+    // ---- stages: groups of <= r register bits ------------------------------------
+    std::vector<char> done(now.size(), 0);
+    size_t left = now.size();
+    while (left > 0) {
+      std::vector<int> R;  // tile-local bits
+      uint32_t closed = 0;
+      std::vector<int> inner, post;
+      bool progress = true;
+      while (progress) {
+        progress = false;
+        uint64_t pend_nd = 0, pend_any = 0;  // qubits with an earlier unscheduled gate
+        for (size_t i = 0; i < now.size(); ++i) {
+          const Gate &x = gates[now[i]];
+          const uint64_t qm = (1ull << x.q0) | (kind_two_qubit(x.kind) ? (1ull << x.q1) : 0ull);
+          const bool diag = kind_is_diag(x.kind);
+          if (done[i]) continue;
+          // ready: no earlier unscheduled gate that fails to commute with this one
+          const bool ready = diag ? !(qm & pend_nd) : !(qm & pend_any);
+          bool placed = false;
+          if (ready) {
+            if (!diag) {
+              const int a = local_of[x.q0];
+              const bool inR = std::find(R.begin(), R.end(), a) != R.end();
+              if (!(closed & (1u << a)) && (inR || (int)R.size() < r)) {
+                if (!inR) R.push_back(a);
+                inner.push_back(now[i]);
+                placed = true;
+              }
+            } else {
+              bool all_in = true;
+              uint32_t locals = 0;
+              const int qs[2] = {x.q0, x.q1};
+              for (int t = 0; t < (kind_two_qubit(x.kind) ? 2 : 1); ++t) {
+                const int a = local_of[qs[t]];
+                if (a < 0) { all_in = false; continue; }
+                locals |= 1u << a;
+                if (std::find(R.begin(), R.end(), a) == R.end()) all_in = false;
+              }
+              if (all_in) inner.push_back(now[i]);
+              else { post.push_back(now[i]); closed |= locals; }
+              placed = true;
+            }
+          }
+          if (placed) {
+            done[i] = 1;
+            --left;
+            progress = true;
+          } else {
+            pend_any |= qm;
+            if (!diag) pend_nd |= qm;
+          }
+        }
+      }
+      // device stage
+      DevStage ds;
+      std::memset(&ds, 0, sizeof(ds));
+      ds.r = (uint8_t)R.size();
+      std::vector<int> rb = R;
+      for (int b = 0; (int)rb.size() < r && b < m; ++b)
+        if (std::find(rb.begin(), rb.end(), b) == rb.end()) rb.push_back(b);
+      for (int j = 0; j < r; ++j) ds.rbit[j] = (uint8_t)rb[j];
+      std::vector<int> nonr;
+      for (int b = 0; b < m; ++b)
+        if (std::find(rb.begin(), rb.end(), b) == rb.end()) nonr.push_back(b);
+      order_group_bits(m, nonr, ds.nonr);
+      ds.op_begin = (uint16_t)P.ops.size();
+      ds.diag_only = inner.empty() ? 1 : 0;
+      auto reg_of = [&](int q) -> int {
+        const int a = local_of[q];
+        if (a < 0) return -1;
+        for (int j = 0; j < r; ++j)
+          if (rb[j] == a) return j;
+        return -1;
+      };
+      auto emit = [&](uint8_t act, int j, int k, int arg, uint64_t cm, uint64_t cv) {
+        DevOp o;
+        std::memset(&o, 0, sizeof(o));
+        o.act = act; o.j = (uint8_t)(j < 0 ? 0 : j); o.k = (uint8_t)(k < 0 ? 0 : k);
+        o.arg = (uint8_t)arg; o.cmask = cm; o.cval = cv;
+        P.ops.push_back(o);
+      };
+      auto lower = [&](int gi) {
+        const Gate &x = gates[gi];
+        const int j = reg_of(x.q0);
+        const int k = kind_two_qubit(x.kind) ? reg_of(x.q1) : -1;
+        const uint64_t b0 = 1ull << x.q0, b1 = 1ull << x.q1;
+        switch (x.kind) {
+          case K_H: emit(A_H, j, 0, 0, 0, 0); break;
+          case K_SX: emit(A_SX, j, 0, 0, 0, 0); break;
+          case K_SY: emit(A_SY, j, 0, 0, 0, 0); break;
+          case K_SXDG: emit(A_SXDG, j, 0, 0, 0, 0); break;
+          case K_SYDG: emit(A_SYDG, j, 0, 0, 0, 0); break;
+          case K_T: if (j >= 0) emit(A_T, j, 0, 0, 0, 0); else emit(A_PHASE, 0, 0, 1, b0, b0); break;
+          case K_TDG: if (j >= 0) emit(A_TDG, j, 0, 0, 0, 0); else emit(A_PHASE, 0, 0, 7, b0, b0); break;
+          case K_Z: if (j >= 0) emit(A_Z, j, 0, 0, 0, 0); else emit(A_PHASE, 0, 0, 4, b0, b0); break;
+          case K_P0: if (j >= 0) emit(A_P0, j, 0, 0, 0, 0); else emit(A_ZERO, 0, 0, 0, b0, b0); break;
+          case K_P1: if (j >= 0) emit(A_P1, j, 0, 0, 0, 0); else emit(A_ZERO, 0, 0, 0, b0, 0); break;
+          case K_CZ:
+            if (j >= 0 && k >= 0) emit(A_CZ, j, k, 0, 0, 0);
+            else if (j >= 0) emit(A_Z, j, 0, 0, b1, b1);
+            else if (k >= 0) emit(A_Z, k, 0, 0, b0, b0);
+            else emit(A_PHASE, 0, 0, 4, b0 | b1, b0 | b1);
+            break;
+          case K_PEQ:
+            if (j >= 0 && k >= 0) emit(A_PEQ, j, k, 0, 0, 0);
+            else if (j >= 0) { emit(A_P0, j, 0, 0, b1, 0); emit(A_P1, j, 0, 0, b1, b1); }
+            else if (k >= 0) { emit(A_P0, k, 0, 0, b0, 0); emit(A_P1, k, 0, 0, b0, b0); }
+            else { emit(A_ZERO, 0, 0, 0, b0 | b1, b0); emit(A_ZERO, 0, 0, 0, b0 | b1, b1); }
+            break;
+          default: break;
+        }
+      };
+      if (!opt.fused)
+        for (int gi : inner) lower(gi);
+      for (int gi : post) lower(gi);
+      ds.op_count = (uint16_t)(P.ops.size() - ds.op_begin);
+      P.stages.push_back(ds);
+      P.stage_gates.push_back(inner);
+      P.stage_post.push_back(post);
+      const int pass_index = (int)P.passes.size();
+      for (int gi : inner) { P.order.push_back(gi); P.pass_of.push_back(pass_index); }
+      for (int gi : post) { P.order.push_back(gi); P.pass_of.push_back(pass_index); }
+    }
+    dp.stage_count = (uint16_t)(P.stages.size() - dp.stage_begin);
+    P.passes.push_back(dp);
+    rem.swap(later);
+    first_pass = false;
+    if (P.passes.size() > 100000) { *err = "planner did not converge"; return false; }
+  }
+  if (P.ops.size() > 65535 || P.stages.size() > 65535) { *err = "plan too large"; return false; }
+  return true;
+}
+
+void stage_unitary(const Plan &P, const std::vector<Gate> &gates, int stage, int r,
+                   std::vector<double> *u) {
+  const DevStage &ds = P.stages[stage];
+  const DevPass *pass = nullptr;
+  for (const DevPass &p : P.passes)
+    if (stage >= p.stage_begin && stage < p.stage_begin + p.stage_count) pass = &p;
+  const int d = 1 << r;
+  u->assign((size_t)2 * d * d, 0.0);
+  for (int i = 0; i < d; ++i) (*u)[2 * ((size_t)i * d + i)] = 1.0;
+  int local_of[64];
+  for (int q = 0; q < 64; ++q) local_of[q] = -1;
+  for (int i = 0; pass && i < pass->m; ++i) local_of[pass->tq[i]] = i;
+  auto reg_of = [&](int q) {
+    for (int j = 0; j < r; ++j)
+      if (local_of[q] >= 0 && ds.rbit[j] == local_of[q]) return j;
+    return -1;
+  };
+  for (int gi : P.stage_gates[stage]) {
+    const Gate &x = gates[gi];
+    if (kind_two_qubit(x.kind)) {
+      const int j = reg_of(x.q0), k = reg_of(x.q1);
+      for (int row = 0; row < d; ++row) {
+        const bool bj = (row >> j) & 1, bk = (row >> k) & 1;
+        double s = 1.0;
+        if (x.kind == K_CZ && bj && bk) s = -1.0;
+        if (x.kind == K_PEQ && bj != bk) s = 0.0;
+        for (int col = 0; col < d; ++col) {
+          (*u)[2 * ((size_t)row * d + col)] *= s;
+          (*u)[2 * ((size_t)row * d + col) + 1] *= s;
+        }
+      }
+      continue;
+    }
+    double mm[8];
+    kind_matrix(x.kind, mm);
+    const int j = reg_of(x.q0);
+    for (int col = 0; col < d; ++col) {
+      for (int row = 0; row < d; ++row) {
+        if ((row >> j) & 1) continue;
+        const int r1 = row | (1 << j);
+        const double xr = (*u)[2 * ((size_t)row * d + col)], xi = (*u)[2 * ((size_t)row * d + col) + 1];
+        const double yr = (*u)[2 * ((size_t)r1 * d + col)], yi = (*u)[2 * ((size_t)r1 * d + col) + 1];
+        (*u)[2 * ((size_t)row * d + col)] = mm[0] * xr - mm[1] * xi + mm[2] * yr - mm[3] * yi;
+        (*u)[2 * ((size_t)row * d + col) + 1] = mm[0] * xi + mm[1] * xr + mm[2] * yi + mm[3] * yr;
+        (*u)[2 * ((size_t)r1 * d + col)] = mm[4] * xr - mm[5] * xi + mm[6] * yr - mm[7] * yi;
+        (*u)[2 * ((size_t)r1 * d + col) + 1] = mm[4] * xi + mm[5] * xr + mm[6] * yi + mm[7] * yr;
+      }
+    }
+  }
+}
+
+}  // namespace svp

@@ -1,0 +1,125 @@
+// Internal plan format shared by the host planner and the CUDA kernels.
+//
+// A plan turns a gate list into PASSES.  Each pass is one sweep of the state in HBM:
+// the state is cut into 2^m-amplitude gathered TILES -- the amplitudes whose indices
+// differ only in the m tile qubits (the c lowest qubits, for coalesced access, plus
+// m-c chosen high qubits).  This is the paper's idea of "local qubits" (§2.3: keep a
+// block of amplitudes on-chip and apply every gate that acts inside it), with the tile
+// qubits chosen anew for every pass instead of fixed low ranks plus rank swaps.
+// Inside a pass the gates are grouped into STAGES of at most r "register" qubits: the
+// plain kernel holds 2^r amplitudes per thread and applies the stage's gates in
+// registers; the tensor-core kernel multiplies them into one 2^r x 2^r unitary.
+#pragma once
+
+#include <cstdint>
+#include <vector>
+
+namespace svp {
+
+// Gate kinds (same codes as sv_kind) plus the internal branch projector.
+enum Kind : uint8_t {
+  K_H = 0, K_T = 1, K_SX = 2, K_SY = 3, K_CZ = 4, K_P0 = 5, K_P1 = 6, K_Z = 7,
+  K_TDG = 8, K_SXDG = 9, K_SYDG = 10,
+  K_PEQ = 11,  // zero the amplitudes whose bits q0 and q1 differ (branch projector)
+  K_COUNT = 12
+};
+
+inline bool kind_is_diag(int k) {
+  return k == K_T || k == K_CZ || k == K_P0 || k == K_P1 || k == K_Z || k == K_TDG ||
+         k == K_PEQ;
+}
+inline bool kind_two_qubit(int k) { return k == K_CZ || k == K_PEQ; }
+
+struct Gate {
+  uint8_t kind, q0, q1;
+};
+
+// Actions of a device op on a thread's register group (2^r amplitudes, element e has
+// register bit j = bit j of e).
+enum Act : uint8_t {
+  A_U = 0,      // general 2x2 (matrix slot `arg`) on register bit j
+  A_H, A_SX, A_SY, A_SXDG, A_SYDG,  // fixed one-qubit gates on register bit j
+  A_T, A_TDG, A_Z, A_P0, A_P1,      // diagonal on register bit j
+  A_CZ,         // -1 where register bits j and k are both 1
+  A_PEQ,        // 0 where register bits j and k differ
+  A_PHASE,      // every element times w^arg, w = e^{i pi/4}
+  A_ZERO,       // every element set to 0
+  A_COUNT
+};
+
+// One device op.  It acts only where (G0 & cmask) == cval, G0 being the global index
+// of the group's element 0 (all register bits zero): conditions on qubits that are not
+// register bits of the stage (the other tile qubits and the tile's fixed qubits).
+struct DevOp {
+  uint8_t act, j, k, arg;
+  uint32_t pad;
+  uint64_t cmask, cval;
+};
+static_assert(sizeof(DevOp) == 24, "DevOp layout");
+
+constexpr int kMaxTileBits = 13;
+constexpr int kMaxReg = 5;
+
+struct DevStage {
+  uint8_t r;              // register bits in use (<= kMaxReg); the rest are padding
+  uint8_t rbit[kMaxReg];  // tile-local bit of register bit j (all distinct, padded)
+  uint8_t nonr[kMaxTileBits];  // tile-local bits of the group index, lane bits first
+  uint8_t pad0;
+  uint16_t op_begin, op_count;   // into the plan's op array
+  uint32_t mat_begin;            // fused path: offset of this stage's unitary (floats)
+  uint8_t diag_only, pad1[3];
+};
+
+enum PassFlags : uint8_t {
+  PF_INIT_UNIFORM = 1,  // tile content is 2^{-n/2} everywhere; nothing is read
+  PF_INIT_ZERO = 2,     // tile content is |0..0>; nothing is read
+};
+
+struct DevPass {
+  uint8_t m, c, flags, n;
+  uint8_t tq[kMaxTileBits];   // tile-local bit -> global qubit (tq[i] = i for i < c)
+  uint8_t nt;                 // number of non-tile qubits (n - m)
+  uint8_t ntq[64];            // non-tile qubits, ascending (tile index bit -> qubit)
+  uint16_t stage_begin, stage_count;
+  uint32_t pad;
+  float init_amp;             // uniform amplitude for PF_INIT_UNIFORM
+  float pad2;
+};
+
+struct Options {
+  int m = 13;        // tile qubits
+  int c = 4;         // contiguous low qubits in every tile
+  int r = 5;         // register qubits per stage
+  bool fused = false;
+};
+
+struct Plan {
+  int n = 0;
+  std::vector<DevPass> passes;
+  std::vector<DevStage> stages;
+  std::vector<DevOp> ops;
+  std::vector<float> mats;          // 8 floats per A_U matrix (re/im of a,b,c,d)
+  std::vector<int32_t> order;       // executed gate index, in execution order
+  std::vector<int32_t> pass_of;     // pass of each executed gate
+  std::vector<std::vector<int>> stage_gates;  // per stage: gate indices (inner, in order)
+  std::vector<std::vector<int>> stage_post;   // per stage: diagonal gates applied after
+  bool init_uniform = false;
+  double hbm_bytes = 0;
+};
+
+// Build the plan.  fresh_state: the state is |0..0> and was never written, so a
+// leading layer of H on every qubit may become the uniform initial tile, and a plan
+// without that layer starts from |0..0> generated in the first pass.  Gates must be
+// validated by the caller.  Returns false with *err set on failure.
+bool build_plan(int n, const std::vector<Gate> &gates, const Options &opt, bool fresh_state,
+                Plan *plan, const char **err);
+
+// Matrix (re/im of a, b, c, d) of a one-qubit kind, in double precision.
+void kind_matrix(int kind, double m[8]);
+
+// The unitary of a stage's inner ops on its r register bits: 2^r x 2^r complex
+// (row-major, re/im interleaved; row/column bit j = register bit j), in double precision.
+void stage_unitary(const Plan &plan, const std::vector<Gate> &gates, int stage, int r,
+                   std::vector<double> *u);
+
+}  // namespace svp

@@ -1,0 +1,50 @@
+// The state handle behind the opaque sv_state, and helpers shared by the C-ABI files.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <vector>
+
+#include "../../include/sv.h"
+#include "kernels.h"
+#include "plan.h"
+
+struct sv_state {
+  int n = 0;
+  float2 *psi = nullptr;  // 2^n complex64 amplitudes on the device
+  bool owns = false;      // allocated by sv_create (freed by sv_destroy)
+  sv_options opts{};
+  cudaStream_t stream = nullptr;
+  int device = 0;
+  bool fresh = false;     // logically |0..0> but not yet written (lazy initial state)
+  bool broken = false;    // an apply failed part-way: content undefined
+  // device scratch: packed plan, gather/reduction buffers
+  void *d_plan = nullptr;
+  size_t d_plan_cap = 0;
+  std::vector<char> h_plan;
+  void *d_scratch = nullptr;
+  size_t d_scratch_cap = 0;
+  // profiling: event pairs around each pass launch
+  bool prof = false;
+  std::vector<cudaEvent_t> events;
+  size_t ev_used = 0;
+  std::vector<double> ev_bytes;
+  double h2d = 0, d2h = 0;
+  int other_launches = 0;
+};
+
+namespace svc {
+
+sv_status cuda_fail(cudaError_t e, const char *what);
+sv_status ensure_device_buffer(void **buf, size_t *cap, size_t need);
+svp::Options plan_options(const sv_options &o);
+sv_status check_options(const sv_options &o);
+sv_status convert_gates(int n, const sv_gate *g, size_t count, bool inverse, std::vector<svp::Gate> *out);
+sv_status upload_plan(sv_state *s, const svp::Plan &P, svk::DevPlanView *view);
+sv_status run_plan(sv_state *s, const svp::Plan &P, const svk::DevPlanView &view);
+// Plan and run an internal gate list (kinds may include K_PEQ) on the state.
+sv_status apply_gates(sv_state *s, const std::vector<svp::Gate> &g);
+// Fused path: the stage unitaries as split-TF32 operands (see k_fused.cu).
+sv_status build_stage_mats(svp::Plan *P, const std::vector<svp::Gate> &g, int r);
+
+}  // namespace svc

@@ -1,0 +1,252 @@
+"""GPU parity: the CUDA library (through its C interface) against the complex128 CPU
+oracle on the same seeded circuits.
+
+Bar (floating point): relative L2 error of the complex64 state <= 1e-5 and
+|norm^2 - 1| <= 1e-6 (fp64 reduction) -- the tolerance the target sets for complex64
+against an fp64 oracle.  Amplitude-level values that the method fixes exactly (uniform
+layer 0, zeros of projectors) are compared at fp32 rounding.
+"""
+import numpy as np
+import pytest
+
+from oracle import circuit as oc
+from oracle import csim
+from oracle import statevec as ov
+from paper_1804_04797_gb300 import inputs
+from paper_1804_04797_gb300 import sv
+
+pytestmark = pytest.mark.gpu
+
+REL_L2 = 1e-5
+NORM_TOL = 1e-6
+
+
+def rel_l2(a, b):
+    a = np.asarray(a, dtype=np.complex128)
+    b = np.asarray(b, dtype=np.complex128)
+    return float(np.linalg.norm(a - b) / np.linalg.norm(b))
+
+
+def oracle_gates(lat):
+    return oc.generate(lat.rows, lat.cols, lat.removed_mask, lat.depth, lat.seed)
+
+
+def run_gpu(lat, **kw):
+    g = sv.sv_generate_circuit(lat)
+    h = sv.sv_create(lat.n_qubits, sv.options(**kw))
+    try:
+        sv.sv_apply_circuit(h, g)
+        psi = sv.sv_copy_state(h, lat.n_qubits)
+        norm2, sp2 = sv.sv_norm(h)
+    finally:
+        sv.sv_destroy(h)
+    return psi, norm2, sp2
+
+
+MODES = [dict(), dict(tile_bits=10, low_bits=4, fuse_k=5), dict(tile_bits=8, low_bits=2, fuse_k=3),
+         dict(tile_bits=12, low_bits=5, fuse_k=4), dict(precision=sv.SV_PREC_PERGATE)]
+
+
+@pytest.mark.parametrize('kw', MODES)
+def test_16q_depth10_matches_oracle(kw):
+    lat = inputs.C16
+    n, gates = oracle_gates(lat)
+    want = csim.run(n, gates)
+    psi, norm2, sp2 = run_gpu(lat, **kw)
+    assert rel_l2(psi, want) <= REL_L2
+    assert abs(norm2 - 1) <= NORM_TOL
+    assert abs(sp2 - ov.sum_p2(want)) <= 1e-6 * ov.sum_p2(want) + 1e-12
+
+
+SIZES = [inputs.lattice_for(2, 3, 8, seed=4),            # 6 qubits: one tile = the state
+         inputs.lattice_for(3, 3, 12, seed=2),           # 9
+         inputs.lattice_for(3, 5, 16, seed=7, removed=[(1, 2)]),   # 14, removed site
+         inputs.lattice_for(4, 5, 18, seed=11),          # 20: 128 tiles of 2^13
+         inputs.lattice_for(4, 6, 24, seed=13),          # 24
+         inputs.lattice_for(1, 3, 6, seed=1),            # 3 qubits (per-gate path)
+         inputs.lattice_for(1, 1, 0, seed=0)]            # 1 qubit, H only
+
+
+@pytest.mark.parametrize('lat', SIZES, ids=lambda l: '%dx%d_d%d' % (l.rows, l.cols, l.depth))
+def test_sizes_match_oracle(lat):
+    n, gates = oracle_gates(lat)
+    want = csim.run(n, gates)
+    for kw in (dict(), dict(tile_bits=min(13, max(6, n)), low_bits=min(4, n), fuse_k=5)):
+        psi, norm2, _ = run_gpu(lat, **kw)
+        assert rel_l2(psi, want) <= REL_L2, kw
+        assert abs(norm2 - 1) <= NORM_TOL
+
+
+def test_layer0_only_is_uniform():
+    lat = inputs.lattice_for(4, 5, 0)
+    psi, norm2, _ = run_gpu(lat)
+    np.testing.assert_allclose(psi, np.full(1 << 20, 2.0 ** -10), rtol=0, atol=0)
+    assert abs(norm2 - 1) < 1e-12
+
+
+def _random_gate_list(n, count, seed):
+    """Every kind of the interface, random qubits, no leading H layer."""
+    rng = np.random.default_rng(seed)
+    out = []
+    kinds = ['H', 'T', 'SX', 'SY', 'CZ', 'Z', 'TDG', 'SXDG', 'SYDG']
+    for _ in range(count):
+        k = kinds[rng.integers(len(kinds))]
+        a = int(rng.integers(n))
+        if k == 'CZ':
+            b = int(rng.integers(n - 1))
+            b = b + 1 if b >= a else b
+            out.append((k, a, b))
+        else:
+            out.append((k, a, -1))
+    return out
+
+
+_CODE = dict(oc.KIND_CODE, TDG=8, SXDG=9, SYDG=10)
+
+
+def _to_lib(gl):
+    return sv.gates_from_tuples([(_CODE[k], a, max(b, 0), 1) for (k, a, b) in gl])
+
+
+def _oracle_apply(n, gl, psi):
+    psi = np.array(psi, dtype=np.complex128)
+    for k, a, b in gl:
+        if k == 'CZ':
+            ov.apply_cz(psi, a, b)
+        elif k.endswith('DG'):
+            ov.apply_1q(psi, ov.gate_matrix(k[:-2]).conj().T, a)
+        else:
+            ov.apply_1q(psi, ov.gate_matrix(k), a)
+    return psi
+
+
+@pytest.mark.parametrize('n,kw', [(7, {}), (13, {}), (18, {}), (18, dict(tile_bits=9, low_bits=3, fuse_k=2)),
+                                  (16, dict(precision=sv.SV_PREC_PERGATE))])
+def test_all_gate_kinds_from_zero_and_loaded_state(n, kw):
+    gl = _random_gate_list(n, 120, seed=n)
+    # from |0..0> (no H layer: the first pass generates |0..0>)
+    want = _oracle_apply(n, gl, ov.zero_state(n))
+    h = sv.sv_create(n, sv.options(**kw))
+    try:
+        sv.sv_apply_circuit(h, _to_lib(gl))
+        assert rel_l2(sv.sv_copy_state(h, n), want) <= REL_L2
+        # from a loaded random state (not fresh: the first pass reads it)
+        rng = np.random.default_rng(3)
+        start = (rng.normal(size=1 << n) + 1j * rng.normal(size=1 << n)).astype(np.complex64)
+        start /= np.linalg.norm(start)
+        sv.sv_load_state(h, start)
+        sv.sv_apply_circuit(h, _to_lib(gl))
+        want2 = _oracle_apply(n, gl, start.astype(np.complex128))
+        assert rel_l2(sv.sv_copy_state(h, n), want2) <= REL_L2
+    finally:
+        sv.sv_destroy(h)
+
+
+def test_projectors_zero_exactly():
+    n = 12
+    gl = [('H', q, -1) for q in range(n)] + [('SX', 3, -1), ('CZ', 3, 9, -1)]
+    codes = sv.gates_from_tuples([(_CODE[k], a, max(b, 0), 0) for (k, a, b, *_r) in gl] +
+                                 [(5, 3, 0, 1), (6, 9, 0, 1), (5, 0, 0, 1)])
+    h = sv.sv_create(n)
+    try:
+        sv.sv_apply_circuit(h, codes)
+        psi = sv.sv_copy_state(h, n)
+    finally:
+        sv.sv_destroy(h)
+    idx = np.arange(1 << n)
+    dead = (((idx >> 3) & 1) == 1) | (((idx >> 9) & 1) == 0) | (((idx >> 0) & 1) == 1)
+    assert np.all(psi[dead] == 0)
+    assert np.count_nonzero(psi[~dead]) == np.count_nonzero(~dead)
+
+
+def test_inverse_circuit_returns_to_zero_state():
+    lat = inputs.lattice_for(4, 5, 16, seed=21)
+    g = sv.sv_generate_circuit(lat)
+    h = sv.sv_create(20)
+    try:
+        sv.sv_apply_circuit(h, g)
+        sv.sv_apply_circuit_inverse(h, g)
+        psi = sv.sv_copy_state(h, 20)
+    finally:
+        sv.sv_destroy(h)
+    e0 = np.zeros(1 << 20, dtype=np.complex128)
+    e0[0] = 1
+    assert rel_l2(psi, e0) <= 1e-5
+
+
+def test_amplitudes_and_probabilities_gather():
+    lat = inputs.lattice_for(4, 5, 14, seed=5)
+    n, gates = oracle_gates(lat)
+    want = csim.run(n, gates)
+    bits = inputs.bitstrings(n, 64, seed=2) + [0, (1 << n) - 1]
+    h = sv.sv_create(n)
+    try:
+        sv.sv_apply_circuit(h, sv.sv_generate_circuit(lat))
+        amps = sv.sv_get_amplitudes(h, bits)
+        probs = sv.sv_get_probabilities(h, bits)
+        with pytest.raises(sv.SvError):
+            sv.sv_get_amplitudes(h, [1 << n])
+    finally:
+        sv.sv_destroy(h)
+    sel = want[np.array(bits, dtype=np.int64)]
+    assert rel_l2(amps, sel) <= REL_L2
+    np.testing.assert_allclose(probs, np.abs(amps) ** 2, rtol=1e-12, atol=0)
+
+
+def test_invalid_arguments_leave_state_usable():
+    h = sv.sv_create(10)
+    try:
+        with pytest.raises(sv.SvError):
+            sv.sv_apply_circuit(h, sv.gates_from_tuples([(4, 2, 2, 1)]))
+        with pytest.raises(sv.SvError):
+            sv.sv_apply_circuit(h, sv.gates_from_tuples([(1, 10, 0, 1)]))
+        sv.sv_apply_circuit(h, sv.gates_from_tuples([(0, q, 0, 0) for q in range(10)]))
+        n2, _ = sv.sv_norm(h)
+        assert abs(n2 - 1) < 1e-6
+    finally:
+        sv.sv_destroy(h)
+    with pytest.raises(sv.SvError):
+        sv.sv_create(35)
+    with pytest.raises(sv.SvError):
+        sv.sv_create(0)
+
+
+def test_branch_amplitudes_small_cut_match_oracle():
+    lat = inputs.lattice_for(4, 4, 9, seed=31)
+    half_a = (1 << 8) - 1
+    n, gates = oracle_gates(lat)
+    bits = inputs.bitstrings(n, 64, seed=2)
+    want_full = csim.run(n, gates)[np.array(bits, dtype=np.int64)]
+    want_branch = csim.branch_amplitudes(n, gates, half_a, bits)
+    got = sv.sv_branch_amplitudes(lat, half_a, bits)
+    assert rel_l2(want_branch, want_full) < 1e-12
+    assert rel_l2(got, want_full) <= REL_L2
+
+
+def test_branch_amplitudes_28q_check_against_full_state():
+    """4x7 depth 10 cut 1|2 (t = 7): branch sum == a full 28-qubit GPU state, and both
+    == the oracle's branch sum."""
+    lat = inputs.C28
+    n, gates = oracle_gates(lat)
+    bits = inputs.bitstrings(n, 64, seed=2)
+    got = sv.sv_branch_amplitudes(lat, inputs.C28_HALF_A, bits)
+    h = sv.sv_create(n)
+    try:
+        sv.sv_apply_circuit(h, sv.sv_generate_circuit(lat))
+        full = sv.sv_get_amplitudes(h, bits)
+    finally:
+        sv.sv_destroy(h)
+    want = csim.branch_amplitudes(n, gates, inputs.C28_HALF_A, bits)
+    assert rel_l2(got, want) <= REL_L2
+    assert rel_l2(full, want) <= REL_L2
+
+
+def test_batch_stats_match_oracle():
+    lats = inputs.batch(6)
+    stats = sv.sv_apply_batch(lats)
+    for lat, row in zip(lats, stats):
+        n, gates = oracle_gates(lat)
+        s2, s4 = csim.reductions(csim.run(n, gates))
+        assert row[2] == n
+        assert abs(row[0] - 1) <= NORM_TOL
+        assert abs(row[1] - s4) <= 1e-5 * s4

@@ -1,0 +1,124 @@
+"""Host-side checks of the CUDA library (no GPU needed): the shared library loads and
+exports every function declared in include/sv.h, the generator matches the oracle's
+independent generator bit for bit, and the planner's execution order is a valid
+reordering of the circuit (checked by running both orders through the CPU oracle)."""
+import os
+import re
+
+import numpy as np
+import pytest
+
+from oracle import circuit as oc
+from oracle import statevec as ov
+from paper_1804_04797_gb300 import inputs
+from paper_1804_04797_gb300 import sv
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _declared_functions():
+    names = set()
+    for fn in os.listdir(os.path.join(ROOT, 'include')):
+        if fn.endswith('.h'):
+            text = open(os.path.join(ROOT, 'include', fn)).read()
+            text = re.sub(r'/\*.*?\*/', '', text, flags=re.S)
+            names |= set(re.findall(r'\b(sv_[a-z0-9_]+)\s*\(', text))
+    return names
+
+
+def test_library_exports_every_declared_function():
+    import ctypes
+    L = ctypes.CDLL(sv.lib()._name)
+    names = _declared_functions()
+    assert len(names) >= 15
+    missing = [n for n in sorted(names) if not hasattr(L, n)]
+    assert not missing, missing
+
+
+def _lib_gates(lat):
+    g = sv.sv_generate_circuit(lat)
+    out = []
+    for x in g:
+        k = oc.CODE_KIND[int(x['kind'])]
+        out.append((k, int(x['q0']), int(x['q1']) if k == 'CZ' else -1, int(x['layer'])))
+    return out
+
+
+LATTICES = [inputs.C16, inputs.C30, inputs.C34, inputs.C42, inputs.C28,
+            inputs.lattice_for(3, 5, 17, seed=99), inputs.lattice_for(1, 7, 9, seed=5),
+            inputs.lattice_for(5, 5, 40, seed=12345, removed=[(2, 2), (0, 4)])]
+
+
+@pytest.mark.parametrize('lat', LATTICES)
+def test_generator_matches_oracle_generator(lat):
+    n_o, g_o = oc.generate(lat.rows, lat.cols, lat.removed_mask, lat.depth, lat.seed)
+    assert n_o == lat.n_qubits
+    assert _lib_gates(lat) == g_o
+
+
+def test_generator_batch_lattices():
+    for lat in inputs.batch(64):
+        n_o, g_o = oc.generate(lat.rows, lat.cols, lat.removed_mask, lat.depth, lat.seed)
+        assert 16 <= n_o <= 24 and 10 <= lat.depth <= 24
+        assert _lib_gates(lat) == g_o
+
+
+def test_generator_rejects_bad_lattices():
+    with pytest.raises(sv.SvError):
+        sv.sv_generate_circuit(sv.sv_lattice(9, 8, 0, 3, 0))       # 72 sites
+    with pytest.raises(sv.SvError):
+        sv.sv_generate_circuit(sv.sv_lattice(2, 2, 0xF, 3, 0))     # every site removed
+
+
+def _oracle_run_order(n, gates, order):
+    return ov.run(n, [gates[i] for i in order])
+
+
+PLAN_CASES = [(inputs.lattice_for(3, 4, 14, seed=3), dict()),
+              (inputs.lattice_for(3, 4, 14, seed=3), dict(tile_bits=8, low_bits=2, fuse_k=3)),
+              (inputs.lattice_for(4, 4, 12, seed=8), dict(tile_bits=10, low_bits=4, fuse_k=5)),
+              (inputs.lattice_for(4, 4, 12, seed=8), dict(tile_bits=7, low_bits=1, fuse_k=2)),
+              (inputs.lattice_for(2, 7, 20, seed=1), dict(tile_bits=9, low_bits=3, fuse_k=4)),
+              (inputs.lattice_for(4, 4, 12, seed=8), dict(tile_bits=8, low_bits=4, fuse_k=5,
+                                                          precision=sv.SV_PREC_TF32X3))]
+
+
+@pytest.mark.parametrize('lat,kw', PLAN_CASES)
+def test_planner_order_is_a_valid_reordering(lat, kw):
+    gates = _lib_gates(lat)
+    n = lat.n_qubits
+    g = sv.sv_generate_circuit(lat)
+    summ, order, pass_of, tiles = sv.sv_plan(n, g, sv.options(**kw), fresh_state=True)
+    assert sorted(order.tolist()) == list(range(len(gates)))
+    assert summ.init_uniform == 1
+    # every non-diagonal gate of a pass acts on a tile qubit of that pass
+    for i, p in zip(order.tolist(), pass_of.tolist()):
+        k, a, _b, _l = gates[i]
+        if k in ('SX', 'SY', 'H') and gates[i][3] > 0:
+            assert a in set(tiles[p][tiles[p] >= 0].tolist())
+    want = ov.run(n, gates)
+    got = _oracle_run_order(n, gates, order.tolist())
+    np.testing.assert_allclose(got, want, atol=1e-12)
+
+
+def test_planner_pass_counts_headline_workload():
+    """The 34-qubit depth-30 circuit needs far fewer state sweeps than gates."""
+    g = sv.sv_generate_circuit(inputs.C34)
+    summ, *_ = sv.sv_plan(34, g, sv.options(), fresh_state=True)
+    assert len(g) == 478
+    assert summ.passes <= 12
+    assert summ.hbm_bytes == pytest.approx(8.0 * 2 ** 34 + 16.0 * 2 ** 34 * (summ.passes - 1))
+
+
+def test_planner_rejects_invalid_gates():
+    bad = sv.gates_from_tuples([(4, 3, 3, 1)])  # CZ on one qubit
+    with pytest.raises(sv.SvError):
+        sv.sv_plan(8, bad)
+    bad = sv.gates_from_tuples([(2, 9, 0, 1)])  # qubit out of range
+    with pytest.raises(sv.SvError):
+        sv.sv_plan(8, bad)
+    bad = sv.gates_from_tuples([(42, 1, 0, 1)])  # unknown kind
+    with pytest.raises(sv.SvError):
+        sv.sv_plan(8, bad)
+    with pytest.raises(sv.SvError):
+        sv.sv_plan(8, sv.gates_from_tuples([(0, 1, 0, 0)]), sv.options(tile_bits=14))
