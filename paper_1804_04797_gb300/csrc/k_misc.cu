@@ -2,6 +2,8 @@
 // diagonal factor), fp64 reductions and gathers (K5).
 #include <cuda_runtime.h>
 
+#include <cmath>
+
 #include "kernels.h"
 
 namespace svk {
@@ -23,10 +25,6 @@ __global__ void init_kernel(float4 *psi4, uint64_t n4, float a, bool zero_state)
     if (zero_state) psi4[i] = make_float4(i == 0 ? 1.f : 0.f, 0.f, 0.f, 0.f);
     else psi4[i] = make_float4(a, 0.f, a, 0.f);
   }
-}
-
-__global__ void init_one_kernel(float2 *psi, float a, bool zero_state) {
-  psi[0] = make_float2(zero_state ? 1.f : a, 0.f);
 }
 
 // Pair update of §2 on qubit q >= 1: each thread takes the two adjacent pairs
@@ -82,14 +80,17 @@ __device__ __forceinline__ uint64_t deposit_skip(uint64_t t, uint64_t mask) {
   return out;
 }
 
-// Diagonal factor on the amplitudes whose bits under mask equal val.
+// Diagonal factor (fr + fr_lo) + i (fi + fi_lo) on the amplitudes whose bits under mask
+// equal val; the lo parts carry what fp32 cannot hold of 1/sqrt2 (unbiased rounding).
 __global__ void diag_kernel(float2 *psi, uint64_t items, uint64_t mask, uint64_t val, float fr,
-                            float fi) {
+                            float fi, float fr_lo, float fi_lo) {
   for (uint64_t p = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; p < items;
        p += (uint64_t)gridDim.x * blockDim.x) {
     const uint64_t i = deposit_skip(p, mask) | val;
     const float2 z = psi[i];
-    psi[i] = make_float2(fr * z.x - fi * z.y, fr * z.y + fi * z.x);
+    const float re = fmaf(fr, z.x, fmaf(-fi, z.y, fr_lo * z.x - fi_lo * z.y));
+    const float im = fmaf(fr, z.y, fmaf(fi, z.x, fr_lo * z.y + fi_lo * z.x));
+    psi[i] = make_float2(re, im);
   }
 }
 
@@ -180,10 +181,6 @@ int device_sm_count() {
 
 cudaError_t launch_init(float2 *psi, int n, bool uniform, float amp, cudaStream_t st) {
   if (n == 0) return cudaErrorInvalidValue;
-  if (n == 1 && !uniform) {
-    init_one_kernel<<<1, 1, 0, st>>>(psi, amp, true);
-    return cudaGetLastError();
-  }
   const uint64_t n4 = 1ull << (n - 1);
   init_kernel<<<grid_for(n4), kBlock, 0, st>>>(reinterpret_cast<float4 *>(psi), n4, amp, !uniform);
   return cudaGetLastError();
@@ -204,7 +201,14 @@ cudaError_t launch_gate_diag(float2 *psi, int n, uint64_t mask, uint64_t val, fl
                              cudaStream_t st) {
   const int fixed = __builtin_popcountll(mask);
   const uint64_t items = 1ull << (n - fixed);
-  diag_kernel<<<grid_for(items), kBlock, 0, st>>>(psi, items, mask, val, fr, fi);
+  // split each factor into fp32 hi + lo (exact for 0, +-1; 1/sqrt2 keeps its remainder)
+  const double s2 = 0.70710678118654752440;
+  auto lo = [&](float f) -> float {
+    const double a = std::fabs((double)f);
+    if (std::fabs(a - s2) < 1e-6) return (float)((f < 0 ? -s2 : s2) - (double)f);
+    return 0.f;
+  };
+  diag_kernel<<<grid_for(items), kBlock, 0, st>>>(psi, items, mask, val, fr, fi, lo(fr), lo(fi));
   return cudaGetLastError();
 }
 

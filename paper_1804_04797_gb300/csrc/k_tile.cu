@@ -26,7 +26,13 @@ using svp::DevStage;
 constexpr int kR = 5;
 constexpr int kE = 1 << kR;
 constexpr int kThreads = 256;  // 2^(13 - kR): one register group per thread
+// 1/sqrt2 as an unevaluated sum hi + lo: the float nearest 1/sqrt2 is 1.7e-8 low, and
+// multiplying by it alone shrinks the norm by that much at every T gate (a systematic
+// drift of 1e-6 over ~80 T gates); v*hi + v*lo in one fma rounds v/sqrt2 to nearest.
 constexpr float kS2 = 0.70710678118654752440f;
+constexpr float kS2lo = 1.21016171e-8f;  // 1/sqrt2 - kS2
+
+__device__ __forceinline__ float rs2(float v) { return fmaf(v, kS2, v * kS2lo); }
 
 __device__ __forceinline__ uint32_t swz(uint32_t L) {
   return L ^ (((L >> 4) ^ (L >> 8) ^ (L >> 12)) & 15u);
@@ -38,8 +44,8 @@ __device__ __forceinline__ float2 f2(float a, float b) { return make_float2(a, b
 struct GH {
   __device__ __forceinline__ static void f(float2 &x, float2 &y) {
     const float2 a = x, b = y;
-    x = f2(kS2 * (a.x + b.x), kS2 * (a.y + b.y));
-    y = f2(kS2 * (a.x - b.x), kS2 * (a.y - b.y));
+    x = f2(rs2(a.x + b.x), rs2(a.y + b.y));
+    y = f2(rs2(a.x - b.x), rs2(a.y - b.y));
   }
 };
 // X^{1/2}: x' = (s + i d)/2, y' = (s - i d)/2 with s = x + y, d = x - y
@@ -76,10 +82,10 @@ struct GSYDG {
 
 // ---- diagonal actions on one element -------------------------------------------------
 struct DT {  // times e^{i pi/4}
-  __device__ __forceinline__ static void f(float2 &z) { z = f2(kS2 * (z.x - z.y), kS2 * (z.x + z.y)); }
+  __device__ __forceinline__ static void f(float2 &z) { z = f2(rs2(z.x - z.y), rs2(z.x + z.y)); }
 };
 struct DTDG {
-  __device__ __forceinline__ static void f(float2 &z) { z = f2(kS2 * (z.x + z.y), kS2 * (z.y - z.x)); }
+  __device__ __forceinline__ static void f(float2 &z) { z = f2(rs2(z.x + z.y), rs2(z.y - z.x)); }
 };
 struct DNEG {
   __device__ __forceinline__ static void f(float2 &z) { z = f2(-z.x, -z.y); }
@@ -171,11 +177,12 @@ __device__ __forceinline__ void phase_all(float2 (&v)[kE], int p) {
       for (int e = 0; e < kE; ++e) v[e] = f2(v[e].y, -v[e].x);
       break;
     default: {
-      // w^p for odd p: (+-1 +- i)/sqrt2
-      const float cr = (p == 1 || p == 7) ? kS2 : -kS2;
-      const float ci = (p == 1 || p == 3) ? kS2 : -kS2;
+      // w^p for odd p: (sr + i si)/sqrt2 with sr, si = +-1
+      const float sr = (p == 1 || p == 7) ? 1.f : -1.f;
+      const float si = (p == 1 || p == 3) ? 1.f : -1.f;
 #pragma unroll
-      for (int e = 0; e < kE; ++e) v[e] = f2(cr * v[e].x - ci * v[e].y, cr * v[e].y + ci * v[e].x);
+      for (int e = 0; e < kE; ++e)
+        v[e] = f2(rs2(sr * v[e].x - si * v[e].y), rs2(sr * v[e].y + si * v[e].x));
     }
   }
 }

@@ -238,10 +238,13 @@ bool build_plan(int n, const std::vector<Gate> &gates, const Options &opt, bool 
       DevStage ds;
       std::memset(&ds, 0, sizeof(ds));
       ds.r = (uint8_t)R.size();
+      // the plain kernel always holds 2^kMaxReg amplitudes per thread: pad the register
+      // bits with unused tile bits (the fused kernel uses the first r of them)
       std::vector<int> rb = R;
-      for (int b = 0; (int)rb.size() < r && b < m; ++b)
+      const int rpad = std::min(kMaxReg, m);
+      for (int b = 0; (int)rb.size() < rpad && b < m; ++b)
         if (std::find(rb.begin(), rb.end(), b) == rb.end()) rb.push_back(b);
-      for (int j = 0; j < r; ++j) ds.rbit[j] = (uint8_t)rb[j];
+      for (int j = 0; j < rpad; ++j) ds.rbit[j] = (uint8_t)rb[j];
       std::vector<int> nonr;
       for (int b = 0; b < m; ++b)
         if (std::find(rb.begin(), rb.end(), b) == rb.end()) nonr.push_back(b);
@@ -251,7 +254,7 @@ bool build_plan(int n, const std::vector<Gate> &gates, const Options &opt, bool 
       auto reg_of = [&](int q) -> int {
         const int a = local_of[q];
         if (a < 0) return -1;
-        for (int j = 0; j < r; ++j)
+        for (int j = 0; j < rpad; ++j)
           if (rb[j] == a) return j;
         return -1;
       };
