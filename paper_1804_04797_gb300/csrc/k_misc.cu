@@ -100,16 +100,34 @@ __device__ __forceinline__ double warp_sum(double x) {
   return x;
 }
 
-// Level 1: each block sums a fixed, grid-strided share in fp64.
+// Level 1: each block sums a fixed, grid-strided share.  GB300's fp64 rate is a small
+// fraction of its fp32 rate, so |alpha|^2 and |alpha|^4 of 8 amplitudes are summed in
+// fp32 (relative error ~1e-7 per chunk, unbiased) and the chunk sums accumulate in fp64.
 __global__ void norm_partial_kernel(const float4 *psi4, uint64_t n4, double *partials) {
   double s2 = 0.0, s4 = 0.0;
-  for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < n4;
-       i += (uint64_t)gridDim.x * blockDim.x) {
+  const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+  uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x;
+  for (; i + 3 * stride < n4; i += 4 * stride) {
+    float4 z[4];
+#pragma unroll
+    for (int k = 0; k < 4; ++k) z[k] = psi4[i + k * stride];
+    float a2 = 0.f, a4 = 0.f;
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+      const float p0 = fmaf(z[k].x, z[k].x, z[k].y * z[k].y);
+      const float p1 = fmaf(z[k].z, z[k].z, z[k].w * z[k].w);
+      a2 += p0 + p1;
+      a4 = fmaf(p0, p0, fmaf(p1, p1, a4));
+    }
+    s2 += a2;
+    s4 += a4;
+  }
+  for (; i < n4; i += stride) {
     const float4 z = psi4[i];
-    const double p0 = (double)z.x * z.x + (double)z.y * z.y;
-    const double p1 = (double)z.z * z.z + (double)z.w * z.w;
-    s2 += p0 + p1;
-    s4 += p0 * p0 + p1 * p1;
+    const float p0 = fmaf(z.x, z.x, z.y * z.y);
+    const float p1 = fmaf(z.z, z.z, z.w * z.w);
+    s2 += (double)(p0 + p1);
+    s4 += (double)fmaf(p0, p0, p1 * p1);
   }
   __shared__ double r2[kBlock / 32], r4[kBlock / 32];
   s2 = warp_sum(s2);
