@@ -155,6 +155,23 @@ sv_status sv_get_amplitudes(sv_state *s, const uint64_t *bits, size_t m, double 
  * Deterministic (fixed two-level tree). */
 sv_status sv_norm(sv_state *s, double *norm2, double *sum_p2);
 
+/* Allocation-free variant of sv_norm, for callers that cannot allocate device memory:
+ * code under a device-memory budget owned by another allocator (a framework's caching
+ * allocator that has reserved the GPU), or code that must avoid the implicit device-wide
+ * synchronisation of cudaMalloc/cudaFree.  The paper has no counterpart; this is a
+ * library-usage convenience.
+ *   dev_state  2^n_qubits complex64 amplitudes on the current device (caller-owned).
+ *   n_qubits   1..34; anything else is SV_ERR_ARG.
+ *   stream     cudaStream_t to run on (NULL = legacy default stream); synchronised.
+ *   norm2, sum_p2  host doubles for sum |alpha|^2 and sum |alpha|^4 (either may be NULL).
+ * The scratch is one fixed file-scope device array of 1024 partial sums (16 KB + 16 B)
+ * that every GPU loading the library keeps until the process exits; the call makes no
+ * cudaMalloc/cudaFree.  The first call on a device looks up the array's device address
+ * (cudaGetSymbolAddress) with that device current: make it before any stream capture.
+ * All calls share the array and it keeps the last call's contents: calls that overlap
+ * on the GPU (other streams or host threads) race and can return wrong sums. */
+sv_status sv_norm_noalloc(const void *dev_state, int n_qubits, void *stream, double *norm2, double *sum_p2);
+
 /* Probabilities |alpha_x|^2 for m indices, in fp64. */
 sv_status sv_get_probabilities(sv_state *s, const uint64_t *bits, size_t m, double *out);
 
