@@ -29,7 +29,8 @@ def _sources():
 
 
 def _headers():
-    return glob.glob(os.path.join(CSRC, '*.h')) + glob.glob(os.path.join(ROOT, 'include', '*.h'))
+    return (glob.glob(os.path.join(CSRC, '*.h')) + glob.glob(os.path.join(CSRC, '*.cuh')) +
+            glob.glob(os.path.join(ROOT, 'include', '*.h')))
 
 
 def _stale(obj, src, hdr_time):

@@ -192,7 +192,8 @@ sv_status upload_plan(sv_state *s, const svp::Plan &P, svk::DevPlanView *view) {
   const size_t o_stage = align(o_pass + P.passes.size() * sizeof(svp::DevPass));
   const size_t o_op = align(o_stage + P.stages.size() * sizeof(svp::DevStage));
   const size_t o_mat = align(o_op + P.ops.size() * sizeof(svp::DevOp));
-  const size_t total = align(o_mat + P.mats.size() * sizeof(float)) + 256;
+  const size_t o_err = align(o_mat + P.mats.size() * sizeof(float));
+  const size_t total = o_err + 256;
   sv_status st = ensure_device_buffer(&s->d_plan, &s->d_plan_cap, total);
   if (st != SV_OK) return st;
   s->h_plan.assign(total, 0);
@@ -208,18 +209,18 @@ sv_status upload_plan(sv_state *s, const svp::Plan &P, svk::DevPlanView *view) {
   view->stages = reinterpret_cast<const svp::DevStage *>(d + o_stage);
   view->ops = reinterpret_cast<const svp::DevOp *>(d + o_op);
   view->mats = reinterpret_cast<const float *>(d + o_mat);
+  view->err = reinterpret_cast<int *>(d + o_err);
   return SV_OK;
 }
 
-sv_status run_plan(sv_state *s, const svp::Plan &P, const svk::DevPlanView &view) {
+sv_status run_plan(sv_state *s, const svp::Plan &P, const svk::DevPlanView &view, bool fused) {
   const double amps = std::ldexp(1.0, s->n);
   for (size_t p = 0; p < P.passes.size(); ++p) {
     const svp::DevPass &hp = P.passes[p];
     const double bytes = (hp.flags & (svp::PF_INIT_UNIFORM | svp::PF_INIT_ZERO)) ? 8.0 * amps : 16.0 * amps;
     prof_begin(s);
-    cudaError_t e = s->opts.precision == SV_PREC_TF32X3
-                        ? svk::launch_fused_pass(s->psi, s->n, view, (int)p, hp, s->stream)
-                        : svk::launch_tile_pass(s->psi, s->n, view, (int)p, hp, s->stream);
+    cudaError_t e = fused ? svk::launch_fused_pass(s->psi, s->n, view, (int)p, hp, s->stream)
+                          : svk::launch_tile_pass(s->psi, s->n, view, (int)p, hp, s->stream);
     prof_end(s, bytes);
     if (e != cudaSuccess) { s->broken = true; return cuda_fail(e, "tile pass kernel"); }
   }
@@ -242,12 +243,28 @@ sv_status apply_gates(sv_state *s, const std::vector<svp::Gate> &g) {
   svp::Plan P;
   const char *err = nullptr;
   svp::Options po = plan_options(s->opts);
+  // the tensor-core kernel takes 12- or 13-qubit tiles; smaller states use the plain one
+  if (po.fused && std::min(po.m, s->n) < 12) po.fused = false;
   if (!svp::build_plan(s->n, g, po, s->fresh, &P, &err)) return fail(SV_ERR_ARG, err ? err : "planning failed");
   if (po.fused && (st = build_stage_mats(&P, g, std::min(po.r, std::min(po.m, s->n)))) != SV_OK) return st;
+  if (po.fused)
+    for (const svp::DevPass &dp : P.passes)
+      if (dp.stage_count > 256) return fail(SV_ERR_ARG, "fused path: more than 256 stages in one pass");
   svk::DevPlanView view;
   if ((st = upload_plan(s, P, &view)) != SV_OK) return st;
-  if ((st = run_plan(s, P, view)) != SV_OK) return st;
+  if ((st = run_plan(s, P, view, po.fused)) != SV_OK) return st;
   s->fresh = false;
+  if (po.fused) {
+    // a fused pass whose bounded wait gave up leaves a non-zero error word
+    int h_err = 0;
+    cudaError_t e = cudaMemcpyAsync(&h_err, view.err, sizeof(int), cudaMemcpyDeviceToHost, s->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s->stream);
+    if (e != cudaSuccess) { s->broken = true; return cuda_fail(e, "fused pass"); }
+    if (h_err != 0) {
+      s->broken = true;
+      return fail(SV_ERR_TIMEOUT, "fused pass: a tensor-core wait gave up (state undefined)");
+    }
+  }
   return SV_OK;
 }
 

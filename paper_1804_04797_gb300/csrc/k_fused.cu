@@ -1,20 +1,480 @@
-// Fused k-qubit blocks on the tcgen05 tensor cores (split-TF32).  Placeholder until
-// the kernel lands: the fused precision mode reports itself unavailable.
+// Fused tile pass on the tcgen05 tensor cores (split-TF32, fp32 accumulation).
+//
+// Same passes and tiles as the plain kernel, but each stage's gates on its five
+// register qubits are applied as ONE 32x32 complex unitary U (multiplied out on the
+// host in fp64 from the gates, the "bunch of gates" of §2.3 as a matrix), i.e. a real
+// GEMM per tile:
+//     D[row, 2t+c'] = sum_{s,c} A[row, 2s+c] * B[2t+c', 2s+c],
+//     A = the tile's amplitudes, one row per group of 32 (register bits = column index s),
+//     B = [[Re U, -Im U], [Im U, Re U]] interleaved (64 x 64).
+// Precision: A = A_hi + A_lo and B = B_hi + B_lo, hi = x rounded to the nearest TF32,
+// lo = (x - hi) rounded to the nearest TF32; D = A_hi B_hi + A_hi B_lo + A_lo B_hi
+// accumulated in fp32 in tensor memory (the dropped terms are ~2^-22 relative).
+// Data movement per stage: each thread gathers its row (32 amplitudes) from the shared
+// tile, splits it and stores A_hi/A_lo into TMEM (its own lane); one thread issues the
+// 24 MMAs per 128-row block (A from TMEM, B from shared memory) and commits them to an
+// mbarrier; every thread then loads its row of D back from TMEM, applies the stage's
+// diagonal epilogue (gates that touch a non-register qubit) and scatters the row back
+// into the shared tile.  B (hi and lo, 32 KB per stage) is streamed from the plan in
+// global memory by TMA bulk copies into two shared buffers, one stage ahead.
+// All waits are bounded: a wait that gives up sets the error word, the CTA stops
+// issuing work, drains its outstanding copies and MMAs (bounded), frees its TMEM and
+// returns.
 #include <cuda_runtime.h>
 
+#include <cmath>
+#include <cstring>
+#include <vector>
+
 #include "kernels.h"
+#include "capi_util.h"
 #include "state.h"
+#include "tile_common.cuh"
 
 namespace svk {
+namespace {
 
-bool fused_supported() { return false; }
+using namespace tile;
 
-cudaError_t launch_fused_pass(float2 *, int, const DevPlanView &, int, const svp::DevPass &, cudaStream_t) {
-  return cudaErrorNotSupported;
+constexpr int kK = 64;                   // real K = N = 2 * 2^5
+constexpr int kBBytes = kK * kK * 4;     // one 64x64 fp32 matrix: 16 KB
+constexpr int kBStage = 2 * kBBytes;     // hi + lo
+constexpr unsigned long long kWaitNs = 1000000000ull;  // give up a wait after 1 s
+
+__host__ __device__ inline uint32_t kmaj_off(int row, int k) {
+  // K-major, no swizzle: 8-row x 16-byte core matrices, K-adjacent core matrices 128 B
+  // apart (leading byte offset), row-adjacent core matrices (kK/4)*128 B apart (stride).
+  return (uint32_t)((((row >> 3) * (kK / 4) + (k >> 2)) * 128) + (row & 7) * 16 + (k & 3) * 4);
+}
+
+__device__ __forceinline__ uint32_t smem_u32(const void *p) {
+  return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+
+__device__ __forceinline__ uint64_t smem_desc(uint32_t saddr) {
+  uint64_t d = 0;
+  d |= (uint64_t)((saddr & 0x3FFFF) >> 4);
+  d |= (uint64_t)(128 >> 4) << 16;               // leading byte offset (K direction)
+  d |= (uint64_t)(((kK / 4) * 128) >> 4) << 32;  // stride byte offset (row direction)
+  d |= (uint64_t)1 << 46;                         // tcgen05 descriptor version
+  return d;                                       // base offset 0, no swizzle
+}
+
+// kind::tf32 instruction descriptor: D fp32, A/B tf32, K-major, M = 128, N = 64.
+constexpr uint32_t kIdesc = (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(kK >> 3) << 17) | ((uint32_t)(128 >> 4) << 24);
+
+__device__ __forceinline__ bool mbar_try(uint32_t bar, uint32_t phase) {
+  uint32_t ok;
+  asm volatile("{\n .reg .pred P1;\n mbarrier.try_wait.parity.shared::cta.b64 P1, [%1], %2;\n selp.b32 %0, 1, 0, P1;\n}\n"
+               : "=r"(ok) : "r"(bar), "r"(phase) : "memory");
+  return ok != 0;
+}
+__device__ __forceinline__ unsigned long long global_ns() {
+  unsigned long long t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t phase) {
+  if (mbar_try(bar, phase)) return true;
+  const unsigned long long t0 = global_ns();
+  while (global_ns() - t0 < kWaitNs)
+    if (mbar_try(bar, phase)) return true;
+  return false;
+}
+
+__device__ __forceinline__ void mma_tf32(uint32_t d, uint32_t a_tmem, uint64_t b_desc, uint32_t acc) {
+  asm volatile("{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n tcgen05.mma.cta_group::1.kind::tf32 [%0], [%1], %2, %3, p;\n}\n"
+               :: "r"(d), "r"(a_tmem), "l"(b_desc), "r"(kIdesc), "r"(acc));
+}
+
+#define SV_TMEM_ST16(taddr, r)                                                                              \
+  asm volatile("tcgen05.st.sync.aligned.32x32b.x16.b32 [%0], {%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,%16};" \
+               :: "r"(taddr), "r"(r[0]), "r"(r[1]), "r"(r[2]), "r"(r[3]), "r"(r[4]), "r"(r[5]), "r"(r[6]), "r"(r[7]), \
+                 "r"(r[8]), "r"(r[9]), "r"(r[10]), "r"(r[11]), "r"(r[12]), "r"(r[13]), "r"(r[14]), "r"(r[15]) : "memory")
+#define SV_TMEM_LD16(taddr, r)                                                                              \
+  asm volatile("tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];" \
+               : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]), \
+                 "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]) \
+               : "r"(taddr) : "memory")
+
+// Round to the nearest TF32 value (ties away from zero).  Both split parts are rounded
+// this way so that each is exactly representable (the tensor core then drops nothing)
+// and the residual x - hi - lo has no sign bias; truncating instead biases every
+// product toward zero and shrinks the norm by ~2e-7 per stage (measured).
+__device__ __forceinline__ float tf32_rn(float x) {
+  uint32_t r;
+  asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(x));
+  return __uint_as_float(r);
+}
+
+// TMEM columns: A_hi at [64 mb, +64), A_lo at [64 MB + 64 mb, +64), D at [128 MB + 64 mb, +64)
+template <int MB>
+struct Cols {
+  static constexpr uint32_t kAlloc = MB == 1 ? 256 : 512;
+  __device__ static uint32_t a_hi(int mb) { return 64u * mb; }
+  __device__ static uint32_t a_lo(int mb) { return 64u * MB + 64u * mb; }
+  __device__ static uint32_t d(int mb) { return 128u * MB + 64u * mb; }
+};
+
+// Issue the B load (hi and lo) of stage `st` into buffer `buf`.
+__device__ __forceinline__ void issue_b_load(const float *mats, const DevStage &st, unsigned char *bbuf, int buf,
+                                             uint32_t bar) {
+  const float *src = mats + st.mat_begin;
+  const uint32_t dst = smem_u32(bbuf + buf * kBStage);
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" :: "r"(bar), "r"(kBStage) : "memory");
+  asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];"
+               :: "r"(dst), "l"(src), "r"(kBBytes), "r"(bar) : "memory");
+  asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];"
+               :: "r"(dst + kBBytes), "l"(src + kK * kK), "r"(kBBytes), "r"(bar) : "memory");
+}
+
+// Norm^2 of the shared tile: fp32 over each thread's 16 float4 slots, fp64 across the
+// CTA (fixed order).  Result broadcast through red[0].
+__device__ __forceinline__ double tile_norm2(const float2 *tile, int m, double *red) {
+  const int tid = threadIdx.x, nthreads = blockDim.x;
+  float s = 0.f;
+  const uint32_t half = 1u << (m - 1);
+  for (uint32_t f = tid; f < half; f += nthreads) {
+    const float4 x = reinterpret_cast<const float4 *>(tile)[f];
+    s = fmaf(x.x, x.x, fmaf(x.y, x.y, fmaf(x.z, x.z, fmaf(x.w, x.w, s))));
+  }
+  double d = s;
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) d += __shfl_xor_sync(0xffffffffu, d, o);
+  if ((tid & 31) == 0) red[1 + (tid >> 5)] = d;
+  __syncthreads();
+  if (tid == 0) {
+    double t = 0.0;
+    for (int w = 0; w < nthreads / 32; ++w) t += red[1 + w];
+    red[0] = t;
+  }
+  __syncthreads();
+  return red[0];
+}
+
+__device__ __forceinline__ uint32_t mix32(uint32_t x) {  // integer hash (xorshift-multiply)
+  x ^= x >> 16;
+  x *= 0x7feb352du;
+  x ^= x >> 15;
+  x *= 0x846ca68bu;
+  x ^= x >> 16;
+  return x;
+}
+
+// x * (1 + delta) rounded stochastically: the RN sum plus, with probability
+// |residual| / ulp, one ulp toward the residual.  Unbiased for sub-ulp delta, which
+// plain rounding would drop.
+__device__ __forceinline__ float scale_sr(float x, float delta, uint32_t h) {
+  const float c = x * delta;
+  const float y = x + c;
+  const float e = (x - y) + c;  // exact error of the sum (|x| >= |c|)
+  const float ay = fabsf(y);
+  if (!(ay > 1e-30f)) return y;
+  const float ulp = __uint_as_float(__float_as_uint(ay) & 0x7F800000u) * 1.1920928955078125e-7f;
+  const float u = (float)(h >> 8) * 5.9604644775390625e-8f;  // [0, 1)
+  return (u * ulp < fabsf(e)) ? y + copysignf(ulp, e) : y;
+}
+
+__device__ __forceinline__ void rescale_tile(float2 *tile, int m, float delta, uint64_t base, int pass_index) {
+  const uint32_t n = 1u << m;
+  const uint32_t seed = mix32((uint32_t)base ^ (uint32_t)(base >> 32) ^ (0x9E3779B9u * (uint32_t)(pass_index + 1)));
+  for (uint32_t i = threadIdx.x; i < n; i += blockDim.x) {
+    float2 z = tile[i];
+    const uint32_t h = mix32(seed ^ (2u * i));
+    z.x = scale_sr(z.x, delta, h);
+    z.y = scale_sr(z.y, delta, mix32(h + 0x632BE5ABu));
+    tile[i] = z;
+  }
+}
+
+template <int MB>
+__global__ void __launch_bounds__(128 * MB, 1)
+fused_pass_kernel(float2 *__restrict__ psi, DevPlanView plan, int pass_index, uint64_t num_tiles) {
+  int *err = plan.err;
+  extern __shared__ __align__(1024) unsigned char smem_raw[];
+  unsigned char *bbuf = smem_raw;                                      // 2 x 32 KB
+  float2 *tile = reinterpret_cast<float2 *>(smem_raw + 2 * kBStage);  // 2^m amplitudes
+  __shared__ DevPass P;
+  __shared__ uint64_t chunk_off[1 << 10];
+  __shared__ __align__(8) uint64_t bars[3];  // [0] MMA done, [1],[2] B buffer full
+  __shared__ uint32_t tmem_slot;
+  __shared__ int abort_flag;
+  __shared__ int16_t mma_list[256];
+  __shared__ int n_mma;
+  __shared__ double red[1 + 8];
+
+  const int tid = threadIdx.x, warp = tid >> 5;
+  if (tid == 0) {
+    P = plan.passes[pass_index];
+    abort_flag = 0;
+    for (int i = 0; i < 3; ++i)
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" :: "r"(smem_u32(&bars[i])), "r"(1));
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;"
+                 :: "r"(smem_u32(&tmem_slot)), "r"(Cols<MB>::kAlloc));
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+  }
+  __syncthreads();
+  build_chunk_table(P, chunk_off);
+  if (tid == 0) {
+    int k = 0;
+    for (int s = 0; s < P.stage_count && k < 256; ++s)
+      if (!plan.stages[P.stage_begin + s].diag_only) mma_list[k++] = (int16_t)s;
+    n_mma = k;
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  const uint32_t tmem = tmem_slot;
+  const uint32_t lane_off = (uint32_t)(32 * (warp & 3)) << 16;
+  const int mb = tid >> 7;
+  const uint32_t bar_mma = smem_u32(&bars[0]);
+  uint32_t mma_phase = 0;
+  uint32_t b_phase0 = 0, b_phase1 = 0;  // tid 0 only
+  int qglob = 0;                        // MMA stages issued so far (B buffer = qglob & 1)
+  int b_loads_out = 0;                  // tid 0: B loads issued and not yet waited for
+  bool mma_out = false;                 // tid 0: MMAs committed and not yet waited for
+
+  if (tid == 0 && n_mma > 0 && blockIdx.x < num_tiles) {
+    issue_b_load(plan.mats, plan.stages[P.stage_begin + mma_list[0]], bbuf, 0, smem_u32(&bars[1]));
+    ++b_loads_out;
+  }
+
+  for (uint64_t tile_id = blockIdx.x; tile_id < num_tiles && !abort_flag; tile_id += gridDim.x) {
+    const uint64_t base = tile_base(P, tile_id);
+    const bool last_tile = tile_id + gridDim.x >= num_tiles;
+    load_tile(psi, tile, P, chunk_off, base);
+    __syncthreads();
+    const bool keep_norm = (P.flags & svp::PF_UNITARY) && n_mma > 0;
+    const double norm_in = keep_norm ? tile_norm2(tile, P.m, red) : 0.0;
+    int q = 0;  // MMA stage index within this tile
+    for (int s = 0; s < P.stage_count; ++s) {
+      const DevStage &st = plan.stages[P.stage_begin + s];
+      uint32_t L0;
+      uint64_t G0;
+      group_base(st, P, tid, base, &L0, &G0);
+      float2 v[kE];
+      load_group(tile, st, L0, v);
+      if (!st.diag_only) {
+        const int buf = qglob & 1;
+        // prefetch the next MMA stage's B into the other buffer (its last reader, the
+        // previous MMA stage, has completed)
+        if (tid == 0) {
+          const bool more_here = q + 1 < n_mma;
+          if (more_here || !last_tile) {
+            const DevStage &nx = plan.stages[P.stage_begin + mma_list[more_here ? q + 1 : 0]];
+            issue_b_load(plan.mats, nx, bbuf, buf ^ 1, smem_u32(&bars[1 + (buf ^ 1)]));
+            ++b_loads_out;
+          }
+        }
+        // A = this thread's row, split into TF32 hi + lo, into its TMEM lane
+#pragma unroll
+        for (int h = 0; h < 4; ++h) {
+          uint32_t rh[16], rl[16];
+#pragma unroll
+          for (int e = 0; e < 8; ++e) {
+            const float2 z = v[8 * h + e];
+            const float hr = tf32_rn(z.x), hi = tf32_rn(z.y);
+            rh[2 * e] = __float_as_uint(hr);
+            rh[2 * e + 1] = __float_as_uint(hi);
+            rl[2 * e] = __float_as_uint(tf32_rn(z.x - hr));
+            rl[2 * e + 1] = __float_as_uint(tf32_rn(z.y - hi));
+          }
+          SV_TMEM_ST16(tmem + lane_off + Cols<MB>::a_hi(mb) + 16 * h, rh);
+          SV_TMEM_ST16(tmem + lane_off + Cols<MB>::a_lo(mb) + 16 * h, rl);
+        }
+        asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
+        asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+        __syncthreads();
+        if (tid == 0) {
+          asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+          const uint32_t bbar = smem_u32(&bars[1 + buf]);
+          const uint32_t ph = buf ? b_phase1 : b_phase0;
+          if (!mbar_wait(bbar, ph)) {
+            atomicExch(err, 1);
+            abort_flag = 1;
+          } else {
+            --b_loads_out;
+            if (buf) b_phase1 ^= 1; else b_phase0 ^= 1;
+            const uint32_t bhi = smem_u32(bbuf + buf * kBStage), blo = bhi + kBBytes;
+#pragma unroll
+            for (int m = 0; m < MB; ++m) {
+              const uint32_t d = tmem + Cols<MB>::d(m);
+              const uint32_t ah = tmem + Cols<MB>::a_hi(m), al = tmem + Cols<MB>::a_lo(m);
+#pragma unroll
+              for (int kk = 0; kk < kK / 8; ++kk) mma_tf32(d, ah + 8 * kk, smem_desc(bhi + 256 * kk), kk > 0);
+#pragma unroll
+              for (int kk = 0; kk < kK / 8; ++kk) mma_tf32(d, ah + 8 * kk, smem_desc(blo + 256 * kk), 1);
+#pragma unroll
+              for (int kk = 0; kk < kK / 8; ++kk) mma_tf32(d, al + 8 * kk, smem_desc(bhi + 256 * kk), 1);
+            }
+            asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];"
+                         :: "r"(bar_mma) : "memory");
+            mma_out = true;
+          }
+        }
+        __syncthreads();
+        if (abort_flag) break;
+        if (!mbar_wait(bar_mma, mma_phase)) {
+          atomicExch(err, 2);
+          abort_flag = 1;
+        }
+        mma_phase ^= 1;
+        if (tid == 0) mma_out = false;
+        __syncthreads();  // every thread sees the same abort_flag before the warp-wide loads
+        if (abort_flag) break;
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        {
+#pragma unroll
+          for (int h = 0; h < 4; ++h) {
+            uint32_t r[16];
+            SV_TMEM_LD16(tmem + lane_off + Cols<MB>::d(mb) + 16 * h, r);
+            asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+            for (int e = 0; e < 8; ++e) v[8 * h + e] = make_float2(__uint_as_float(r[2 * e]), __uint_as_float(r[2 * e + 1]));
+          }
+        }
+        asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+        ++q;
+        ++qglob;
+      }
+      apply_ops(v, plan.ops, st.op_begin, st.op_count, G0, plan.mats);
+      asm volatile("" ::: "memory");
+      group_base(st, P, tid, base, &L0, &G0);
+      store_group(tile, st, L0, v);
+      __syncthreads();
+      if (abort_flag) break;
+    }
+    if (abort_flag) break;
+    // Every gate of the pass acts inside the tile, so a unitary pass keeps the tile's
+    // norm exactly.  The tensor core's fp32 accumulation truncates toward zero and
+    // loses ~0.3 ulp of every output per stage (a systematic norm drift of ~6e-8 per
+    // stage); restore the tile's norm with unbiased stochastic rounding.
+    if (keep_norm) {
+      const double norm_out = tile_norm2(tile, P.m, red);
+      if (norm_out > 0.0) {
+        const float delta = (float)(sqrt(norm_in / norm_out) - 1.0);
+        rescale_tile(tile, P.m, delta, base, pass_index);
+        __syncthreads();
+      }
+    }
+    store_tile(psi, tile, P, chunk_off, base);
+    __syncthreads();
+  }
+
+  // drain what is still in flight (bounded), then free the tensor memory
+  if (tid == 0) {
+    if (mma_out) mbar_wait(bar_mma, mma_phase);
+    for (int i = 0; i < 2 && b_loads_out > 0; ++i) {
+      const uint32_t ph = (qglob & 1) ? b_phase1 : b_phase0;
+      if (mbar_wait(smem_u32(&bars[1 + (qglob & 1)]), ph)) --b_loads_out;
+      ++qglob;
+    }
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  if (warp == 0)
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" :: "r"(tmem), "r"(Cols<MB>::kAlloc));
+}
+
+template <int MB>
+cudaError_t launch_mb(float2 *psi, int n, const DevPlanView &plan, int pass_index, const svp::DevPass &hp,
+                      cudaStream_t st) {
+  static bool configured = false;
+  // m = 12: 32 KB tile + 64 KB B buffers (+9 KB static): two CTAs per SM, never three
+  // (2 x 256 TMEM columns); m = 13: 64 KB tile, one CTA per SM (512 columns).
+  const size_t smem = (size_t)(2 * kBStage) + (sizeof(float2) << (MB == 1 ? 12 : 13));
+  if (!configured) {
+    cudaError_t e = cudaFuncSetAttribute(fused_pass_kernel<MB>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    configured = true;
+  }
+  const uint64_t tiles = 1ull << (n - hp.m);
+  uint64_t grid = (uint64_t)device_sm_count() * (MB == 1 ? 2 : 1);
+  if (grid > tiles) grid = tiles;
+  fused_pass_kernel<MB><<<(unsigned)grid, 128 * MB, smem, st>>>(psi, plan, pass_index, tiles);
+  return cudaGetLastError();
+}
+
+}  // namespace
+
+bool fused_supported() {
+  static int cached = -1;
+  if (cached < 0) {
+    int dev = 0, major = 0, minor = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&major, cudaDevAttrComputeCapabilityMajor, dev);
+    cudaDeviceGetAttribute(&minor, cudaDevAttrComputeCapabilityMinor, dev);
+    cached = (major == 10 && minor == 3) ? 1 : 0;
+  }
+  return cached == 1;
+}
+
+cudaError_t launch_fused_pass(float2 *psi, int n, const DevPlanView &plan, int pass_index, const svp::DevPass &hp,
+                              cudaStream_t st) {
+  if (hp.m == 12) return launch_mb<1>(psi, n, plan, pass_index, hp, st);
+  if (hp.m == 13) return launch_mb<2>(psi, n, plan, pass_index, hp, st);
+  return cudaErrorInvalidValue;
 }
 
 }  // namespace svk
 
 namespace svc {
-sv_status build_stage_mats(svp::Plan *, const std::vector<svp::Gate> &, int) { return SV_OK; }
+
+// Nearest TF32 value of a finite float, ties away from zero (the host twin of
+// cvt.rna.tf32.f32): add half a TF32 ulp to the magnitude bits, clear the 13 low bits.
+static float tf32_round_host(float x) {
+  uint32_t b;
+  std::memcpy(&b, &x, 4);
+  b = (b + 0x1000u) & 0xFFFFE000u;
+  float y;
+  std::memcpy(&y, &b, 4);
+  return y;
+}
+
+// Stage unitaries as split-TF32 B operands in the kernel's shared-memory layout.
+sv_status build_stage_mats(svp::Plan *P, const std::vector<svp::Gate> &g, int r) {
+  if (r != 5) return svc::fail(SV_ERR_ARG, "fused path: fuse_k must be 5");
+  P->mats.clear();
+  std::vector<double> u;
+  for (size_t s = 0; s < P->stages.size(); ++s) {
+    svp::DevStage &ds = P->stages[s];
+    if (P->stage_gates[s].empty()) {
+      ds.diag_only = 1;
+      continue;
+    }
+    ds.diag_only = 0;
+    ds.unitary = 1;
+    for (int gi : P->stage_gates[s]) {
+      const int k = g[gi].kind;
+      if (k == svp::K_P0 || k == svp::K_P1 || k == svp::K_PEQ) ds.unitary = 0;
+    }
+    svp::stage_unitary(*P, g, (int)s, 5, &u);
+    const size_t off = P->mats.size();
+    ds.mat_begin = (uint32_t)off;
+    P->mats.resize(off + 2 * svk::kK * svk::kK, 0.f);
+    float *hi = P->mats.data() + off;
+    float *lo = hi + svk::kK * svk::kK;
+    for (int t = 0; t < 32; ++t) {
+      for (int sidx = 0; sidx < 32; ++sidx) {
+        const double ur = u[2 * ((size_t)t * 32 + sidx)], ui = u[2 * ((size_t)t * 32 + sidx) + 1];
+        const double b[2][2] = {{ur, -ui}, {ui, ur}};  // [c'][c]
+        for (int cp = 0; cp < 2; ++cp) {
+          for (int c = 0; c < 2; ++c) {
+            const double x = b[cp][c];
+            const float h = tf32_round_host((float)x);
+            const float l = tf32_round_host((float)(x - (double)h));
+            const uint32_t o = svk::kmaj_off(2 * t + cp, 2 * sidx + c) / 4;
+            hi[o] = h;
+            lo[o] = l;
+          }
+        }
+      }
+    }
+  }
+  return SV_OK;
+}
+
 }  // namespace svc

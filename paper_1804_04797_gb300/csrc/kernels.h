@@ -19,6 +19,7 @@ struct DevPlanView {
   const svp::DevStage *stages;
   const svp::DevOp *ops;
   const float *mats;
+  int *err;  // error word of the plan (0 = ok; set by a kernel whose bounded wait gave up)
 };
 
 // K0: write |0..0> (uniform == false) or the uniform 2^{-n/2} state.  Write-only.
@@ -31,7 +32,7 @@ cudaError_t launch_tile_pass(float2 *psi, int n, const DevPlanView &plan, int pa
 
 // K4 fused tensor-core tile pass (tcgen05, split-TF32).
 cudaError_t launch_fused_pass(float2 *psi, int n, const DevPlanView &plan, int pass_index,
-                              const svp::DevPass &host_pass, cudaStream_t st);
+                              const svp::DevPass &host_pass, cudaStream_t st);  // tile_bits 12 or 13
 bool fused_supported();
 
 // Per-gate sweeps (K2 one-qubit pair update, K3 diagonal factor on a bit pattern).

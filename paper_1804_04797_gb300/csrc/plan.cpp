@@ -308,6 +308,14 @@ bool build_plan(int n, const std::vector<Gate> &gates, const Options &opt, bool 
       for (int gi : post) { P.order.push_back(gi); P.pass_of.push_back(pass_index); }
     }
     dp.stage_count = (uint16_t)(P.stages.size() - dp.stage_begin);
+    {
+      bool unitary = true;
+      for (int gi : now) {
+        const int k = gates[gi].kind;
+        if (k == K_P0 || k == K_P1 || k == K_PEQ) unitary = false;
+      }
+      if (unitary) dp.flags |= PF_UNITARY;
+    }
     P.passes.push_back(dp);
     rem.swap(later);
     first_pass = false;

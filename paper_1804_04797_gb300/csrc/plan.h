@@ -67,12 +67,15 @@ struct DevStage {
   uint8_t pad0;
   uint16_t op_begin, op_count;   // into the plan's op array
   uint32_t mat_begin;            // fused path: offset of this stage's unitary (floats)
-  uint8_t diag_only, pad1[3];
+  uint8_t diag_only;
+  uint8_t unitary;  // fused path: the inner gates contain no projector (U is unitary)
+  uint8_t pad1[2];
 };
 
 enum PassFlags : uint8_t {
   PF_INIT_UNIFORM = 1,  // tile content is 2^{-n/2} everywhere; nothing is read
   PF_INIT_ZERO = 2,     // tile content is |0..0>; nothing is read
+  PF_UNITARY = 4,       // no projector in the pass: every tile keeps its norm
 };
 
 struct DevPass {

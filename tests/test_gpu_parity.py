@@ -43,8 +43,10 @@ def run_gpu(lat, **kw):
     return psi, norm2, sp2
 
 
+TC = sv.SV_PREC_TF32X3
 MODES = [dict(), dict(tile_bits=10, low_bits=4, fuse_k=5), dict(tile_bits=8, low_bits=2, fuse_k=3),
-         dict(tile_bits=12, low_bits=5, fuse_k=4), dict(precision=sv.SV_PREC_PERGATE)]
+         dict(tile_bits=12, low_bits=5, fuse_k=4), dict(precision=sv.SV_PREC_PERGATE),
+         dict(precision=TC), dict(precision=TC, tile_bits=12), dict(precision=TC, tile_bits=12, low_bits=3)]
 
 
 @pytest.mark.parametrize('kw', MODES)
@@ -71,7 +73,8 @@ SIZES = [inputs.lattice_for(2, 3, 8, seed=4),            # 6 qubits: one tile = 
 def test_sizes_match_oracle(lat):
     n, gates = oracle_gates(lat)
     want = csim.run(n, gates)
-    for kw in (dict(), dict(tile_bits=min(13, max(6, n)), low_bits=min(4, n), fuse_k=5)):
+    for kw in (dict(), dict(tile_bits=min(13, max(6, n)), low_bits=min(4, n), fuse_k=5), dict(precision=TC),
+               dict(precision=TC, tile_bits=12)):
         psi, norm2, _ = run_gpu(lat, **kw)
         assert rel_l2(psi, want) <= REL_L2, kw
         assert abs(norm2 - 1) <= NORM_TOL
@@ -121,7 +124,8 @@ def _oracle_apply(n, gl, psi):
 
 
 @pytest.mark.parametrize('n,kw', [(7, {}), (13, {}), (18, {}), (18, dict(tile_bits=9, low_bits=3, fuse_k=2)),
-                                  (16, dict(precision=sv.SV_PREC_PERGATE))])
+                                  (16, dict(precision=sv.SV_PREC_PERGATE)), (12, dict(precision=TC)),
+                                  (17, dict(precision=TC)), (19, dict(precision=TC, tile_bits=12))])
 def test_all_gate_kinds_from_zero_and_loaded_state(n, kw):
     gl = _random_gate_list(n, 120, seed=n)
     # from |0..0> (no H layer: the first pass generates |0..0>)
@@ -159,10 +163,11 @@ def test_projectors_zero_exactly():
     assert np.count_nonzero(psi[~dead]) == np.count_nonzero(~dead)
 
 
-def test_inverse_circuit_returns_to_zero_state():
+@pytest.mark.parametrize('prec', [sv.SV_PREC_PLAIN, TC])
+def test_inverse_circuit_returns_to_zero_state(prec):
     lat = inputs.lattice_for(4, 5, 16, seed=21)
     g = sv.sv_generate_circuit(lat)
-    h = sv.sv_create(20)
+    h = sv.sv_create(20, sv.options(precision=prec))
     try:
         sv.sv_apply_circuit(h, g)
         sv.sv_apply_circuit_inverse(h, g)
@@ -218,9 +223,10 @@ def test_branch_amplitudes_small_cut_match_oracle():
     bits = inputs.bitstrings(n, 64, seed=2)
     want_full = csim.run(n, gates)[np.array(bits, dtype=np.int64)]
     want_branch = csim.branch_amplitudes(n, gates, half_a, bits)
-    got = sv.sv_branch_amplitudes(lat, half_a, bits)
     assert rel_l2(want_branch, want_full) < 1e-12
-    assert rel_l2(got, want_full) <= REL_L2
+    for kw in (dict(), dict(precision=TC)):
+        got = sv.sv_branch_amplitudes(lat, half_a, bits, sv.options(**kw))
+        assert rel_l2(got, want_full) <= REL_L2, kw
 
 
 def test_branch_amplitudes_28q_check_against_full_state():
