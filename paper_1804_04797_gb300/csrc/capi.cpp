@@ -23,7 +23,8 @@ extern "C" const char *sv_last_error(void) { return svc::last_error().c_str(); }
 namespace svc {
 
 sv_status cuda_fail(cudaError_t e, const char *what) {
-  return failf(SV_ERR_CUDA, "%s: %s", (std::string(what) + " / " + cudaGetErrorString(e)).c_str(), 0);
+  last_error() = std::string(what) + ": " + cudaGetErrorString(e);
+  return SV_ERR_CUDA;
 }
 
 sv_status ensure_device_buffer(void **buf, size_t *cap, size_t need) {

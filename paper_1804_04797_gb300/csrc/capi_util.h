@@ -18,7 +18,8 @@ inline sv_status fail(sv_status st, const char *msg) {
   return st;
 }
 
-inline sv_status failf(sv_status st, const char *fmt, const char *a, long long b = 0) {
+// fmt takes exactly one %s (a) followed by one %lld (b)
+inline sv_status failf(sv_status st, const char *fmt, const char *a, long long b) {
   char buf[512];
   std::snprintf(buf, sizeof(buf), fmt, a, b);
   last_error() = buf;

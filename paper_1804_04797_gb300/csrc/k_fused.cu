@@ -97,14 +97,13 @@ __device__ __forceinline__ void mma_tf32(uint32_t d, uint32_t a_tmem, uint64_t b
                  "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]) \
                : "r"(taddr) : "memory")
 
-// Round to the nearest TF32 value (ties away from zero).  Both split parts are rounded
-// this way so that each is exactly representable (the tensor core then drops nothing)
-// and the residual x - hi - lo has no sign bias; truncating instead biases every
-// product toward zero and shrinks the norm by ~2e-7 per stage (measured).
+// Round to the nearest TF32 value, ties away from zero (add half a TF32 ulp to the
+// magnitude bits, clear the 13 low mantissa bits).  Both split parts are rounded this
+// way so that each is exactly representable (the tensor core then drops nothing) and
+// the residual x - hi - lo has no sign bias; truncating instead biases every product
+// toward zero.
 __device__ __forceinline__ float tf32_rn(float x) {
-  uint32_t r;
-  asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(x));
-  return __uint_as_float(r);
+  return __uint_as_float((__float_as_uint(x) + 0x1000u) & 0xFFFFE000u);
 }
 
 // TMEM columns: A_hi at [64 mb, +64), A_lo at [64 MB + 64 mb, +64), D at [128 MB + 64 mb, +64)
@@ -128,17 +127,10 @@ __device__ __forceinline__ void issue_b_load(const float *mats, const DevStage &
                :: "r"(dst + kBBytes), "l"(src + kK * kK), "r"(kBBytes), "r"(bar) : "memory");
 }
 
-// Norm^2 of the shared tile: fp32 over each thread's 16 float4 slots, fp64 across the
-// CTA (fixed order).  Result broadcast through red[0].
-__device__ __forceinline__ double tile_norm2(const float2 *tile, int m, double *red) {
+// Sum over the CTA of one double per thread, fixed order; red holds one slot per warp
+// plus the result.  Every thread returns the total.
+__device__ __forceinline__ double cta_sum(double d, double *red) {
   const int tid = threadIdx.x, nthreads = blockDim.x;
-  float s = 0.f;
-  const uint32_t half = 1u << (m - 1);
-  for (uint32_t f = tid; f < half; f += nthreads) {
-    const float4 x = reinterpret_cast<const float4 *>(tile)[f];
-    s = fmaf(x.x, x.x, fmaf(x.y, x.y, fmaf(x.z, x.z, fmaf(x.w, x.w, s))));
-  }
-  double d = s;
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) d += __shfl_xor_sync(0xffffffffu, d, o);
   if ((tid & 31) == 0) red[1 + (tid >> 5)] = d;
@@ -152,38 +144,33 @@ __device__ __forceinline__ double tile_norm2(const float2 *tile, int m, double *
   return red[0];
 }
 
-__device__ __forceinline__ uint32_t mix32(uint32_t x) {  // integer hash (xorshift-multiply)
-  x ^= x >> 16;
-  x *= 0x7feb352du;
-  x ^= x >> 15;
-  x *= 0x846ca68bu;
-  x ^= x >> 16;
-  return x;
+__device__ __forceinline__ float row_norm2(const float2 (&v)[kE]) {
+  float s = 0.f;
+#pragma unroll
+  for (int e = 0; e < kE; ++e) s = fmaf(v[e].x, v[e].x, fmaf(v[e].y, v[e].y, s));
+  return s;
 }
 
 // x * (1 + delta) rounded stochastically: the RN sum plus, with probability
 // |residual| / ulp, one ulp toward the residual.  Unbiased for sub-ulp delta, which
-// plain rounding would drop.
-__device__ __forceinline__ float scale_sr(float x, float delta, uint32_t h) {
+// plain rounding would drop.  u in [0, 1).
+__device__ __forceinline__ float scale_sr(float x, float delta, float u) {
   const float c = x * delta;
   const float y = x + c;
   const float e = (x - y) + c;  // exact error of the sum (|x| >= |c|)
-  const float ay = fabsf(y);
-  if (!(ay > 1e-30f)) return y;
-  const float ulp = __uint_as_float(__float_as_uint(ay) & 0x7F800000u) * 1.1920928955078125e-7f;
-  const float u = (float)(h >> 8) * 5.9604644775390625e-8f;  // [0, 1)
+  const float ulp = __uint_as_float(__float_as_uint(y) & 0x7F800000u) * 1.1920928955078125e-7f;
   return (u * ulp < fabsf(e)) ? y + copysignf(ulp, e) : y;
 }
 
-__device__ __forceinline__ void rescale_tile(float2 *tile, int m, float delta, uint64_t base, int pass_index) {
-  const uint32_t n = 1u << m;
-  const uint32_t seed = mix32((uint32_t)base ^ (uint32_t)(base >> 32) ^ (0x9E3779B9u * (uint32_t)(pass_index + 1)));
-  for (uint32_t i = threadIdx.x; i < n; i += blockDim.x) {
-    float2 z = tile[i];
-    const uint32_t h = mix32(seed ^ (2u * i));
-    z.x = scale_sr(z.x, delta, h);
-    z.y = scale_sr(z.y, delta, mix32(h + 0x632BE5ABu));
-    tile[i] = z;
+// Scale a register row by (1 + delta) with stochastic rounding; the uniform numbers
+// come from a Weyl sequence (golden-ratio increments) seeded per tile, pass and row.
+__device__ __forceinline__ void scale_row(float2 (&v)[kE], float delta, uint32_t seed) {
+#pragma unroll
+  for (int e = 0; e < kE; ++e) {
+    const uint32_t h0 = seed + (uint32_t)(2 * e) * 0x9E3779B9u;
+    const uint32_t h1 = h0 + 0x9E3779B9u;
+    v[e].x = scale_sr(v[e].x, delta, (float)(h0 >> 8) * 5.9604644775390625e-8f);
+    v[e].y = scale_sr(v[e].y, delta, (float)(h1 >> 8) * 5.9604644775390625e-8f);
   }
 }
 
@@ -247,8 +234,13 @@ fused_pass_kernel(float2 *__restrict__ psi, DevPlanView plan, int pass_index, ui
     const bool last_tile = tile_id + gridDim.x >= num_tiles;
     load_tile(psi, tile, P, chunk_off, base);
     __syncthreads();
+    // Every gate of the pass acts inside the tile, so a unitary pass keeps the tile's
+    // norm exactly.  The tensor core's fp32 accumulation truncates toward zero and loses
+    // ~0.3 ulp of every output per stage (a systematic norm drift of ~6e-8 per stage);
+    // the tile's norm is measured in the first stage and restored in the last one with
+    // unbiased stochastic rounding.
     const bool keep_norm = (P.flags & svp::PF_UNITARY) && n_mma > 0;
-    const double norm_in = keep_norm ? tile_norm2(tile, P.m, red) : 0.0;
+    double norm_in = 0.0;
     int q = 0;  // MMA stage index within this tile
     for (int s = 0; s < P.stage_count; ++s) {
       const DevStage &st = plan.stages[P.stage_begin + s];
@@ -257,6 +249,7 @@ fused_pass_kernel(float2 *__restrict__ psi, DevPlanView plan, int pass_index, ui
       group_base(st, P, tid, base, &L0, &G0);
       float2 v[kE];
       load_group(tile, st, L0, v);
+      if (keep_norm && s == 0) norm_in = cta_sum((double)row_norm2(v), red);
       if (!st.diag_only) {
         const int buf = qglob & 1;
         // prefetch the next MMA stage's B into the other buffer (its last reader, the
@@ -298,17 +291,20 @@ fused_pass_kernel(float2 *__restrict__ psi, DevPlanView plan, int pass_index, ui
           } else {
             --b_loads_out;
             if (buf) b_phase1 ^= 1; else b_phase0 ^= 1;
-            const uint32_t bhi = smem_u32(bbuf + buf * kBStage), blo = bhi + kBBytes;
+            const uint32_t bhi = smem_u32(bbuf + buf * kBStage);
+            const uint64_t dhi = smem_desc(bhi), dlo = smem_desc(bhi + kBBytes);  // +16 per 256 B K step
 #pragma unroll
             for (int m = 0; m < MB; ++m) {
               const uint32_t d = tmem + Cols<MB>::d(m);
               const uint32_t ah = tmem + Cols<MB>::a_hi(m), al = tmem + Cols<MB>::a_lo(m);
+              // small correction terms first, the large hi*hi term last: fewer truncating
+              // accumulations at full magnitude
 #pragma unroll
-              for (int kk = 0; kk < kK / 8; ++kk) mma_tf32(d, ah + 8 * kk, smem_desc(bhi + 256 * kk), kk > 0);
+              for (int kk = 0; kk < kK / 8; ++kk) mma_tf32(d, al + 8 * kk, dhi + 16 * kk, kk > 0);
 #pragma unroll
-              for (int kk = 0; kk < kK / 8; ++kk) mma_tf32(d, ah + 8 * kk, smem_desc(blo + 256 * kk), 1);
+              for (int kk = 0; kk < kK / 8; ++kk) mma_tf32(d, ah + 8 * kk, dlo + 16 * kk, 1);
 #pragma unroll
-              for (int kk = 0; kk < kK / 8; ++kk) mma_tf32(d, al + 8 * kk, smem_desc(bhi + 256 * kk), 1);
+              for (int kk = 0; kk < kK / 8; ++kk) mma_tf32(d, ah + 8 * kk, dhi + 16 * kk, 1);
             }
             asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];"
                          :: "r"(bar_mma) : "memory");
@@ -327,20 +323,30 @@ fused_pass_kernel(float2 *__restrict__ psi, DevPlanView plan, int pass_index, ui
         if (abort_flag) break;
         asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
         {
+          uint32_t r[4][16];
 #pragma unroll
-          for (int h = 0; h < 4; ++h) {
-            uint32_t r[16];
-            SV_TMEM_LD16(tmem + lane_off + Cols<MB>::d(mb) + 16 * h, r);
-            asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+          for (int h = 0; h < 4; ++h) SV_TMEM_LD16(tmem + lane_off + Cols<MB>::d(mb) + 16 * h, r[h]);
+          asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 #pragma unroll
-            for (int e = 0; e < 8; ++e) v[8 * h + e] = make_float2(__uint_as_float(r[2 * e]), __uint_as_float(r[2 * e + 1]));
-          }
+          for (int h = 0; h < 4; ++h)
+#pragma unroll
+            for (int e = 0; e < 8; ++e)
+              v[8 * h + e] = make_float2(__uint_as_float(r[h][2 * e]), __uint_as_float(r[h][2 * e + 1]));
         }
         asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
         ++q;
         ++qglob;
       }
       apply_ops(v, plan.ops, st.op_begin, st.op_count, G0, plan.mats);
+      if (keep_norm && s == P.stage_count - 1) {
+        const double norm_out = cta_sum((double)row_norm2(v), red);
+        if (norm_out > 0.0) {
+          const float delta = (float)(sqrt(norm_in / norm_out) - 1.0);
+          const uint32_t seed = (uint32_t)base * 0x85EBCA6Bu + (uint32_t)(base >> 32) * 0xC2B2AE35u +
+                                (uint32_t)pass_index * 0x27D4EB2Fu + (uint32_t)tid * 0x165667B1u;
+          scale_row(v, delta, seed);
+        }
+      }
       asm volatile("" ::: "memory");
       group_base(st, P, tid, base, &L0, &G0);
       store_group(tile, st, L0, v);
@@ -348,18 +354,6 @@ fused_pass_kernel(float2 *__restrict__ psi, DevPlanView plan, int pass_index, ui
       if (abort_flag) break;
     }
     if (abort_flag) break;
-    // Every gate of the pass acts inside the tile, so a unitary pass keeps the tile's
-    // norm exactly.  The tensor core's fp32 accumulation truncates toward zero and
-    // loses ~0.3 ulp of every output per stage (a systematic norm drift of ~6e-8 per
-    // stage); restore the tile's norm with unbiased stochastic rounding.
-    if (keep_norm) {
-      const double norm_out = tile_norm2(tile, P.m, red);
-      if (norm_out > 0.0) {
-        const float delta = (float)(sqrt(norm_in / norm_out) - 1.0);
-        rescale_tile(tile, P.m, delta, base, pass_index);
-        __syncthreads();
-      }
-    }
     store_tile(psi, tile, P, chunk_off, base);
     __syncthreads();
   }
