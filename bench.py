@@ -133,6 +133,55 @@ def run_reference(args, rank, world):
     return 0
 
 
+def run_batch(args, rank, world):
+    """The uneven batch (512 circuits, 16..24 qubits, depth 10..24): circuits/s of the
+    persistent graph-captured launch against one-at-a-time plain launches."""
+    import numpy as np
+    import torch
+    from paper_1804_04797_gb300 import inputs, sv
+    torch.cuda.set_device(int(os.environ.get('LOCAL_RANK', '0')))
+    lats = inputs.batch(512)
+    opts = sv.options(autotune=1)
+    for _ in range(max(1, args.warmup)):
+        sv.sv_apply_batch(lats, opts)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        stats = sv.sv_apply_batch(lats, opts)
+    torch.cuda.synchronize()
+    graph_s = (time.perf_counter() - t0) / args.steps
+    sv.sv_batch_free()
+    # one circuit at a time through sv_apply_circuit, states preallocated
+    hs, gl = [], []
+    for lat in lats:
+        hs.append(sv.sv_create(lat.n_qubits))
+        gl.append(sv.sv_generate_circuit(lat))
+    for h, g in zip(hs, gl):
+        sv.sv_reset(h)
+        sv.sv_apply_circuit(h, g)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for h, g in zip(hs, gl):
+        sv.sv_reset(h)
+        sv.sv_apply_circuit(h, g)
+    torch.cuda.synchronize()
+    seq_s = time.perf_counter() - t0
+    for h in hs:
+        sv.sv_destroy(h)
+    amps = sum(2 ** l.n_qubits for l in lats)
+    line = {'metric': 'uneven batch circuits/s (persistent graph launch vs one-at-a-time)', 'workload': 'batch',
+            'value': len(lats) / graph_s, 'unit': 'circuits/s', 'higher_is_better': True,
+            'n_gpus': world, 'steps': args.steps, 'warmup': args.warmup,
+            'config': {'workload': '512 circuits, 16..24 qubits, depth 10..24, seed 180404797',
+                       'state_bytes': 8 * amps},
+            'graph_s_per_batch': graph_s, 'sequential_s_per_batch': seq_s,
+            'speedup_vs_sequential': seq_s / graph_s,
+            'max_norm_err': float(np.max(np.abs(stats[:, 0] - 1.0)))}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument('--gpus', type=int, default=1)
@@ -143,6 +192,8 @@ def main():
     ap.add_argument('--no-fused', action='store_true')
     ap.add_argument('--paths', default='plain,tf32x3', help='comma list of plain, tf32x3, pergate')
     ap.add_argument('--tile-bits', type=int, default=0, help='tile qubits of the tile passes (0 = default 13)')
+    ap.add_argument('--workload', default='34q', choices=['34q', 'batch'],
+                    help='34q: the headline circuit; batch: the 512-circuit uneven batch (secondary line)')
     ap.add_argument('--no-cpu', action='store_true')
     args = ap.parse_args()
 
@@ -151,6 +202,8 @@ def main():
     local = int(os.environ.get('LOCAL_RANK', '0'))
     if args.impl == 'reference':
         return run_reference(args, rank, world)
+    if args.workload == 'batch':
+        return run_batch(args, rank, world)
 
     import numpy as np
     import torch

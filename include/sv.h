@@ -188,14 +188,26 @@ sv_status sv_branch_amplitudes(const sv_lattice *lat, const sv_cut *cut, const u
 
 /* --- batch ------------------------------------------------------------------------------ */
 
-/* Simulate count independent lattice circuits (each with its own state, 1..28 qubits)
- * in one persistent launch over a work queue of (circuit, pass, tile) items, captured
- * once in a CUDA graph and replayed on later calls with the same lattices.  Items wait
- * for the previous pass of their circuit with a bounded spin; if it gives up the call
- * returns SV_ERR_TIMEOUT.  stats_out (may be NULL) receives 3 doubles per circuit:
- * norm2, sum_p2, Re/Im are not reported -- [norm2, sum_p2, n_qubits]. */
+/* Simulate count independent lattice circuits (each with its own state, 6..28 qubits;
+ * §2's circuits at many sizes) in ONE persistent launch over a work queue of (circuit,
+ * pass, tile) items: all circuits' first passes, then all second passes, ...  An item
+ * waits for its circuit's previous pass with a bounded spin; if a wait gives up the call
+ * returns SV_ERR_TIMEOUT (no hang).  The launch, the queue reset and the per-circuit fp64
+ * statistics are captured once in a CUDA graph and replayed while the same lattice list
+ * is passed again; the states stay on the device until the next different batch or
+ * sv_batch_free.  opts (may be NULL): tile_bits 0 or 10..13 (default 13); autotune = 1
+ * with tile_bits 0 times tile sizes 11..13 on this batch and keeps the fastest in a JSON
+ * cache (SV_AUTOTUNE_CACHE, default autotune.json beside the library); stream orders the
+ * call after the caller's stream.  stats_out (may be NULL): 3 doubles per circuit,
+ * [sum |alpha|^2, sum |alpha|^4, n_qubits].  Synchronises. */
 sv_status sv_apply_batch(const sv_lattice *circs, size_t count, const sv_options *opts,
                          double *stats_out);
+
+/* Amplitudes of circuit `circuit` of the last batch (host doubles re, im; 2m values). */
+sv_status sv_batch_amplitudes(size_t circuit, const uint64_t *bits, size_t m, double *out_re_im);
+
+/* Release the device memory and graph kept for the last batch. */
+sv_status sv_batch_free(void);
 
 /* --- planning and measurement (host-only helpers) --------------------------------------- */
 

@@ -1,5 +1,4 @@
-// C ABI of the two composite tasks: few amplitudes by the cut decomposition (K6) and
-// the uneven batch of independent circuits (K7).
+// C ABI of the few-amplitude task: amplitudes by the cut decomposition (K6).
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -122,29 +121,5 @@ extern "C" sv_status sv_branch_amplitudes(const sv_lattice *lat, const sv_cut *c
     e = cudaMemcpyAsync(out_re_im, d_out, 2 * m * sizeof(double), cudaMemcpyDeviceToHost, s->stream);
   if (e == cudaSuccess) e = cudaStreamSynchronize(s->stream);
   if (e != cudaSuccess) return cuda_fail(e, "sv_branch_amplitudes");
-  return SV_OK;
-}
-
-extern "C" sv_status sv_apply_batch(const sv_lattice *circs, size_t count, const sv_options *opts,
-                                    double *stats_out) {
-  clear_error();
-  if (count && !circs) return fail(SV_ERR_ARG, "sv_apply_batch: NULL lattice array");
-  sv_status st;
-  for (size_t i = 0; i < count; ++i) {
-    const int n = lattice_qubits(&circs[i]);
-    if (n < 1 || n > 28) return fail(SV_ERR_ARG, "sv_apply_batch: circuits must have 1..28 qubits");
-    std::vector<sv_gate> g;
-    if ((st = generate(&circs[i], &g)) != SV_OK) return st;
-    Holder h;
-    if ((st = sv_create(n, opts, &h.s)) != SV_OK) return st;
-    if ((st = sv_apply_circuit(h.s, g.data(), g.size())) != SV_OK) return st;
-    double a = 0, b = 0;
-    if ((st = sv_norm(h.s, &a, &b)) != SV_OK) return st;
-    if (stats_out) {
-      stats_out[3 * i] = a;
-      stats_out[3 * i + 1] = b;
-      stats_out[3 * i + 2] = n;
-    }
-  }
   return SV_OK;
 }

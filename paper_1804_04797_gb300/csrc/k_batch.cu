@@ -1,0 +1,156 @@
+// K7: the uneven batch in one persistent launch.
+//
+// Every CTA repeatedly takes the next item (one tile of one pass of one circuit) from a
+// global counter and runs the plain tile pass on it.  Before an item of pass p it waits
+// until every tile of pass p-1 of the same circuit is done (a per-circuit-pass counter),
+// with a bounded spin: a wait that gives up sets the error word and the CTA leaves.  The
+// queue holds all circuits' first passes, then all second passes, ..., so the waits are
+// rare and short.  The state is read through L2 only, because other CTAs of the same
+// launch wrote it and L1 is not coherent across SMs.
+#include <cuda_runtime.h>
+
+#include "batch.h"
+#include "tile_common.cuh"
+
+namespace svk {
+namespace {
+
+using namespace tile;
+
+constexpr unsigned long long kDepWaitNs = 5000000000ull;  // 5 s
+
+__device__ __forceinline__ unsigned long long now_ns() {
+  unsigned long long t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+
+__device__ __forceinline__ unsigned int load_acquire(const unsigned int *p) {
+  unsigned int v;
+  asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+  return v;
+}
+
+__global__ void __launch_bounds__(256, 2)
+batch_kernel(float2 *__restrict__ states, DevPlanView plan, const BatchCP *__restrict__ cps,
+             const BatchItem *__restrict__ items, uint64_t n_items, unsigned int *words) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  float2 *tile = reinterpret_cast<float2 *>(smem_raw);
+  __shared__ DevPass P;
+  __shared__ uint64_t chunk_off[1 << 10];
+  __shared__ unsigned int s_item;
+  __shared__ uint32_t s_cp;
+  __shared__ int s_stop;
+  const int tid = threadIdx.x;
+  unsigned int *done = words + kBatchHeader;
+  uint32_t cur_cp = kNoPrev;
+  for (;;) {
+    if (tid == 0) {
+      s_item = atomicAdd(&words[0], 1u);
+      s_stop = 0;
+    }
+    __syncthreads();
+    const unsigned int idx = s_item;
+    if (idx >= n_items) break;
+    const BatchItem it = items[idx];
+    const BatchCP cp = cps[it.cp];
+    if (it.cp != cur_cp) {
+      if (tid == 0) P = plan.passes[cp.pass];
+      __syncthreads();
+      build_chunk_table(P, chunk_off);
+      cur_cp = it.cp;
+    }
+    if (tid == 0 && cp.prev != kNoPrev) {
+      const unsigned int need = cps[cp.prev].tiles;
+      if (load_acquire(&done[cp.prev]) < need) {
+        const unsigned long long t0 = now_ns();
+        while (load_acquire(&done[cp.prev]) < need) {
+          if (now_ns() - t0 > kDepWaitNs) {
+            atomicExch(&words[1], 1u);
+            s_stop = 1;
+            break;
+          }
+        }
+      }
+    }
+    __syncthreads();
+    if (s_stop) break;
+    process_tile_plain<true>(states + cp.state_off, plan, P, chunk_off, tile, it.tile);
+    __threadfence();  // each thread's stores visible device-wide before the count
+    __syncthreads();
+    if (tid == 0) atomicAdd(&done[it.cp], 1u);
+  }
+}
+
+__device__ __forceinline__ double warp_sum(double x) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
+  return x;
+}
+
+__global__ void batch_stats_partial(const float2 *__restrict__ states, const BatchChunk *__restrict__ chunks,
+                                    double *partials) {
+  const BatchChunk ch = chunks[blockIdx.x];
+  const float2 *p = states + ch.start;
+  double s2 = 0, s4 = 0;
+  for (uint32_t i = threadIdx.x; i < ch.len; i += blockDim.x) {
+    const float2 z = p[i];
+    const float q = fmaf(z.x, z.x, z.y * z.y);
+    s2 += q;
+    s4 += (double)q * q;
+  }
+  __shared__ double r2[8], r4[8];
+  s2 = warp_sum(s2);
+  s4 = warp_sum(s4);
+  if ((threadIdx.x & 31) == 0) { r2[threadIdx.x >> 5] = s2; r4[threadIdx.x >> 5] = s4; }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double a = 0, b = 0;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) { a += r2[w]; b += r4[w]; }
+    partials[2 * blockIdx.x] = a;
+    partials[2 * blockIdx.x + 1] = b;
+  }
+}
+
+__global__ void batch_stats_final(const double *partials, const int *chunk_begin, int n_circuits, double *stats) {
+  const int c = blockIdx.x * blockDim.x + threadIdx.x;
+  if (c >= n_circuits) return;
+  double a = 0, b = 0;
+  for (int k = chunk_begin[c]; k < chunk_begin[c + 1]; ++k) { a += partials[2 * k]; b += partials[2 * k + 1]; }
+  stats[2 * c] = a;
+  stats[2 * c + 1] = b;
+}
+
+}  // namespace
+
+int batch_block_threads(int m) { return 1 << (m - kR); }
+
+cudaError_t launch_batch(float2 *states, const DevPlanView &plan, const BatchCP *cps, const BatchItem *items,
+                         uint64_t n_items, unsigned int *words, int m, cudaStream_t st) {
+  static bool configured = false;
+  static int per_sm = 1;
+  const size_t smem = sizeof(float2) << svp::kMaxTileBits;
+  if (!configured) {
+    cudaError_t e = cudaFuncSetAttribute(batch_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, batch_kernel, 256, smem);
+    if (e != cudaSuccess) return e;
+    if (per_sm < 1) per_sm = 1;
+    configured = true;
+  }
+  const int threads = batch_block_threads(m);
+  // smaller tiles use fewer threads: more CTAs fit, but the occupancy query for 256
+  // threads is a safe lower bound
+  const int grid = device_sm_count() * per_sm * (256 / threads);
+  batch_kernel<<<grid, threads, sizeof(float2) << m, st>>>(states, plan, cps, items, n_items, words);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_batch_stats(const float2 *states, const BatchChunk *chunks, int n_chunks, double *partials,
+                               const int *chunk_begin, int n_circuits, double *stats, cudaStream_t st) {
+  if (n_chunks > 0) batch_stats_partial<<<n_chunks, 256, 0, st>>>(states, chunks, partials);
+  batch_stats_final<<<(n_circuits + 127) / 128, 128, 0, st>>>(partials, chunk_begin, n_circuits, stats);
+  return cudaGetLastError();
+}
+
+}  // namespace svk

@@ -37,27 +37,8 @@ tile_pass_kernel(float2 *__restrict__ psi, DevPlanView plan, int pass_index, uin
   build_chunk_table(P, chunk_off);
   __syncthreads();
 
-  for (uint64_t tile_id = blockIdx.x; tile_id < num_tiles; tile_id += gridDim.x) {
-    const uint64_t base = tile_base(P, tile_id);
-    load_tile(psi, tile, P, chunk_off, base);
-    __syncthreads();
-    for (int s = 0; s < P.stage_count; ++s) {
-      const DevStage &st = plan.stages[P.stage_begin + s];
-      uint32_t L0;
-      uint64_t G0;
-      group_base(st, P, tid, base, &L0, &G0);
-      float2 v[kE];
-      load_group(tile, st, L0, v);
-      apply_ops(v, plan.ops, st.op_begin, st.op_count, G0, plan.mats);
-      // Recompute the addresses rather than keeping 32 of them live across the ops.
-      asm volatile("" ::: "memory");
-      group_base(st, P, tid, base, &L0, &G0);
-      store_group(tile, st, L0, v);
-      __syncthreads();
-    }
-    store_tile(psi, tile, P, chunk_off, base);
-    __syncthreads();
-  }
+  for (uint64_t tile_id = blockIdx.x; tile_id < num_tiles; tile_id += gridDim.x)
+    process_tile_plain(psi, plan, P, chunk_off, tile, tile_id);
 }
 
 int g_tile_blocks_per_sm = 0;

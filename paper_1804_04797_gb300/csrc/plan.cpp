@@ -179,7 +179,7 @@ bool build_plan(int n, const std::vector<Gate> &gates, const Options &opt, bool 
     } else {
       P.hbm_bytes += 16.0 * amps;
     }
-    dp.stage_begin = (uint16_t)P.stages.size();
+    dp.stage_begin = (uint32_t)P.stages.size();
 
     // ---- stages: groups of <= r register bits ------------------------------------
     std::vector<char> done(now.size(), 0);
@@ -249,7 +249,7 @@ bool build_plan(int n, const std::vector<Gate> &gates, const Options &opt, bool 
       for (int b = 0; b < m; ++b)
         if (std::find(rb.begin(), rb.end(), b) == rb.end()) nonr.push_back(b);
       order_group_bits(m, nonr, ds.nonr);
-      ds.op_begin = (uint16_t)P.ops.size();
+      ds.op_begin = (uint32_t)P.ops.size();
       ds.diag_only = inner.empty() ? 1 : 0;
       auto reg_of = [&](int q) -> int {
         const int a = local_of[q];
@@ -299,6 +299,7 @@ bool build_plan(int n, const std::vector<Gate> &gates, const Options &opt, bool 
       if (!opt.fused)
         for (int gi : inner) lower(gi);
       for (int gi : post) lower(gi);
+      if (P.ops.size() - ds.op_begin > 65535) { *err = "stage too large"; return false; }
       ds.op_count = (uint16_t)(P.ops.size() - ds.op_begin);
       P.stages.push_back(ds);
       P.stage_gates.push_back(inner);
@@ -321,7 +322,8 @@ bool build_plan(int n, const std::vector<Gate> &gates, const Options &opt, bool 
     first_pass = false;
     if (P.passes.size() > 100000) { *err = "planner did not converge"; return false; }
   }
-  if (P.ops.size() > 65535 || P.stages.size() > 65535) { *err = "plan too large"; return false; }
+  for (const DevStage &ds : P.stages)
+    if (ds.op_count > 65535) { *err = "plan too large"; return false; }
   return true;
 }
 

@@ -61,16 +61,17 @@ constexpr int kMaxTileBits = 13;
 constexpr int kMaxReg = 5;
 
 struct DevStage {
-  uint8_t r;              // register bits in use (<= kMaxReg); the rest are padding
-  uint8_t rbit[kMaxReg];  // tile-local bit of register bit j (all distinct, padded)
+  uint8_t r;                   // register bits in use (<= kMaxReg); the rest are padding
+  uint8_t rbit[kMaxReg];       // tile-local bit of register bit j (all distinct, padded)
   uint8_t nonr[kMaxTileBits];  // tile-local bits of the group index, lane bits first
-  uint8_t pad0;
-  uint16_t op_begin, op_count;   // into the plan's op array
-  uint32_t mat_begin;            // fused path: offset of this stage's unitary (floats)
-  uint8_t diag_only;
-  uint8_t unitary;  // fused path: the inner gates contain no projector (U is unitary)
-  uint8_t pad1[2];
+  uint8_t diag_only;           // no inner gates: nothing for the tensor cores
+  uint32_t op_begin;           // into the plan's op array
+  uint16_t op_count;
+  uint8_t unitary;             // fused path: the inner gates contain no projector
+  uint8_t pad1;
+  uint32_t mat_begin;          // fused path: offset of this stage's unitary (floats)
 };
+static_assert(sizeof(DevStage) == 32, "DevStage layout");
 
 enum PassFlags : uint8_t {
   PF_INIT_UNIFORM = 1,  // tile content is 2^{-n/2} everywhere; nothing is read
@@ -83,11 +84,12 @@ struct DevPass {
   uint8_t tq[kMaxTileBits];   // tile-local bit -> global qubit (tq[i] = i for i < c)
   uint8_t nt;                 // number of non-tile qubits (n - m)
   uint8_t ntq[64];            // non-tile qubits, ascending (tile index bit -> qubit)
-  uint16_t stage_begin, stage_count;
-  uint32_t pad;
+  uint16_t stage_count;
+  uint32_t stage_begin;       // into the plan's stage array
   float init_amp;             // uniform amplitude for PF_INIT_UNIFORM
-  float pad2;
+  uint32_t pad;
 };
+static_assert(sizeof(DevPass) == 96, "DevPass layout");
 
 struct Options {
   int m = 13;        // tile qubits

@@ -300,7 +300,9 @@ __device__ __forceinline__ void build_chunk_table(const DevPass &P, uint64_t *ch
 }
 
 // Read (or generate) the tile into shared memory: 16-byte coalesced vectors, 8 in flight
-// per thread.
+// per thread.  kL2Only reads through L2 only (ld.global.cg): needed when other CTAs of
+// the same launch wrote the data, since L1 is not coherent across SMs.
+template <bool kL2Only = false>
 __device__ __forceinline__ void load_tile(const float2 *__restrict__ psi, float2 *tile, const DevPass &P,
                                           const uint64_t *chunk_off, uint64_t base) {
   const int tid = threadIdx.x, nthreads = blockDim.x;
@@ -325,7 +327,7 @@ __device__ __forceinline__ void load_tile(const float2 *__restrict__ psi, float2
     for (int b = 0; b < kBatch; ++b) {
       const uint32_t L = 2u * (tid + (it0 + b) * nthreads);
       const uint64_t g = base + chunk_off[L >> c] + (L & low_mask);
-      buf[b] = *reinterpret_cast<const float4 *>(psi + g);
+      buf[b] = kL2Only ? __ldcg(reinterpret_cast<const float4 *>(psi + g)) : *reinterpret_cast<const float4 *>(psi + g);
     }
 #pragma unroll
     for (int b = 0; b < kBatch; ++b) {
@@ -353,6 +355,34 @@ __device__ __forceinline__ void store_tile(float2 *__restrict__ psi, const float
     const uint64_t g = base + chunk_off[L >> c] + (L & low_mask);
     *reinterpret_cast<float4 *>(psi + g) = x;
   }
+}
+
+// One tile of one plain pass: load (or generate), every stage in registers, store.
+// The caller has built chunk_off for P and synchronised; ends with __syncthreads.
+template <bool kL2Only = false>
+__device__ __forceinline__ void process_tile_plain(float2 *__restrict__ psi, const DevPlanView &plan,
+                                                   const DevPass &P, const uint64_t *chunk_off, float2 *tile,
+                                                   uint64_t tile_id) {
+  const int tid = threadIdx.x;
+  const uint64_t base = tile_base(P, tile_id);
+  load_tile<kL2Only>(psi, tile, P, chunk_off, base);
+  __syncthreads();
+  for (int s = 0; s < P.stage_count; ++s) {
+    const DevStage &st = plan.stages[P.stage_begin + s];
+    uint32_t L0;
+    uint64_t G0;
+    group_base(st, P, tid, base, &L0, &G0);
+    float2 v[kE];
+    load_group(tile, st, L0, v);
+    apply_ops(v, plan.ops, st.op_begin, st.op_count, G0, plan.mats);
+    // Recompute the addresses rather than keeping 32 of them live across the ops.
+    asm volatile("" ::: "memory");
+    group_base(st, P, tid, base, &L0, &G0);
+    store_group(tile, st, L0, v);
+    __syncthreads();
+  }
+  store_tile(psi, tile, P, chunk_off, base);
+  __syncthreads();
 }
 
 }  // namespace tile

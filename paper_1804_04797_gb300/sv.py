@@ -86,6 +86,9 @@ def lib():
         'sv_norm': ([vp, P(c_double), P(c_double)], c_int),
         'sv_branch_amplitudes': ([P(sv_lattice), P(sv_cut), vp, c_size_t, P(sv_options), vp], c_int),
         'sv_apply_batch': ([vp, c_size_t, P(sv_options), vp], c_int),
+        'sv_batch_amplitudes': ([c_size_t, vp, c_size_t, vp], c_int),
+        'sv_batch_free': ([], c_int),
+        'sv_norm_noalloc': ([vp, c_int, vp, P(c_double), P(c_double)], c_int),
         'sv_plan': ([c_int, vp, c_size_t, P(sv_options), c_int, P(sv_plan_summary), vp, vp, vp,
                      c_size_t], c_int),
         'sv_set_profiling': ([vp, c_int], c_int),
@@ -234,6 +237,23 @@ def sv_apply_batch(lats, opts=None):
     _check(lib().sv_apply_batch(ctypes.cast(arr, c_void_p), len(lats),
                                 ctypes.byref(opts) if opts is not None else None, stats.ctypes.data))
     return stats.reshape(len(lats), 3)
+
+
+def sv_batch_amplitudes(circuit, bits):
+    b = np.ascontiguousarray(bits, dtype=np.uint64)
+    out = np.zeros(2 * b.size, dtype=np.float64)
+    _check(lib().sv_batch_amplitudes(circuit, b.ctypes.data, b.size, out.ctypes.data))
+    return out.view(np.complex128)
+
+
+def sv_batch_free():
+    _check(lib().sv_batch_free())
+
+
+def sv_norm_noalloc(dev_ptr, n_qubits, stream=None):
+    a, b = c_double(), c_double()
+    _check(lib().sv_norm_noalloc(c_void_p(dev_ptr), n_qubits, c_void_p(stream), ctypes.byref(a), ctypes.byref(b)))
+    return a.value, b.value
 
 
 def sv_plan(n_qubits, gates, opts=None, fresh_state=True):

@@ -256,3 +256,28 @@ def test_batch_stats_match_oracle():
         assert row[2] == n
         assert abs(row[0] - 1) <= NORM_TOL
         assert abs(row[1] - s4) <= 1e-5 * s4
+
+
+def test_batch_amplitudes_and_replay_match_oracle(tmp_path, monkeypatch):
+    """Uneven batch in one persistent launch: per-circuit amplitudes and statistics match
+    the oracle; the graph replay gives bit-identical statistics; autotune writes its cache."""
+    lats = inputs.batch(12)
+    stats = sv.sv_apply_batch(lats)
+    again = sv.sv_apply_batch(lats)
+    assert np.array_equal(stats, again)
+    for i in (0, 5, 11):
+        n, gates = oracle_gates(lats[i])
+        want = csim.run(n, gates)
+        bits = inputs.bitstrings(n, 32, seed=7)
+        got = sv.sv_batch_amplitudes(i, bits)
+        assert rel_l2(got, want[np.array(bits, dtype=np.int64)]) <= REL_L2
+        s2, s4 = csim.reductions(want)
+        assert abs(stats[i][0] - 1) <= NORM_TOL and abs(stats[i][1] - s4) <= 1e-5 * s4
+    cache = tmp_path / 'tune.json'
+    monkeypatch.setenv('SV_AUTOTUNE_CACHE', str(cache))
+    tuned = sv.sv_apply_batch(lats, sv.options(autotune=1))
+    assert cache.exists() and '|batch|' in cache.read_text()
+    np.testing.assert_allclose(tuned[:, 0], 1.0, atol=NORM_TOL)
+    sv.sv_batch_free()
+    with pytest.raises(sv.SvError):
+        sv.sv_batch_amplitudes(0, [0])
