@@ -182,6 +182,34 @@ def run_batch(args, rank, world):
     return 0
 
 
+def run_branch(args, rank, world):
+    """The amplitude task: 64 amplitudes of the 42-qubit 6x7 depth-10 circuit by the cut
+    decomposition (t = 10 crossing CZs, 1024 branches, two 31-qubit batched half-states)."""
+    import torch
+    from paper_1804_04797_gb300 import inputs, sv
+    torch.cuda.set_device(int(os.environ.get('LOCAL_RANK', '0')))
+    lat = inputs.C42
+    bits = inputs.bitstrings(lat.n_qubits, 64, seed=2)
+    out = {}
+    for name, prec in (('plain', sv.SV_PREC_PLAIN), ('tf32x3', sv.SV_PREC_TF32X3)):
+        o = sv.options(precision=prec)
+        for _ in range(max(1, args.warmup)):
+            sv.sv_branch_amplitudes(lat, inputs.C42_HALF_A, bits, o)
+        t0 = time.perf_counter()
+        for _ in range(args.steps):
+            amps = sv.sv_branch_amplitudes(lat, inputs.C42_HALF_A, bits, o)
+        out[name] = {'s_per_task': (time.perf_counter() - t0) / args.steps, 'amp0': [amps[0].real, amps[0].imag]}
+    # each half-state: (21 + 10) qubits, 16 GiB; passes read and write it once
+    line = {'metric': '42q cut-branch amplitude task, s per 64 amplitudes', 'workload': 'branch42',
+            'value': min(v['s_per_task'] for v in out.values()), 'unit': 's/task', 'higher_is_better': False,
+            'n_gpus': world, 'steps': args.steps, 'warmup': args.warmup,
+            'config': {'workload': '6x7 lattice, depth 10, cut rows 2|3, t = 10, 64 bitstrings (seed 2)'},
+            'paths': out}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument('--gpus', type=int, default=1)
@@ -192,8 +220,9 @@ def main():
     ap.add_argument('--no-fused', action='store_true')
     ap.add_argument('--paths', default='plain,tf32x3', help='comma list of plain, tf32x3, pergate')
     ap.add_argument('--tile-bits', type=int, default=0, help='tile qubits of the tile passes (0 = default 13)')
-    ap.add_argument('--workload', default='34q', choices=['34q', 'batch'],
-                    help='34q: the headline circuit; batch: the 512-circuit uneven batch (secondary line)')
+    ap.add_argument('--workload', default='34q', choices=['34q', 'batch', 'branch42'],
+                    help='34q: the headline circuit; batch: the 512-circuit uneven batch; branch42: the '
+                         '42-qubit cut-branch amplitude task (secondary lines)')
     ap.add_argument('--no-cpu', action='store_true')
     args = ap.parse_args()
 
@@ -204,6 +233,8 @@ def main():
         return run_reference(args, rank, world)
     if args.workload == 'batch':
         return run_batch(args, rank, world)
+    if args.workload == 'branch42':
+        return run_branch(args, rank, world)
 
     import numpy as np
     import torch

@@ -209,6 +209,12 @@ sv_status sv_batch_amplitudes(size_t circuit, const uint64_t *bits, size_t m, do
 /* Release the device memory and graph kept for the last batch. */
 sv_status sv_batch_free(void);
 
+/* Failure-detection self-test, with no GPU fault: runs the batch kernel on a queue whose
+ * single item waits for a pass that is never queued, with a wait limit of limit_ms
+ * (1..10000).  Returns SV_ERR_TIMEOUT when the kernel gave up and reported it as designed
+ * (the expected result); SV_OK would mean the bounded wait did not fire. */
+sv_status sv_selftest_wait_timeout(int limit_ms);
+
 /* --- planning and measurement (host-only helpers) --------------------------------------- */
 
 typedef struct {

@@ -30,8 +30,11 @@ struct BatchItem {
 // Device words of one launch: [0] next item, [1] error flag, then one done counter per cp.
 constexpr int kBatchHeader = 2;
 
+// wait_ns: limit of one dependency wait (after which the error word is set and the CTA
+// leaves); max_grid > 0 caps the number of CTAs.
 cudaError_t launch_batch(float2 *states, const DevPlanView &plan, const BatchCP *cps, const BatchItem *items,
-                         uint64_t n_items, unsigned int *words, int m, cudaStream_t st);
+                         uint64_t n_items, unsigned int *words, int m, cudaStream_t st,
+                         unsigned long long wait_ns = 5000000000ull, int max_grid = 0);
 int batch_block_threads(int m);
 
 // Per-circuit fp64 norm and sum |alpha|^4: chunk c covers [start, start + len) of circuit

@@ -398,6 +398,49 @@ extern "C" sv_status sv_batch_amplitudes(size_t circuit, const uint64_t *bits, s
   return SV_OK;
 }
 
+// A queue whose only item depends on a pass that has no items: its wait can never be
+// met, so the kernel must give up after limit_ms and report it.
+extern "C" sv_status sv_selftest_wait_timeout(int limit_ms) {
+  clear_error();
+  if (limit_ms < 1 || limit_ms > 10000) return fail(SV_ERR_ARG, "sv_selftest_wait_timeout: limit_ms must be 1..10000");
+  std::lock_guard<std::mutex> lock(g_mu);
+  const int m = 13;
+  svp::DevPass dp;
+  std::memset(&dp, 0, sizeof(dp));
+  dp.m = m;
+  dp.c = 4;
+  dp.n = m;
+  for (int i = 0; i < m; ++i) dp.tq[i] = (uint8_t)i;
+  const svk::BatchCP cps[2] = {{0, 0, svk::kNoPrev, 1, 0}, {0, 0, 0, 1, 0}};
+  const svk::BatchItem item = {1, 0};  // waits for cp 0, whose tile is never queued
+  DeviceBuf state, plan, dcps, ditems, words;
+  sv_status st;
+  if ((st = state.alloc(sizeof(float2) << m)) != SV_OK) return st;
+  if ((st = plan.alloc(1024)) != SV_OK) return st;
+  if ((st = dcps.alloc(sizeof(cps))) != SV_OK) return st;
+  if ((st = ditems.alloc(sizeof(item))) != SV_OK) return st;
+  if ((st = words.alloc((svk::kBatchHeader + 2) * sizeof(unsigned int))) != SV_OK) return st;
+  cudaError_t e = cudaMemcpy(plan.p, &dp, sizeof(dp), cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) e = cudaMemcpy(dcps.p, cps, sizeof(cps), cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) e = cudaMemcpy(ditems.p, &item, sizeof(item), cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) e = cudaMemset(words.p, 0, (svk::kBatchHeader + 2) * sizeof(unsigned int));
+  svk::DevPlanView view{};
+  view.passes = static_cast<const svp::DevPass *>(plan.p);
+  view.stages = reinterpret_cast<const svp::DevStage *>(static_cast<char *>(plan.p) + 512);
+  view.ops = nullptr;
+  view.mats = nullptr;
+  view.err = nullptr;
+  if (e == cudaSuccess)
+    e = svk::launch_batch(static_cast<float2 *>(state.p), view, static_cast<const svk::BatchCP *>(dcps.p),
+                          static_cast<const svk::BatchItem *>(ditems.p), 1, static_cast<unsigned int *>(words.p), m, 0,
+                          (unsigned long long)limit_ms * 1000000ull, 1);
+  unsigned int hw[svk::kBatchHeader] = {0, 0};
+  if (e == cudaSuccess) e = cudaMemcpy(hw, words.p, sizeof(hw), cudaMemcpyDeviceToHost);
+  if (e != cudaSuccess) return cuda_fail(e, "sv_selftest_wait_timeout");
+  if (hw[1] != 0) return fail(SV_ERR_TIMEOUT, "dependency wait gave up as designed");
+  return SV_OK;
+}
+
 extern "C" sv_status sv_batch_free(void) {
   clear_error();
   std::lock_guard<std::mutex> lock(g_mu);

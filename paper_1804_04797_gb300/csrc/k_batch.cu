@@ -17,8 +17,6 @@ namespace {
 
 using namespace tile;
 
-constexpr unsigned long long kDepWaitNs = 5000000000ull;  // 5 s
-
 __device__ __forceinline__ unsigned long long now_ns() {
   unsigned long long t;
   asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
@@ -33,7 +31,8 @@ __device__ __forceinline__ unsigned int load_acquire(const unsigned int *p) {
 
 __global__ void __launch_bounds__(256, 2)
 batch_kernel(float2 *__restrict__ states, DevPlanView plan, const BatchCP *__restrict__ cps,
-             const BatchItem *__restrict__ items, uint64_t n_items, unsigned int *words) {
+             const BatchItem *__restrict__ items, uint64_t n_items, unsigned int *words,
+             unsigned long long wait_ns) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   float2 *tile = reinterpret_cast<float2 *>(smem_raw);
   __shared__ DevPass P;
@@ -65,7 +64,7 @@ batch_kernel(float2 *__restrict__ states, DevPlanView plan, const BatchCP *__res
       if (load_acquire(&done[cp.prev]) < need) {
         const unsigned long long t0 = now_ns();
         while (load_acquire(&done[cp.prev]) < need) {
-          if (now_ns() - t0 > kDepWaitNs) {
+          if (now_ns() - t0 > wait_ns) {
             atomicExch(&words[1], 1u);
             s_stop = 1;
             break;
@@ -126,7 +125,8 @@ __global__ void batch_stats_final(const double *partials, const int *chunk_begin
 int batch_block_threads(int m) { return 1 << (m - kR); }
 
 cudaError_t launch_batch(float2 *states, const DevPlanView &plan, const BatchCP *cps, const BatchItem *items,
-                         uint64_t n_items, unsigned int *words, int m, cudaStream_t st) {
+                         uint64_t n_items, unsigned int *words, int m, cudaStream_t st,
+                         unsigned long long wait_ns, int max_grid) {
   static bool configured = false;
   static int per_sm = 1;
   const size_t smem = sizeof(float2) << svp::kMaxTileBits;
@@ -141,8 +141,9 @@ cudaError_t launch_batch(float2 *states, const DevPlanView &plan, const BatchCP 
   const int threads = batch_block_threads(m);
   // smaller tiles use fewer threads: more CTAs fit, but the occupancy query for 256
   // threads is a safe lower bound
-  const int grid = device_sm_count() * per_sm * (256 / threads);
-  batch_kernel<<<grid, threads, sizeof(float2) << m, st>>>(states, plan, cps, items, n_items, words);
+  int grid = device_sm_count() * per_sm * (256 / threads);
+  if (max_grid > 0 && grid > max_grid) grid = max_grid;
+  batch_kernel<<<grid, threads, sizeof(float2) << m, st>>>(states, plan, cps, items, n_items, words, wait_ns);
   return cudaGetLastError();
 }
 

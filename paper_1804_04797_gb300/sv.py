@@ -88,6 +88,7 @@ def lib():
         'sv_apply_batch': ([vp, c_size_t, P(sv_options), vp], c_int),
         'sv_batch_amplitudes': ([c_size_t, vp, c_size_t, vp], c_int),
         'sv_batch_free': ([], c_int),
+        'sv_selftest_wait_timeout': ([c_int], c_int),
         'sv_norm_noalloc': ([vp, c_int, vp, P(c_double), P(c_double)], c_int),
         'sv_plan': ([c_int, vp, c_size_t, P(sv_options), c_int, P(sv_plan_summary), vp, vp, vp,
                      c_size_t], c_int),
@@ -244,6 +245,11 @@ def sv_batch_amplitudes(circuit, bits):
     out = np.zeros(2 * b.size, dtype=np.float64)
     _check(lib().sv_batch_amplitudes(circuit, b.ctypes.data, b.size, out.ctypes.data))
     return out.view(np.complex128)
+
+
+def sv_selftest_wait_timeout(limit_ms):
+    """Raw status of the bounded-wait self-test (SV_ERR_TIMEOUT expected)."""
+    return lib().sv_selftest_wait_timeout(int(limit_ms))
 
 
 def sv_batch_free():

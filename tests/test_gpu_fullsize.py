@@ -1,0 +1,99 @@
+"""Full-size configurations on the GPU.
+
+30 qubits (5x6, depth 20): the whole complex64 state against the complex128 C oracle
+(16 GiB on the host).  34 qubits (6x6 minus two corners, depth 30): the oracle would need
+256 GiB, more than the host has, so the state is checked by properties that hold at any
+size: norm, the Porter-Thomas statistic N * sum p^2 ~ 2, the inverse circuit returning
+|0...0>, and agreement of the plain and tensor-core paths on sampled amplitudes.  42 qubits
+(6x7, depth 10, cut between rows 2 and 3, t = 10): the cut-branch amplitudes against the
+oracle's own split-and-sum (complex128, all 1024 branches on the host cores).
+"""
+import numpy as np
+import pytest
+
+from oracle import circuit as oc
+from oracle import csim
+from paper_1804_04797_gb300 import inputs
+from paper_1804_04797_gb300 import sv
+
+pytestmark = [pytest.mark.gpu, pytest.mark.slow]
+
+REL_L2 = 1e-5
+NORM_TOL = 1e-6
+
+
+def rel_l2(a, b):
+    a = np.asarray(a, dtype=np.complex128)
+    b = np.asarray(b, dtype=np.complex128)
+    return float(np.linalg.norm(a - b) / np.linalg.norm(b))
+
+
+def test_30q_depth20_full_state_matches_oracle():
+    lat = inputs.C30
+    n, gates = oc.generate(lat.rows, lat.cols, lat.removed_mask, lat.depth, lat.seed)
+    want = csim.run(n, gates)
+    g = sv.sv_generate_circuit(lat)
+    for prec in (sv.SV_PREC_PLAIN, sv.SV_PREC_TF32X3):
+        h = sv.sv_create(n, sv.options(precision=prec))
+        try:
+            sv.sv_apply_circuit(h, g)
+            norm2, sp2 = sv.sv_norm(h)
+            psi = sv.sv_copy_state(h, n)
+        finally:
+            sv.sv_destroy(h)
+        diff = np.linalg.norm(psi.astype(np.complex128) - want)
+        assert diff <= REL_L2, (prec, diff)          # the oracle state has norm 1
+        assert abs(norm2 - 1) <= NORM_TOL
+        assert 1.9 < (1 << n) * sp2 < 2.1
+        del psi
+
+
+def test_34q_depth30_invariants():
+    lat = inputs.C34
+    n = lat.n_qubits
+    g = sv.sv_generate_circuit(lat)
+    bits = np.array(inputs.sample_indices(n, 1024, seed=1), dtype=np.uint64)
+    h = sv.sv_create(n)
+    try:
+        sv.sv_apply_circuit(h, g)
+        norm2, sp2 = sv.sv_norm(h)
+        assert abs(norm2 - 1) <= NORM_TOL
+        assert abs((1 << n) * sp2 - 2.0) <= 0.1
+        plain = sv.sv_get_amplitudes(h, bits)
+        sv.sv_set_options(h, sv.options(precision=sv.SV_PREC_TF32X3))
+        sv.sv_reset(h)
+        sv.sv_apply_circuit(h, g)
+        fused = sv.sv_get_amplitudes(h, bits)
+        n2f, _ = sv.sv_norm(h)
+        assert abs(n2f - 1) <= NORM_TOL
+        assert rel_l2(fused, plain) <= REL_L2
+        # U then U^dagger returns |0...0>
+        sv.sv_apply_circuit_inverse(h, g)
+        a0 = sv.sv_get_amplitudes(h, [0])[0]
+        assert abs(a0 - 1) <= 1e-5
+    finally:
+        sv.sv_destroy(h)
+
+
+def test_42q_cut_branch_amplitudes_match_oracle():
+    lat = inputs.C42
+    n, gates = oc.generate(lat.rows, lat.cols, lat.removed_mask, lat.depth, lat.seed)
+    assert len(oc.cut_crossings(gates, inputs.C42_HALF_A)) == 10
+    bits = inputs.bitstrings(n, 64, seed=2)
+    want = csim.branch_amplitudes(n, gates, inputs.C42_HALF_A, bits)
+    for prec in (sv.SV_PREC_PLAIN, sv.SV_PREC_TF32X3):
+        got = sv.sv_branch_amplitudes(lat, inputs.C42_HALF_A, bits, sv.options(precision=prec))
+        assert rel_l2(got, want) <= REL_L2, prec
+
+
+def test_bounded_dependency_wait_reports_timeout():
+    """The batch kernel's dependency wait gives up after its limit and reports it (no
+    hang, no fault); the context stays usable afterwards."""
+    assert sv.sv_selftest_wait_timeout(200) == sv.SV_ERR_TIMEOUT
+    h = sv.sv_create(14)
+    try:
+        sv.sv_apply_circuit(h, sv.sv_generate_circuit(inputs.lattice_for(2, 7, 8, seed=3)))
+        n2, _ = sv.sv_norm(h)
+        assert abs(n2 - 1) <= NORM_TOL
+    finally:
+        sv.sv_destroy(h)
