@@ -193,7 +193,8 @@ sv_status upload_plan(sv_state *s, const svp::Plan &P, svk::DevPlanView *view) {
   const size_t o_stage = align(o_pass + P.passes.size() * sizeof(svp::DevPass));
   const size_t o_op = align(o_stage + P.stages.size() * sizeof(svp::DevStage));
   const size_t o_mat = align(o_op + P.ops.size() * sizeof(svp::DevOp));
-  const size_t o_err = align(o_mat + P.mats.size() * sizeof(float));
+  const size_t o_gt = align(o_mat + P.mats.size() * sizeof(float));
+  const size_t o_err = align(o_gt + P.gtab.size() * sizeof(svp::DevGroupEntry));
   const size_t total = o_err + 256;
   sv_status st = ensure_device_buffer(&s->d_plan, &s->d_plan_cap, total);
   if (st != SV_OK) return st;
@@ -202,6 +203,8 @@ sv_status upload_plan(sv_state *s, const svp::Plan &P, svk::DevPlanView *view) {
   if (!P.stages.empty()) std::memcpy(&s->h_plan[o_stage], P.stages.data(), P.stages.size() * sizeof(svp::DevStage));
   if (!P.ops.empty()) std::memcpy(&s->h_plan[o_op], P.ops.data(), P.ops.size() * sizeof(svp::DevOp));
   if (!P.mats.empty()) std::memcpy(&s->h_plan[o_mat], P.mats.data(), P.mats.size() * sizeof(float));
+  if (!P.gtab.empty())
+    std::memcpy(&s->h_plan[o_gt], P.gtab.data(), P.gtab.size() * sizeof(svp::DevGroupEntry));
   cudaError_t e = cudaMemcpyAsync(s->d_plan, s->h_plan.data(), total, cudaMemcpyHostToDevice, s->stream);
   if (e != cudaSuccess) return cuda_fail(e, "plan upload");
   if (s->prof) s->h2d += (double)total;
@@ -211,6 +214,7 @@ sv_status upload_plan(sv_state *s, const svp::Plan &P, svk::DevPlanView *view) {
   view->ops = reinterpret_cast<const svp::DevOp *>(d + o_op);
   view->mats = reinterpret_cast<const float *>(d + o_mat);
   view->err = reinterpret_cast<int *>(d + o_err);
+  view->gtab = reinterpret_cast<const svp::DevGroupEntry *>(d + o_gt);
   return SV_OK;
 }
 

@@ -106,6 +106,7 @@ sv_status build_batch(const sv_lattice *circs, size_t count, int m_req, Batch *B
   std::vector<svp::DevPass> passes;
   std::vector<svp::DevStage> stages;
   std::vector<svp::DevOp> ops;
+  std::vector<svp::DevGroupEntry> gtab;
   std::vector<std::vector<uint32_t>> circ_passes(count);
   std::vector<uint64_t> state_off(count);
   uint64_t total_amps = 0;
@@ -119,6 +120,7 @@ sv_status build_batch(const sv_lattice *circs, size_t count, int m_req, Batch *B
       stages.push_back(ds);
     }
     for (const svp::DevOp &o : P.ops) ops.push_back(o);
+    gtab.insert(gtab.end(), P.gtab.begin(), P.gtab.end());
     for (svp::DevPass dp : P.passes) {
       dp.stage_begin += sb;
       circ_passes[i].push_back((uint32_t)passes.size());
@@ -167,7 +169,8 @@ sv_status build_batch(const sv_lattice *circs, size_t count, int m_req, Batch *B
   auto align = [](size_t x) { return (x + 255) & ~(size_t)255; };
   const size_t o_stage = align(passes.size() * sizeof(svp::DevPass));
   const size_t o_op = o_stage + align(stages.size() * sizeof(svp::DevStage));
-  const size_t o_err = o_op + align(ops.size() * sizeof(svp::DevOp));
+  const size_t o_gt = o_op + align(ops.size() * sizeof(svp::DevOp));
+  const size_t o_err = o_gt + align(gtab.size() * sizeof(svp::DevGroupEntry));
   const size_t plan_bytes = o_err + 256;
   sv_status st;
   if ((st = B->states.alloc(total_amps * sizeof(float2))) != SV_OK) return st;
@@ -184,6 +187,7 @@ sv_status build_batch(const sv_lattice *circs, size_t count, int m_req, Batch *B
   std::memcpy(hp.data(), passes.data(), passes.size() * sizeof(svp::DevPass));
   std::memcpy(hp.data() + o_stage, stages.data(), stages.size() * sizeof(svp::DevStage));
   std::memcpy(hp.data() + o_op, ops.data(), ops.size() * sizeof(svp::DevOp));
+  std::memcpy(hp.data() + o_gt, gtab.data(), gtab.size() * sizeof(svp::DevGroupEntry));
   cudaError_t e = cudaMemcpy(B->plan.p, hp.data(), plan_bytes, cudaMemcpyHostToDevice);
   if (e == cudaSuccess && !cps.empty()) e = cudaMemcpy(B->cps.p, cps.data(), cps.size() * sizeof(svk::BatchCP), cudaMemcpyHostToDevice);
   if (e == cudaSuccess && !items.empty())
@@ -198,6 +202,7 @@ sv_status build_batch(const sv_lattice *circs, size_t count, int m_req, Batch *B
   B->view.ops = reinterpret_cast<const svp::DevOp *>(d + o_op);
   B->view.mats = reinterpret_cast<const float *>(d + o_err);
   B->view.err = reinterpret_cast<int *>(d + o_err);
+  B->view.gtab = reinterpret_cast<const svp::DevGroupEntry *>(d + o_gt);
   return SV_OK;
 }
 

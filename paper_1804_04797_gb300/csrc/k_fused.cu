@@ -243,10 +243,11 @@ fused_pass_kernel(float2 *__restrict__ psi, DevPlanView plan, int pass_index, ui
     double norm_in = 0.0;
     int q = 0;  // MMA stage index within this tile
     for (int s = 0; s < P.stage_count; ++s) {
-      const DevStage &st = plan.stages[P.stage_begin + s];
+      const uint32_t si = P.stage_begin + s;
+      const DevStage &st = plan.stages[si];
       uint32_t L0;
       uint64_t G0;
-      group_base(st, P, tid, base, &L0, &G0);
+      group_base(plan, si, tid, base, &L0, &G0);
       float2 v[kE];
       load_group(tile, st, L0, v);
       if (keep_norm && s == 0) norm_in = cta_sum((double)row_norm2(v), red);
@@ -348,7 +349,7 @@ fused_pass_kernel(float2 *__restrict__ psi, DevPlanView plan, int pass_index, ui
         }
       }
       asm volatile("" ::: "memory");
-      group_base(st, P, tid, base, &L0, &G0);
+      group_base(plan, si, tid, base, &L0, &G0);
       store_group(tile, st, L0, v);
       __syncthreads();
       if (abort_flag) break;

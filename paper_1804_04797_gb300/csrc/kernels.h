@@ -20,6 +20,7 @@ struct DevPlanView {
   const svp::DevOp *ops;
   const float *mats;
   int *err;  // error word of the plan (0 = ok; set by a kernel whose bounded wait gave up)
+  const svp::DevGroupEntry *gtab;  // 32 group-addressing entries per stage
 };
 
 // K0: write |0..0> (uniform == false) or the uniform 2^{-n/2} state.  Write-only.

@@ -249,6 +249,19 @@ bool build_plan(int n, const std::vector<Gate> &gates, const Options &opt, bool 
       for (int b = 0; b < m; ++b)
         if (std::find(rb.begin(), rb.end(), b) == rb.end()) nonr.push_back(b);
       order_group_bits(m, nonr, ds.nonr);
+      for (int half = 0; half < 2; ++half) {
+        for (int v = 0; v < 16; ++v) {
+          DevGroupEntry ge;
+          std::memset(&ge, 0, sizeof(ge));
+          for (int i = 0; i < 4; ++i) {
+            const int gi = 4 * half + i;
+            if (!((v >> i) & 1) || gi >= m - kMaxReg) continue;
+            ge.L |= 1u << ds.nonr[gi];
+            ge.G |= 1ull << dp.tq[ds.nonr[gi]];
+          }
+          P.gtab.push_back(ge);
+        }
+      }
       ds.op_begin = (uint32_t)P.ops.size();
       ds.diag_only = inner.empty() ? 1 : 0;
       auto reg_of = [&](int q) -> int {
@@ -263,6 +276,23 @@ bool build_plan(int n, const std::vector<Gate> &gates, const Options &opt, bool 
         std::memset(&o, 0, sizeof(o));
         o.act = act; o.j = (uint8_t)(j < 0 ? 0 : j); o.k = (uint8_t)(k < 0 ? 0 : k);
         o.arg = (uint8_t)arg; o.cmask = cm; o.cval = cv;
+        switch (act) {
+          case A_H: o.code = C_PAIR + 0 + o.j; break;
+          case A_SX: o.code = C_PAIR + 5 + o.j; break;
+          case A_SY: o.code = C_PAIR + 10 + o.j; break;
+          case A_SXDG: o.code = C_PAIR + 15 + o.j; break;
+          case A_SYDG: o.code = C_PAIR + 20 + o.j; break;
+          case A_T: o.code = C_DIAG + 0 + o.j; break;
+          case A_TDG: o.code = C_DIAG + 5 + o.j; break;
+          case A_Z: o.code = C_DIAG + 10 + o.j; break;
+          case A_P0: o.code = C_DIAG + 15 + o.j; break;
+          case A_P1: o.code = C_DIAG + 20 + o.j; break;
+          case A_CZ: o.code = C_CZ + 5 * o.j + o.k; break;
+          case A_PEQ: o.code = C_PEQ + 5 * o.j + o.k; break;
+          case A_PHASE: o.code = C_PHASE; break;
+          case A_ZERO: o.code = C_ZERO; break;
+          default: o.code = C_U + o.j; break;
+        }
         P.ops.push_back(o);
       };
       auto lower = [&](int gi) {

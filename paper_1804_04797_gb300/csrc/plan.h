@@ -52,8 +52,30 @@ enum Act : uint8_t {
 // register bits of the stage (the other tile qubits and the tile's fixed qubits).
 struct DevOp {
   uint8_t act, j, k, arg;
-  uint32_t pad;
+  uint8_t code;  // flat dispatch code of the plain kernels (see op_code)
+  uint8_t pad[3];
   uint64_t cmask, cval;
+};
+
+// Flat dispatch codes: one switch in the kernel selects both the action and the
+// register bit(s), so each op costs one indirect branch.
+enum Code : uint8_t {
+  C_PAIR = 0,     // + 5*g + j, g in {H, SX, SY, SXDG, SYDG}       (0..24)
+  C_DIAG = 25,    // + 5*d + j, d in {T, TDG, Z, P0, P1}            (25..49)
+  C_CZ = 50,      // + 5*j + k                                       (50..74)
+  C_PEQ = 75,     // + 5*j + k                                       (75..99)
+  C_PHASE = 100,  // scalar phase w^arg of the whole group (accumulated, applied once)
+  C_ZERO = 101,   // the whole group becomes zero
+  C_U = 102,      // + j, general 2x2                                 (102..106)
+  C_COUNT = 107
+};
+
+// Stage group addressing: group index g of a thread -> (tile-local index L0, global
+// index offset G0) of its element 0 = entry[g & 15] | entry[16 + (g >> 4)].
+struct DevGroupEntry {
+  uint32_t L;
+  uint32_t pad;
+  uint64_t G;
 };
 static_assert(sizeof(DevOp) == 24, "DevOp layout");
 
@@ -104,6 +126,7 @@ struct Plan {
   std::vector<DevStage> stages;
   std::vector<DevOp> ops;
   std::vector<float> mats;          // 8 floats per A_U matrix (re/im of a,b,c,d)
+  std::vector<DevGroupEntry> gtab;  // 32 entries per stage
   std::vector<int32_t> order;       // executed gate index, in execution order
   std::vector<int32_t> pass_of;     // pass of each executed gate
   std::vector<std::vector<int>> stage_gates;  // per stage: gate indices (inner, in order)

@@ -189,57 +189,121 @@ __device__ __forceinline__ void general1(float2 (&v)[kE], const float *u) {
   }
 }
 
-__device__ __forceinline__ void apply_op(float2 (&v)[kE], const DevOp &op, const float *mats) {
+// One op by its flat code (one indirect branch).  Scalar phases and zeroing of the whole
+// group commute with every other op and are only recorded (ph, zero) for apply_ops.
+__device__ __forceinline__ void apply_op(float2 (&v)[kE], const DevOp &op, const float *mats, int &ph,
+                                         bool &zero) {
   using namespace svp;
-  switch (op.act) {
-    case A_H: pairs_j<GH>(v, op.j); break;
-    case A_SX: pairs_j<GSX>(v, op.j); break;
-    case A_SY: pairs_j<GSY>(v, op.j); break;
-    case A_SXDG: pairs_j<GSXDG>(v, op.j); break;
-    case A_SYDG: pairs_j<GSYDG>(v, op.j); break;
-    case A_T: diag1_j<DT, 1>(v, op.j); break;
-    case A_TDG: diag1_j<DTDG, 1>(v, op.j); break;
-    case A_Z: diag1_j<DNEG, 1>(v, op.j); break;
-    case A_P0: diag1_j<DZERO, 1>(v, op.j); break;
-    case A_P1: diag1_j<DZERO, 0>(v, op.j); break;
-    case A_CZ: diag2_jk<false>(v, op.j, op.k); break;
-    case A_PEQ: diag2_jk<true>(v, op.j, op.k); break;
-    case A_PHASE: phase_all(v, op.arg); break;
-    case A_ZERO:
-#pragma unroll
-      for (int e = 0; e < kE; ++e) DZERO::f(v[e]);
-      break;
-    case A_U: {
-      const float *u = mats + 8 * (op.arg | (op.k << 8));
-      switch (op.j) {
-        case 0: general1<0>(v, u); break;
-        case 1: general1<1>(v, u); break;
-        case 2: general1<2>(v, u); break;
-        case 3: general1<3>(v, u); break;
-        default: general1<4>(v, u); break;
-      }
-    } break;
+  switch (op.code) {
+    case C_PAIR + 0: pairs<GH, 0>(v); break;
+    case C_PAIR + 1: pairs<GH, 1>(v); break;
+    case C_PAIR + 2: pairs<GH, 2>(v); break;
+    case C_PAIR + 3: pairs<GH, 3>(v); break;
+    case C_PAIR + 4: pairs<GH, 4>(v); break;
+    case C_PAIR + 5: pairs<GSX, 0>(v); break;
+    case C_PAIR + 6: pairs<GSX, 1>(v); break;
+    case C_PAIR + 7: pairs<GSX, 2>(v); break;
+    case C_PAIR + 8: pairs<GSX, 3>(v); break;
+    case C_PAIR + 9: pairs<GSX, 4>(v); break;
+    case C_PAIR + 10: pairs<GSY, 0>(v); break;
+    case C_PAIR + 11: pairs<GSY, 1>(v); break;
+    case C_PAIR + 12: pairs<GSY, 2>(v); break;
+    case C_PAIR + 13: pairs<GSY, 3>(v); break;
+    case C_PAIR + 14: pairs<GSY, 4>(v); break;
+    case C_PAIR + 15: pairs<GSXDG, 0>(v); break;
+    case C_PAIR + 16: pairs<GSXDG, 1>(v); break;
+    case C_PAIR + 17: pairs<GSXDG, 2>(v); break;
+    case C_PAIR + 18: pairs<GSXDG, 3>(v); break;
+    case C_PAIR + 19: pairs<GSXDG, 4>(v); break;
+    case C_PAIR + 20: pairs<GSYDG, 0>(v); break;
+    case C_PAIR + 21: pairs<GSYDG, 1>(v); break;
+    case C_PAIR + 22: pairs<GSYDG, 2>(v); break;
+    case C_PAIR + 23: pairs<GSYDG, 3>(v); break;
+    case C_PAIR + 24: pairs<GSYDG, 4>(v); break;
+    case C_DIAG + 0: diag1<DT, 0, 1>(v); break;
+    case C_DIAG + 1: diag1<DT, 1, 1>(v); break;
+    case C_DIAG + 2: diag1<DT, 2, 1>(v); break;
+    case C_DIAG + 3: diag1<DT, 3, 1>(v); break;
+    case C_DIAG + 4: diag1<DT, 4, 1>(v); break;
+    case C_DIAG + 5: diag1<DTDG, 0, 1>(v); break;
+    case C_DIAG + 6: diag1<DTDG, 1, 1>(v); break;
+    case C_DIAG + 7: diag1<DTDG, 2, 1>(v); break;
+    case C_DIAG + 8: diag1<DTDG, 3, 1>(v); break;
+    case C_DIAG + 9: diag1<DTDG, 4, 1>(v); break;
+    case C_DIAG + 10: diag1<DNEG, 0, 1>(v); break;
+    case C_DIAG + 11: diag1<DNEG, 1, 1>(v); break;
+    case C_DIAG + 12: diag1<DNEG, 2, 1>(v); break;
+    case C_DIAG + 13: diag1<DNEG, 3, 1>(v); break;
+    case C_DIAG + 14: diag1<DNEG, 4, 1>(v); break;
+    case C_DIAG + 15: diag1<DZERO, 0, 1>(v); break;
+    case C_DIAG + 16: diag1<DZERO, 1, 1>(v); break;
+    case C_DIAG + 17: diag1<DZERO, 2, 1>(v); break;
+    case C_DIAG + 18: diag1<DZERO, 3, 1>(v); break;
+    case C_DIAG + 19: diag1<DZERO, 4, 1>(v); break;
+    case C_DIAG + 20: diag1<DZERO, 0, 0>(v); break;
+    case C_DIAG + 21: diag1<DZERO, 1, 0>(v); break;
+    case C_DIAG + 22: diag1<DZERO, 2, 0>(v); break;
+    case C_DIAG + 23: diag1<DZERO, 3, 0>(v); break;
+    case C_DIAG + 24: diag1<DZERO, 4, 0>(v); break;
+    case C_CZ + 1: diag2<0, 1, false>(v); break;
+    case C_PEQ + 1: diag2<0, 1, true>(v); break;
+    case C_CZ + 2: diag2<0, 2, false>(v); break;
+    case C_PEQ + 2: diag2<0, 2, true>(v); break;
+    case C_CZ + 3: diag2<0, 3, false>(v); break;
+    case C_PEQ + 3: diag2<0, 3, true>(v); break;
+    case C_CZ + 4: diag2<0, 4, false>(v); break;
+    case C_PEQ + 4: diag2<0, 4, true>(v); break;
+    case C_CZ + 5: diag2<1, 0, false>(v); break;
+    case C_PEQ + 5: diag2<1, 0, true>(v); break;
+    case C_CZ + 7: diag2<1, 2, false>(v); break;
+    case C_PEQ + 7: diag2<1, 2, true>(v); break;
+    case C_CZ + 8: diag2<1, 3, false>(v); break;
+    case C_PEQ + 8: diag2<1, 3, true>(v); break;
+    case C_CZ + 9: diag2<1, 4, false>(v); break;
+    case C_PEQ + 9: diag2<1, 4, true>(v); break;
+    case C_CZ + 10: diag2<2, 0, false>(v); break;
+    case C_PEQ + 10: diag2<2, 0, true>(v); break;
+    case C_CZ + 11: diag2<2, 1, false>(v); break;
+    case C_PEQ + 11: diag2<2, 1, true>(v); break;
+    case C_CZ + 13: diag2<2, 3, false>(v); break;
+    case C_PEQ + 13: diag2<2, 3, true>(v); break;
+    case C_CZ + 14: diag2<2, 4, false>(v); break;
+    case C_PEQ + 14: diag2<2, 4, true>(v); break;
+    case C_CZ + 15: diag2<3, 0, false>(v); break;
+    case C_PEQ + 15: diag2<3, 0, true>(v); break;
+    case C_CZ + 16: diag2<3, 1, false>(v); break;
+    case C_PEQ + 16: diag2<3, 1, true>(v); break;
+    case C_CZ + 17: diag2<3, 2, false>(v); break;
+    case C_PEQ + 17: diag2<3, 2, true>(v); break;
+    case C_CZ + 19: diag2<3, 4, false>(v); break;
+    case C_PEQ + 19: diag2<3, 4, true>(v); break;
+    case C_CZ + 20: diag2<4, 0, false>(v); break;
+    case C_PEQ + 20: diag2<4, 0, true>(v); break;
+    case C_CZ + 21: diag2<4, 1, false>(v); break;
+    case C_PEQ + 21: diag2<4, 1, true>(v); break;
+    case C_CZ + 22: diag2<4, 2, false>(v); break;
+    case C_PEQ + 22: diag2<4, 2, true>(v); break;
+    case C_CZ + 23: diag2<4, 3, false>(v); break;
+    case C_PEQ + 23: diag2<4, 3, true>(v); break;
+    case C_U + 0: general1<0>(v, mats + 8 * (op.arg | (op.k << 8))); break;
+    case C_U + 1: general1<1>(v, mats + 8 * (op.arg | (op.k << 8))); break;
+    case C_U + 2: general1<2>(v, mats + 8 * (op.arg | (op.k << 8))); break;
+    case C_U + 3: general1<3>(v, mats + 8 * (op.arg | (op.k << 8))); break;
+    case C_U + 4: general1<4>(v, mats + 8 * (op.arg | (op.k << 8))); break;
+    case C_PHASE: ph += op.arg; break;
+    case C_ZERO: zero = true; break;
     default: break;
   }
 }
 
-
-// Global index of element 0 of group `g` and its shared-memory (swizzled) base, for a
-// stage whose group bits are st.nonr[0 .. m-kR).
-__device__ __forceinline__ void group_base(const DevStage &st, const DevPass &P, int g, uint64_t base,
+// Global index of element 0 of group `g` of stage `si` and its tile-local index, from
+// the stage's two 16-entry tables.
+__device__ __forceinline__ void group_base(const DevPlanView &plan, uint32_t si, int g, uint64_t base,
                                            uint32_t *L0, uint64_t *G0) {
-  uint32_t l = 0;
-  uint64_t gg = base;
-  const int ng = P.m - kR;
-  for (int i = 0; i < ng; ++i) {
-    if ((g >> i) & 1) {
-      const int b = st.nonr[i];
-      l |= 1u << b;
-      gg |= 1ull << P.tq[b];
-    }
-  }
-  *L0 = l;
-  *G0 = gg;
+  const svp::DevGroupEntry lo = plan.gtab[32 * si + (g & 15)];
+  const svp::DevGroupEntry hi = plan.gtab[32 * si + 16 + ((g >> 4) & 15)];
+  *L0 = lo.L | hi.L;
+  *G0 = base | lo.G | hi.G;
 }
 
 __device__ __forceinline__ void load_group(const float2 *tile, const DevStage &st, uint32_t L0, float2 (&v)[kE]) {
@@ -272,12 +336,23 @@ __device__ __forceinline__ void store_group(float2 *tile, const DevStage &st, ui
   }
 }
 
-__device__ __forceinline__ void apply_ops(float2 (&v)[kE], const DevOp *ops, int begin, int count, uint64_t G0,
-                                          const float *mats) {
-  for (int o = begin; o < begin + count; ++o) {
-    const DevOp op = ops[o];
-    if ((G0 & op.cmask) != op.cval) continue;
-    apply_op(v, op, mats);
+__device__ __forceinline__ void apply_ops(float2 (&v)[kE], const DevOp *ops, uint32_t begin, int count,
+                                          uint64_t G0, const float *mats) {
+  int ph = 0;
+  bool zero = false;
+  if (count > 0) {
+    DevOp op = ops[begin];
+    for (int o = 0; o < count; ++o) {
+      const DevOp nxt = ops[begin + (o + 1 < count ? o + 1 : o)];  // prefetch
+      if ((G0 & op.cmask) == op.cval) apply_op(v, op, mats, ph, zero);
+      op = nxt;
+    }
+  }
+  if (zero) {
+#pragma unroll
+    for (int e = 0; e < kE; ++e) DZERO::f(v[e]);
+  } else if (ph & 7) {
+    phase_all(v, ph & 7);
   }
 }
 
@@ -368,16 +443,17 @@ __device__ __forceinline__ void process_tile_plain(float2 *__restrict__ psi, con
   load_tile<kL2Only>(psi, tile, P, chunk_off, base);
   __syncthreads();
   for (int s = 0; s < P.stage_count; ++s) {
-    const DevStage &st = plan.stages[P.stage_begin + s];
+    const uint32_t si = P.stage_begin + s;
+    const DevStage &st = plan.stages[si];
     uint32_t L0;
     uint64_t G0;
-    group_base(st, P, tid, base, &L0, &G0);
+    group_base(plan, si, tid, base, &L0, &G0);
     float2 v[kE];
     load_group(tile, st, L0, v);
     apply_ops(v, plan.ops, st.op_begin, st.op_count, G0, plan.mats);
     // Recompute the addresses rather than keeping 32 of them live across the ops.
     asm volatile("" ::: "memory");
-    group_base(st, P, tid, base, &L0, &G0);
+    group_base(plan, si, tid, base, &L0, &G0);
     store_group(tile, st, L0, v);
     __syncthreads();
   }
