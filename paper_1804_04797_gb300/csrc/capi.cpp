@@ -47,8 +47,9 @@ svp::Options plan_options(const sv_options &o) {
   svp::Options p;
   p.m = o.tile_bits > 0 ? o.tile_bits : 13;
   p.c = o.low_bits > 0 ? o.low_bits : 4;
-  p.r = o.fuse_k > 0 ? o.fuse_k : 5;
   p.fused = o.precision == SV_PREC_TF32X3;
+  p.rk = 5;  // register qubits per thread of the tile kernels
+  p.r = std::min(o.fuse_k > 0 ? o.fuse_k : p.rk, p.rk);
   return p;
 }
 
@@ -249,7 +250,9 @@ sv_status apply_gates(sv_state *s, const std::vector<svp::Gate> &g) {
   const char *err = nullptr;
   svp::Options po = plan_options(s->opts);
   // the tensor-core kernel takes 12- or 13-qubit tiles; smaller states use the plain one
-  if (po.fused && std::min(po.m, s->n) < 12) po.fused = false;
+  if (po.fused && std::min(po.m, s->n) < 12) {
+    po.fused = false;
+  }
   if (!svp::build_plan(s->n, g, po, s->fresh, &P, &err)) return fail(SV_ERR_ARG, err ? err : "planning failed");
   if (po.fused && (st = build_stage_mats(&P, g, std::min(po.r, std::min(po.m, s->n)))) != SV_OK) return st;
   if (po.fused)

@@ -102,6 +102,7 @@ sv_status build_batch(const sv_lattice *circs, size_t count, int m_req, Batch *B
   po.m = m;
   po.c = 4;
   po.r = 5;
+  po.rk = 5;
   // combined plan
   std::vector<svp::DevPass> passes;
   std::vector<svp::DevStage> stages;

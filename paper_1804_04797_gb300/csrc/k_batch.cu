@@ -10,6 +10,7 @@
 #include <cuda_runtime.h>
 
 #include "batch.h"
+#define SV_TILE_R 5
 #include "tile_common.cuh"
 
 namespace svk {

@@ -29,6 +29,7 @@
 #include "kernels.h"
 #include "capi_util.h"
 #include "state.h"
+#define SV_TILE_R 5
 #include "tile_common.cuh"
 
 namespace svk {

@@ -15,6 +15,7 @@
 #include <cuda_runtime.h>
 
 #include "kernels.h"
+#define SV_TILE_R 5
 #include "tile_common.cuh"
 
 namespace svk {
@@ -22,7 +23,7 @@ namespace {
 
 using namespace tile;
 
-constexpr int kThreads = 256;  // 2^(13 - kR): one register group per thread
+constexpr int kThreads = 1 << (svp::kMaxTileBits - kR);  // one register group per thread
 
 __global__ void __launch_bounds__(kThreads, 2)
 tile_pass_kernel(float2 *__restrict__ psi, DevPlanView plan, int pass_index, uint64_t num_tiles) {

@@ -126,8 +126,9 @@ bool build_plan(int n, const std::vector<Gate> &gates, const Options &opt, bool 
   P.n = n;
   const int m = std::min(opt.m, n);
   const int c = std::min(opt.c, m);
-  const int r = std::min(opt.r, m);
-  if (m > kMaxTileBits || r > kMaxReg || r < 1 || c < 0) { *err = "bad tile shape"; return false; }
+  const int rk = std::min(opt.rk, m);
+  const int r = std::min(std::min(opt.r, rk), m);
+  if (m > kMaxTileBits || rk > kMaxReg || r < 1 || c < 0 || m - rk > 12) { *err = "bad tile shape"; return false; }
 
   // leading layer of H on every qubit of a fresh state -> uniform first pass
   size_t start = 0;
@@ -238,10 +239,10 @@ bool build_plan(int n, const std::vector<Gate> &gates, const Options &opt, bool 
       DevStage ds;
       std::memset(&ds, 0, sizeof(ds));
       ds.r = (uint8_t)R.size();
-      // the plain kernel always holds 2^kMaxReg amplitudes per thread: pad the register
+      // the kernel holds 2^rk amplitudes per thread: pad the register
       // bits with unused tile bits (the fused kernel uses the first r of them)
       std::vector<int> rb = R;
-      const int rpad = std::min(kMaxReg, m);
+      const int rpad = rk;
       for (int b = 0; (int)rb.size() < rpad && b < m; ++b)
         if (std::find(rb.begin(), rb.end(), b) == rb.end()) rb.push_back(b);
       for (int j = 0; j < rpad; ++j) ds.rbit[j] = (uint8_t)rb[j];
@@ -249,13 +250,13 @@ bool build_plan(int n, const std::vector<Gate> &gates, const Options &opt, bool 
       for (int b = 0; b < m; ++b)
         if (std::find(rb.begin(), rb.end(), b) == rb.end()) nonr.push_back(b);
       order_group_bits(m, nonr, ds.nonr);
-      for (int half = 0; half < 2; ++half) {
+      for (int half = 0; half < kGroupEntries / 16; ++half) {
         for (int v = 0; v < 16; ++v) {
           DevGroupEntry ge;
           std::memset(&ge, 0, sizeof(ge));
           for (int i = 0; i < 4; ++i) {
             const int gi = 4 * half + i;
-            if (!((v >> i) & 1) || gi >= m - kMaxReg) continue;
+            if (!((v >> i) & 1) || gi >= m - rpad) continue;
             ge.L |= 1u << ds.nonr[gi];
             ge.G |= 1ull << dp.tq[ds.nonr[gi]];
           }

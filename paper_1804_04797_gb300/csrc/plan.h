@@ -71,12 +71,14 @@ enum Code : uint8_t {
 };
 
 // Stage group addressing: group index g of a thread -> (tile-local index L0, global
-// index offset G0) of its element 0 = entry[g & 15] | entry[16 + (g >> 4)].
+// index offset G0) of its element 0 = entry[g & 15] | entry[16 + ((g >> 4) & 15)] |
+// entry[32 + (g >> 8)]; kGroupEntries per stage.
 struct DevGroupEntry {
   uint32_t L;
   uint32_t pad;
   uint64_t G;
 };
+constexpr int kGroupEntries = 48;
 static_assert(sizeof(DevOp) == 24, "DevOp layout");
 
 constexpr int kMaxTileBits = 13;
@@ -116,7 +118,8 @@ static_assert(sizeof(DevPass) == 96, "DevPass layout");
 struct Options {
   int m = 13;        // tile qubits
   int c = 4;         // contiguous low qubits in every tile
-  int r = 5;         // register qubits per stage
+  int r = 5;         // qubits a stage may act on (<= rk)
+  int rk = 5;        // register qubits per thread of the kernel that runs the plan
   bool fused = false;
 };
 

@@ -14,7 +14,14 @@ using svp::DevOp;
 using svp::DevPass;
 using svp::DevStage;
 
-constexpr int kR = 5;
+// Register qubits per thread (each thread holds 2^kR amplitudes of a stage).  Every
+// translation unit that includes this header picks its width; all kernels use 5 (32
+// amplitudes, 256 threads per 2^13 tile; for the tensor-core kernel one row of the 32x32
+// unitary per thread).  Width 4 (twice the warps, twice the stages) measured 40 % slower.
+#ifndef SV_TILE_R
+#define SV_TILE_R 5
+#endif
+constexpr int kR = SV_TILE_R;
 constexpr int kE = 1 << kR;
 // 1/sqrt2 as an unevaluated sum hi + lo: the float nearest 1/sqrt2 is 1.7e-8 low, and
 // multiplying by it alone shrinks the norm by that much at every T gate (a systematic
@@ -38,35 +45,36 @@ struct GH {
     y = f2(rs2(a.x - b.x), rs2(a.y - b.y));
   }
 };
-// X^{1/2}: x' = (s + i d)/2, y' = (s - i d)/2 with s = x + y, d = x - y
+// X^{1/2} without its factor 1/2 (apply_ops applies 2^-count once per stage):
+// x' = s + i d, y' = s - i d with s = x + y, d = x - y
 struct GSX {
   __device__ __forceinline__ static void f(float2 &x, float2 &y) {
     const float sr = x.x + y.x, si = x.y + y.y, dr = x.x - y.x, di = x.y - y.y;
-    x = f2(0.5f * (sr - di), 0.5f * (si + dr));
-    y = f2(0.5f * (sr + di), 0.5f * (si - dr));
+    x = f2(sr - di, si + dr);
+    y = f2(sr + di, si - dr);
   }
 };
 struct GSXDG {
   __device__ __forceinline__ static void f(float2 &x, float2 &y) {
     const float sr = x.x + y.x, si = x.y + y.y, dr = x.x - y.x, di = x.y - y.y;
-    x = f2(0.5f * (sr + di), 0.5f * (si - dr));
-    y = f2(0.5f * (sr - di), 0.5f * (si + dr));
+    x = f2(sr + di, si - dr);
+    y = f2(sr - di, si + dr);
   }
 };
-// Y^{1/2}: x' = (1+i)(x - y)/2, y' = (1+i)(x + y)/2
+// Y^{1/2} without its factor 1/2: x' = (1+i)(x - y), y' = (1+i)(x + y)
 struct GSY {
   __device__ __forceinline__ static void f(float2 &x, float2 &y) {
     const float sr = x.x + y.x, si = x.y + y.y, dr = x.x - y.x, di = x.y - y.y;
-    x = f2(0.5f * (dr - di), 0.5f * (dr + di));
-    y = f2(0.5f * (sr - si), 0.5f * (sr + si));
+    x = f2(dr - di, dr + di);
+    y = f2(sr - si, sr + si);
   }
 };
-// (Y^{1/2})^dagger: x' = (1-i)(x + y)/2, y' = -(1-i)(x - y)/2
+// (Y^{1/2})^dagger without its factor 1/2: x' = (1-i)(x + y), y' = -(1-i)(x - y)
 struct GSYDG {
   __device__ __forceinline__ static void f(float2 &x, float2 &y) {
     const float sr = x.x + y.x, si = x.y + y.y, dr = x.x - y.x, di = x.y - y.y;
-    x = f2(0.5f * (sr + si), 0.5f * (si - sr));
-    y = f2(-0.5f * (dr + di), -0.5f * (di - dr));
+    x = f2(sr + si, si - sr);
+    y = f2(-(dr + di), dr - di);
   }
 };
 
@@ -86,6 +94,7 @@ struct DZERO {
 
 template <class G, int J>
 __device__ __forceinline__ void pairs(float2 (&v)[kE]) {
+  if constexpr (J >= kR) return;
 #pragma unroll
   for (int e = 0; e < kE; ++e)
     if (!(e & (1 << J))) G::f(v[e], v[e | (1 << J)]);
@@ -103,6 +112,7 @@ __device__ __forceinline__ void pairs_j(float2 (&v)[kE], int j) {
 // D on the elements whose register bit J equals B
 template <class D, int J, int B>
 __device__ __forceinline__ void diag1(float2 (&v)[kE]) {
+  if constexpr (J >= kR) return;
 #pragma unroll
   for (int e = 0; e < kE; ++e)
     if (((e >> J) & 1) == B) D::f(v[e]);
@@ -120,6 +130,7 @@ __device__ __forceinline__ void diag1_j(float2 (&v)[kE], int j) {
 // CZ: negate where bits J and K are both 1; PEQ: zero where bits J and K differ
 template <int J, int K, bool EQ>
 __device__ __forceinline__ void diag2(float2 (&v)[kE]) {
+  if constexpr (J >= kR || K >= kR) return;
 #pragma unroll
   for (int e = 0; e < kE; ++e) {
     const int bj = (e >> J) & 1, bk = (e >> K) & 1;
@@ -179,6 +190,7 @@ __device__ __forceinline__ void phase_all(float2 (&v)[kE], int p) {
 
 template <int J>
 __device__ __forceinline__ void general1(float2 (&v)[kE], const float *u) {
+  if constexpr (J >= kR) return;
   const float ar = u[0], ai = u[1], br = u[2], bi = u[3], cr = u[4], ci = u[5], dr = u[6], di = u[7];
 #pragma unroll
   for (int e = 0; e < kE; ++e) {
@@ -189,11 +201,13 @@ __device__ __forceinline__ void general1(float2 (&v)[kE], const float *u) {
   }
 }
 
-// One op by its flat code (one indirect branch).  Scalar phases and zeroing of the whole
-// group commute with every other op and are only recorded (ph, zero) for apply_ops.
+// One op by its flat code (one indirect branch).  Scalar phases, zeroing of the whole
+// group and the factors 1/2 of X^{1/2}, Y^{1/2} and their adjoints commute with every other
+// op and are only recorded (ph, zero, halves) for apply_ops.
 __device__ __forceinline__ void apply_op(float2 (&v)[kE], const DevOp &op, const float *mats, int &ph,
-                                         bool &zero) {
+                                         bool &zero, int &halves) {
   using namespace svp;
+  if (op.code >= C_PAIR + 5 && op.code < C_PAIR + 25) ++halves;
   switch (op.code) {
     case C_PAIR + 0: pairs<GH, 0>(v); break;
     case C_PAIR + 1: pairs<GH, 1>(v); break;
@@ -297,13 +311,13 @@ __device__ __forceinline__ void apply_op(float2 (&v)[kE], const DevOp &op, const
 }
 
 // Global index of element 0 of group `g` of stage `si` and its tile-local index, from
-// the stage's two 16-entry tables.
+// the stage's three 16-entry tables (one per 4 bits of the group index).
 __device__ __forceinline__ void group_base(const DevPlanView &plan, uint32_t si, int g, uint64_t base,
                                            uint32_t *L0, uint64_t *G0) {
-  const svp::DevGroupEntry lo = plan.gtab[32 * si + (g & 15)];
-  const svp::DevGroupEntry hi = plan.gtab[32 * si + 16 + ((g >> 4) & 15)];
-  *L0 = lo.L | hi.L;
-  *G0 = base | lo.G | hi.G;
+  const svp::DevGroupEntry *t = plan.gtab + svp::kGroupEntries * si;
+  const svp::DevGroupEntry a = t[g & 15], b = t[16 + ((g >> 4) & 15)], c = t[32 + ((g >> 8) & 15)];
+  *L0 = a.L | b.L | c.L;
+  *G0 = base | a.G | b.G | c.G;
 }
 
 __device__ __forceinline__ void load_group(const float2 *tile, const DevStage &st, uint32_t L0, float2 (&v)[kE]) {
@@ -338,21 +352,30 @@ __device__ __forceinline__ void store_group(float2 *tile, const DevStage &st, ui
 
 __device__ __forceinline__ void apply_ops(float2 (&v)[kE], const DevOp *ops, uint32_t begin, int count,
                                           uint64_t G0, const float *mats) {
-  int ph = 0;
+  int ph = 0, halves = 0;
   bool zero = false;
   if (count > 0) {
-    DevOp op = ops[begin];
     for (int o = 0; o < count; ++o) {
-      const DevOp nxt = ops[begin + (o + 1 < count ? o + 1 : o)];  // prefetch
-      if ((G0 & op.cmask) == op.cval) apply_op(v, op, mats, ph, zero);
-      op = nxt;
+      const DevOp op = ops[begin + o];
+      if ((G0 & op.cmask) == op.cval) apply_op(v, op, mats, ph, zero, halves);
+      if (halves == 32) {  // keep the deferred growth (at most 2^32) far from fp32 overflow
+        const float sc = __int_as_float((127 - 32) << 23);
+#pragma unroll
+        for (int e = 0; e < kE; ++e) v[e] = f2(v[e].x * sc, v[e].y * sc);
+        halves = 0;
+      }
     }
   }
   if (zero) {
 #pragma unroll
     for (int e = 0; e < kE; ++e) DZERO::f(v[e]);
-  } else if (ph & 7) {
-    phase_all(v, ph & 7);
+  } else {
+    if (halves) {
+      const float sc = __int_as_float((127 - halves) << 23);  // 2^-halves, exact
+#pragma unroll
+      for (int e = 0; e < kE; ++e) v[e] = f2(v[e].x * sc, v[e].y * sc);
+    }
+    if (ph & 7) phase_all(v, ph & 7);
   }
 }
 

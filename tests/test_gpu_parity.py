@@ -281,3 +281,23 @@ def test_batch_amplitudes_and_replay_match_oracle(tmp_path, monkeypatch):
     sv.sv_batch_free()
     with pytest.raises(sv.SvError):
         sv.sv_batch_amplitudes(0, [0])
+
+
+def test_many_square_roots_in_one_stage():
+    """200 X^{1/2} / Y^{1/2} gates on five qubits fall into one stage: their factors 1/2
+    (deferred and applied in bulk by the tile kernels) must neither overflow nor lose
+    accuracy."""
+    n = 14
+    gl = [('H', q, -1) for q in range(n)]
+    for i in range(200):
+        gl.append((('SX', 'SY', 'SXDG')[i % 3], i % 5, -1))
+    want = _oracle_apply(n, gl, ov.zero_state(n))
+    for kw in (dict(), dict(precision=TC)):
+        h = sv.sv_create(n, sv.options(**kw))
+        try:
+            sv.sv_apply_circuit(h, sv.gates_from_tuples([(_CODE[k], a, 0, 1) for (k, a, _b) in gl]))
+            got = sv.sv_copy_state(h, n)
+        finally:
+            sv.sv_destroy(h)
+        assert np.all(np.isfinite(got))
+        assert rel_l2(got, want) <= REL_L2, kw
