@@ -185,30 +185,33 @@ bool build_plan(int n, const std::vector<Gate> &gates, const Options &opt, bool 
     // ---- stages: groups of <= r register bits ------------------------------------
     std::vector<char> done(now.size(), 0);
     size_t left = now.size();
-    while (left > 0) {
-      std::vector<int> R;  // tile-local bits
+    // Schedule one stage with a fixed register set Rm (tile-local bit mask): non-diagonal
+    // gates on register bits (not yet closed), diagonal gates inside Rm as inner gates,
+    // other diagonal gates as post gates that close their tile bits for the rest of the
+    // stage.  Marks the placed gates in dn; returns (non-diagonal placed, total placed).
+    auto run_stage = [&](uint32_t Rm, std::vector<char> &dn, std::vector<int> *inner,
+                         std::vector<int> *post) -> std::pair<int, int> {
       uint32_t closed = 0;
-      std::vector<int> inner, post;
+      int nd = 0, tot = 0;
       bool progress = true;
       while (progress) {
         progress = false;
         uint64_t pend_nd = 0, pend_any = 0;  // qubits with an earlier unscheduled gate
         for (size_t i = 0; i < now.size(); ++i) {
+          if (dn[i]) continue;
           const Gate &x = gates[now[i]];
           const uint64_t qm = (1ull << x.q0) | (kind_two_qubit(x.kind) ? (1ull << x.q1) : 0ull);
           const bool diag = kind_is_diag(x.kind);
-          if (done[i]) continue;
           // ready: no earlier unscheduled gate that fails to commute with this one
           const bool ready = diag ? !(qm & pend_nd) : !(qm & pend_any);
           bool placed = false;
           if (ready) {
             if (!diag) {
               const int a = local_of[x.q0];
-              const bool inR = std::find(R.begin(), R.end(), a) != R.end();
-              if (!(closed & (1u << a)) && (inR || (int)R.size() < r)) {
-                if (!inR) R.push_back(a);
-                inner.push_back(now[i]);
+              if (((Rm >> a) & 1u) && !((closed >> a) & 1u)) {
+                if (inner) inner->push_back(now[i]);
                 placed = true;
+                ++nd;
               }
             } else {
               bool all_in = true;
@@ -218,16 +221,16 @@ bool build_plan(int n, const std::vector<Gate> &gates, const Options &opt, bool 
                 const int a = local_of[qs[t]];
                 if (a < 0) { all_in = false; continue; }
                 locals |= 1u << a;
-                if (std::find(R.begin(), R.end(), a) == R.end()) all_in = false;
+                if (!((Rm >> a) & 1u)) all_in = false;
               }
-              if (all_in) inner.push_back(now[i]);
-              else { post.push_back(now[i]); closed |= locals; }
+              if (all_in) { if (inner) inner->push_back(now[i]); }
+              else { if (post) post->push_back(now[i]); closed |= locals; }
               placed = true;
             }
           }
           if (placed) {
-            done[i] = 1;
-            --left;
+            dn[i] = 1;
+            ++tot;
             progress = true;
           } else {
             pend_any |= qm;
@@ -235,6 +238,36 @@ bool build_plan(int n, const std::vector<Gate> &gates, const Options &opt, bool 
           }
         }
       }
+      return {nd, tot};
+    };
+    while (left > 0) {
+      // register bits by greedy lookahead: add the tile bit that lets the stage place the
+      // most non-diagonal gates (then the most gates), up to r bits
+      uint32_t Rm = 0;
+      std::pair<int, int> cur;
+      {
+        std::vector<char> tmp = done;
+        cur = run_stage(0, tmp, nullptr, nullptr);
+      }
+      for (int round = 0; round < r; ++round) {
+        int best = -1;
+        std::pair<int, int> bs = cur;
+        for (int bb = 0; bb < m; ++bb) {
+          if ((Rm >> bb) & 1u) continue;
+          std::vector<char> tmp = done;
+          const std::pair<int, int> sc = run_stage(Rm | (1u << bb), tmp, nullptr, nullptr);
+          if (sc.first > bs.first || (sc.first == bs.first && sc.second > bs.second)) { bs = sc; best = bb; }
+        }
+        if (best < 0) break;
+        Rm |= 1u << best;
+        cur = bs;
+      }
+      std::vector<int> inner, post;
+      const std::pair<int, int> placed = run_stage(Rm, done, &inner, &post);
+      left -= (size_t)placed.second;
+      std::vector<int> R;
+      for (int bb = 0; bb < m; ++bb)
+        if ((Rm >> bb) & 1u) R.push_back(bb);
       // device stage
       DevStage ds;
       std::memset(&ds, 0, sizeof(ds));
