@@ -218,7 +218,7 @@ def main():
     ap.add_argument('--impl', default='ours', choices=['ours', 'reference'])
     ap.add_argument('--qubits', type=int, default=34, help='34 (headline) or a smaller lattice for tests')
     ap.add_argument('--no-fused', action='store_true')
-    ap.add_argument('--paths', default='plain,tf32x3', help='comma list of plain, tf32x3, pergate')
+    ap.add_argument('--paths', default='plain,tf32x3,f16x3', help='comma list of plain, tf32x3, f16x3, pergate')
     ap.add_argument('--tile-bits', type=int, default=0, help='tile qubits of the tile passes (0 = default 13)')
     ap.add_argument('--workload', default='34q', choices=['34q', 'batch', 'branch42'],
                     help='34q: the headline circuit; batch: the 512-circuit uneven batch; branch42: the '
@@ -287,7 +287,8 @@ def main():
 
     results = {}
     bits = np.array(inputs.bitstrings(n, 64, seed=2), dtype=np.uint64)
-    known = {'plain': sv.SV_PREC_PLAIN, 'tf32x3': sv.SV_PREC_TF32X3, 'pergate': sv.SV_PREC_PERGATE}
+    known = {'plain': sv.SV_PREC_PLAIN, 'tf32x3': sv.SV_PREC_TF32X3, 'f16x3': sv.SV_PREC_F16X3,
+             'pergate': sv.SV_PREC_PERGATE}
     modes = [(p, known[p]) for p in args.paths.split(',') if p in known]
     if args.no_fused:
         modes = [m for m in modes if m[0] != 'tf32x3']
@@ -349,13 +350,14 @@ def main():
     line = {
         'metric': METRIC, 'value': value, 'unit': UNIT, 'n_gpus': world, 'steps': args.steps,
         'warmup': args.warmup, 'ms_per_step': best['s_per_circuit'] * 1e3, 'higher_is_better': False,
-        'scaling': 'weak', 'vs_baseline': None, 'dtype': 'c64' if best_name == 'plain' else 'c64/tf32x3',
+        'scaling': 'weak', 'vs_baseline': None, 'dtype': 'c64' if best_name == 'plain' else 'c64/' + best_name,
         'data': 'synthetic',
         'config': {'workload': '34-qubit 6x6-minus-corners lattice circuit, depth 30, seed 0 (478 gates)'
                    if n == 34 else '%d-qubit lattice circuit' % n,
                    'state_bytes': 8 * 2 ** n, 'l2': 'state 137 GB >> L2 129 MB, no flush needed',
                    'path': best_name, 'replicas': world},
-        'roofline': {'bound': 'hbm', 'kernel': {'plain': 'tile_pass_kernel', 'tf32x3': 'fused_pass_kernel',
+        'roofline': {'bound': 'hbm', 'kernel': {'plain': 'tile_pass_kernel', 'tf32x3': 'fused_pass_kernel<tf32>',
+                                                'f16x3': 'fused_pass_kernel<f16>',
                                                 'pergate': 'gate1q_kernel/diag_kernel'}[best_name],
                      'achieved': achieved, 'peak': hbm_peak, 'unit': 'GB/s', 'frac': achieved / hbm_peak,
                      'traffic': None, 'peak_kind': peak_kind,

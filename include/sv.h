@@ -59,6 +59,8 @@ enum {
   SV_PREC_PLAIN = 0,  /* fp32 CUDA-core arithmetic, one gate at a time               */
   SV_PREC_TF32X3 = 1, /* fused k-qubit unitaries on tcgen05 tensor cores, 3-pass     */
                       /* split-TF32 products (hi*hi + hi*lo + lo*hi), fp32 accumulate */
+  SV_PREC_F16X3 = 2,  /* the same with fp16 hi/lo parts (same 11-bit significand,     */
+                      /* twice the tensor rate; rows scaled by powers of two)          */
   SV_PREC_PERGATE = 3 /* one full sweep of the state per gate (no tiling; baseline)  */
 };
 

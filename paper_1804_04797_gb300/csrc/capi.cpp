@@ -47,14 +47,15 @@ svp::Options plan_options(const sv_options &o) {
   svp::Options p;
   p.m = o.tile_bits > 0 ? o.tile_bits : 13;
   p.c = o.low_bits > 0 ? o.low_bits : 4;
-  p.fused = o.precision == SV_PREC_TF32X3;
+  p.fused = o.precision == SV_PREC_TF32X3 || o.precision == SV_PREC_F16X3;
   p.rk = 5;  // register qubits per thread of the tile kernels
   p.r = std::min(o.fuse_k > 0 ? o.fuse_k : p.rk, p.rk);
   return p;
 }
 
 sv_status check_options(const sv_options &o) {
-  if (o.precision != SV_PREC_PLAIN && o.precision != SV_PREC_TF32X3 && o.precision != SV_PREC_PERGATE)
+  if (o.precision != SV_PREC_PLAIN && o.precision != SV_PREC_TF32X3 && o.precision != SV_PREC_F16X3 &&
+      o.precision != SV_PREC_PERGATE)
     return fail(SV_ERR_ARG, "options: unknown precision mode");
   if (o.fuse_k < 0 || o.fuse_k > svp::kMaxReg) return fail(SV_ERR_ARG, "options: fuse_k must be 0 or 1..5");
   if (o.tile_bits != 0 && (o.tile_bits < 6 || o.tile_bits > svp::kMaxTileBits))
@@ -219,13 +220,13 @@ sv_status upload_plan(sv_state *s, const svp::Plan &P, svk::DevPlanView *view) {
   return SV_OK;
 }
 
-sv_status run_plan(sv_state *s, const svp::Plan &P, const svk::DevPlanView &view, bool fused) {
+sv_status run_plan(sv_state *s, const svp::Plan &P, const svk::DevPlanView &view, bool fused, bool f16) {
   const double amps = std::ldexp(1.0, s->n);
   for (size_t p = 0; p < P.passes.size(); ++p) {
     const svp::DevPass &hp = P.passes[p];
     const double bytes = (hp.flags & (svp::PF_INIT_UNIFORM | svp::PF_INIT_ZERO)) ? 8.0 * amps : 16.0 * amps;
     prof_begin(s);
-    cudaError_t e = fused ? svk::launch_fused_pass(s->psi, s->n, view, (int)p, hp, s->stream)
+    cudaError_t e = fused ? svk::launch_fused_pass(s->psi, s->n, view, (int)p, hp, s->stream, f16)
                           : svk::launch_tile_pass(s->psi, s->n, view, (int)p, hp, s->stream);
     prof_end(s, bytes);
     if (e != cudaSuccess) { s->broken = true; return cuda_fail(e, "tile pass kernel"); }
@@ -243,7 +244,7 @@ sv_status apply_gates(sv_state *s, const std::vector<svp::Gate> &g) {
   sv_status st;
   if ((st = set_device(s)) != SV_OK) return st;
   if (s->opts.precision == SV_PREC_PERGATE || s->n < 6) return apply_pergate(s, g);
-  if (s->opts.precision == SV_PREC_TF32X3 && !svk::fused_supported())
+  if ((s->opts.precision == SV_PREC_TF32X3 || s->opts.precision == SV_PREC_F16X3) && !svk::fused_supported())
     return fail(SV_ERR_CUDA, "fused tensor-core path needs an sm_103a device");
   if (g.empty() && !s->fresh) return SV_OK;
   svp::Plan P;
@@ -254,13 +255,14 @@ sv_status apply_gates(sv_state *s, const std::vector<svp::Gate> &g) {
     po.fused = false;
   }
   if (!svp::build_plan(s->n, g, po, s->fresh, &P, &err)) return fail(SV_ERR_ARG, err ? err : "planning failed");
-  if (po.fused && (st = build_stage_mats(&P, g, std::min(po.r, std::min(po.m, s->n)))) != SV_OK) return st;
+  const bool f16 = s->opts.precision == SV_PREC_F16X3;
+  if (po.fused && (st = build_stage_mats(&P, g, std::min(po.r, std::min(po.m, s->n)), f16)) != SV_OK) return st;
   if (po.fused)
     for (const svp::DevPass &dp : P.passes)
       if (dp.stage_count > 256) return fail(SV_ERR_ARG, "fused path: more than 256 stages in one pass");
   svk::DevPlanView view;
   if ((st = upload_plan(s, P, &view)) != SV_OK) return st;
-  if ((st = run_plan(s, P, view, po.fused)) != SV_OK) return st;
+  if ((st = run_plan(s, P, view, po.fused, f16)) != SV_OK) return st;
   s->fresh = false;
   if (po.fused) {
     // a fused pass whose bounded wait gave up leaves a non-zero error word

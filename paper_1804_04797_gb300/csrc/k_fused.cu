@@ -1,4 +1,4 @@
-// Fused tile pass on the tcgen05 tensor cores (split-TF32, fp32 accumulation).
+// Fused tile pass on the tcgen05 tensor cores (split precision, fp32 accumulation).
 //
 // Same passes and tiles as the plain kernel, but each stage's gates on its five
 // register qubits are applied as ONE 32x32 complex unitary U (multiplied out on the
@@ -7,19 +7,25 @@
 //     D[row, 2t+c'] = sum_{s,c} A[row, 2s+c] * B[2t+c', 2s+c],
 //     A = the tile's amplitudes, one row per group of 32 (register bits = column index s),
 //     B = [[Re U, -Im U], [Im U, Re U]] interleaved (64 x 64).
-// Precision: A = A_hi + A_lo and B = B_hi + B_lo, hi = x rounded to the nearest TF32,
-// lo = (x - hi) rounded to the nearest TF32; D = A_hi B_hi + A_hi B_lo + A_lo B_hi
-// accumulated in fp32 in tensor memory (the dropped terms are ~2^-22 relative).
+// Two operand formats, same three products (hi*hi + hi*lo + lo*hi, accumulated in fp32 in
+// tensor memory; the dropped lo*lo term is ~2^-22 relative):
+//   TF32x3  hi = x rounded to the nearest TF32, lo = (x - hi) rounded likewise; K = 8 per
+//           MMA instruction.
+//   F16x3   the same split in fp16 (the same 11-bit significand as TF32), twice the tensor
+//           rate and K = 16 per instruction, half the operand bytes.  fp16's range is
+//           handled by scaling: every row by a power of two bringing its largest component
+//           near 2^6 (exact; U acts within a row, so the scale is undone after the MMA) and
+//           B by 2^8 (keeps the small lo parts normal).
 // Data movement per stage: each thread gathers its row (32 amplitudes) from the shared
-// tile, splits it and stores A_hi/A_lo into TMEM (its own lane); one thread issues the
-// 24 MMAs per 128-row block (A from TMEM, B from shared memory) and commits them to an
-// mbarrier; every thread then loads its row of D back from TMEM, applies the stage's
-// diagonal epilogue (gates that touch a non-register qubit) and scatters the row back
-// into the shared tile.  B (hi and lo, 32 KB per stage) is streamed from the plan in
-// global memory by TMA bulk copies into two shared buffers, one stage ahead.
-// All waits are bounded: a wait that gives up sets the error word, the CTA stops
-// issuing work, drains its outstanding copies and MMAs (bounded), frees its TMEM and
-// returns.
+// tile, splits it and stores A_hi/A_lo into TMEM (its own lane); one thread issues the MMAs
+// (A from TMEM, B from shared memory) and commits them to an mbarrier; every thread then
+// loads its row of D back from TMEM, applies the stage's diagonal epilogue (gates that
+// touch a non-register qubit) and scatters the row back into the shared tile.  B (hi and
+// lo) is streamed from the plan in global memory by TMA bulk copies into two shared
+// buffers, one stage ahead.
+// All waits are bounded: a wait that gives up sets the error word, the CTA stops issuing
+// work, drains its outstanding copies and MMAs (bounded), frees its TMEM and returns.
+#include <cuda_fp16.h>
 #include <cuda_runtime.h>
 
 #include <cmath>
@@ -37,32 +43,53 @@ namespace {
 
 using namespace tile;
 
-constexpr int kK = 64;                   // real K = N = 2 * 2^5
-constexpr int kBBytes = kK * kK * 4;     // one 64x64 fp32 matrix: 16 KB
-constexpr int kBStage = 2 * kBBytes;     // hi + lo
+constexpr int kK = 64;  // real K = N = 2 * 2^5
 constexpr unsigned long long kWaitNs = 1000000000ull;  // give up a wait after 1 s
 
-__host__ __device__ inline uint32_t kmaj_off(int row, int k) {
-  // K-major, no swizzle: 8-row x 16-byte core matrices, K-adjacent core matrices 128 B
-  // apart (leading byte offset), row-adjacent core matrices (kK/4)*128 B apart (stride).
-  return (uint32_t)((((row >> 3) * (kK / 4) + (k >> 2)) * 128) + (row & 7) * 16 + (k & 3) * 4);
-}
+// Operand format traits.
+template <bool F16>
+struct Fmt;
+template <>
+struct Fmt<false> {  // TF32x3
+  static constexpr int kAcols = 64;                 // TMEM columns of one A part per 128 rows
+  static constexpr int kKsteps = kK / 8;            // MMA instructions along K
+  static constexpr int kBBytes = kK * kK * 4;       // one 64x64 B part
+  static constexpr uint32_t kSBO = (kK / 4) * 128;  // row-group stride of the K-major layout
+  // kind::tf32: D fp32, A/B tf32, K-major, M = 128, N = 64
+  static constexpr uint32_t kIdesc = (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(kK >> 3) << 17) | (8u << 24);
+  __host__ __device__ static uint32_t b_off(int row, int k) {  // byte offset in a B part
+    return (uint32_t)((((row >> 3) * (kK / 4) + (k >> 2)) * 128) + (row & 7) * 16 + (k & 3) * 4);
+  }
+};
+template <>
+struct Fmt<true> {  // F16x3
+  static constexpr int kAcols = 32;
+  static constexpr int kKsteps = kK / 16;
+  static constexpr int kBBytes = kK * kK * 2;
+  static constexpr uint32_t kSBO = (kK / 8) * 128;
+  // kind::f16: D fp32, A/B fp16, K-major, M = 128, N = 64
+  static constexpr uint32_t kIdesc = (1u << 4) | (0u << 7) | (0u << 10) | ((uint32_t)(kK >> 3) << 17) | (8u << 24);
+  __host__ __device__ static uint32_t b_off(int row, int k) {
+    return (uint32_t)((((row >> 3) * (kK / 8) + (k >> 3)) * 128) + (row & 7) * 16 + (k & 7) * 2);
+  }
+};
+constexpr int kF16RowExp = 6;  // largest row component scaled to [2^6, 2^7)
+constexpr int kF16BExp = 8;    // B scaled by 2^8
 
 __device__ __forceinline__ uint32_t smem_u32(const void *p) {
   return static_cast<uint32_t>(__cvta_generic_to_shared(p));
 }
 
-__device__ __forceinline__ uint64_t smem_desc(uint32_t saddr) {
+// K-major, no swizzle: 8-row x 16-byte core matrices, K-adjacent core matrices 128 B
+// apart (leading byte offset), row-adjacent ones sbo apart (stride byte offset).
+__device__ __forceinline__ uint64_t smem_desc(uint32_t saddr, uint32_t sbo) {
   uint64_t d = 0;
   d |= (uint64_t)((saddr & 0x3FFFF) >> 4);
-  d |= (uint64_t)(128 >> 4) << 16;               // leading byte offset (K direction)
-  d |= (uint64_t)(((kK / 4) * 128) >> 4) << 32;  // stride byte offset (row direction)
-  d |= (uint64_t)1 << 46;                         // tcgen05 descriptor version
-  return d;                                       // base offset 0, no swizzle
+  d |= (uint64_t)(128 >> 4) << 16;
+  d |= (uint64_t)(sbo >> 4) << 32;
+  d |= (uint64_t)1 << 46;  // tcgen05 descriptor version
+  return d;                // base offset 0, no swizzle
 }
-
-// kind::tf32 instruction descriptor: D fp32, A/B tf32, K-major, M = 128, N = 64.
-constexpr uint32_t kIdesc = (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(kK >> 3) << 17) | ((uint32_t)(128 >> 4) << 24);
 
 __device__ __forceinline__ bool mbar_try(uint32_t bar, uint32_t phase) {
   uint32_t ok;
@@ -83,9 +110,15 @@ __device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t phase) {
   return false;
 }
 
-__device__ __forceinline__ void mma_tf32(uint32_t d, uint32_t a_tmem, uint64_t b_desc, uint32_t acc) {
-  asm volatile("{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n tcgen05.mma.cta_group::1.kind::tf32 [%0], [%1], %2, %3, p;\n}\n"
-               :: "r"(d), "r"(a_tmem), "l"(b_desc), "r"(kIdesc), "r"(acc));
+template <bool F16>
+__device__ __forceinline__ void mma(uint32_t d, uint32_t a_tmem, uint64_t b_desc, uint32_t acc) {
+  if constexpr (F16) {
+    asm volatile("{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n tcgen05.mma.cta_group::1.kind::f16 [%0], [%1], %2, %3, p;\n}\n"
+                 :: "r"(d), "r"(a_tmem), "l"(b_desc), "r"(Fmt<true>::kIdesc), "r"(acc));
+  } else {
+    asm volatile("{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n tcgen05.mma.cta_group::1.kind::tf32 [%0], [%1], %2, %3, p;\n}\n"
+                 :: "r"(d), "r"(a_tmem), "l"(b_desc), "r"(Fmt<false>::kIdesc), "r"(acc));
+  }
 }
 
 #define SV_TMEM_ST16(taddr, r)                                                                              \
@@ -98,34 +131,42 @@ __device__ __forceinline__ void mma_tf32(uint32_t d, uint32_t a_tmem, uint64_t b
                  "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]) \
                : "r"(taddr) : "memory")
 
-// Round to the nearest TF32 value, ties away from zero (add half a TF32 ulp to the
-// magnitude bits, clear the 13 low mantissa bits).  Both split parts are rounded this
-// way so that each is exactly representable (the tensor core then drops nothing) and
-// the residual x - hi - lo has no sign bias; truncating instead biases every product
-// toward zero.
+// Nearest TF32 value, ties away from zero (add half a TF32 ulp to the magnitude bits,
+// clear the 13 low mantissa bits).  Both split parts are rounded this way so that each
+// is exactly representable (the tensor core then drops nothing) and the residual
+// x - hi - lo has no sign bias; truncating instead biases every product toward zero.
 __device__ __forceinline__ float tf32_rn(float x) {
   return __uint_as_float((__float_as_uint(x) + 0x1000u) & 0xFFFFE000u);
 }
 
-// TMEM columns: A_hi at [64 mb, +64), A_lo at [64 MB + 64 mb, +64), D at [128 MB + 64 mb, +64)
-template <int MB>
+__device__ __forceinline__ uint32_t pack_h2(float a, float b) {
+  return (uint32_t)__half_as_ushort(__float2half_rn(a)) | ((uint32_t)__half_as_ushort(__float2half_rn(b)) << 16);
+}
+
+// TMEM columns: A_hi at [kAcols mb, +kAcols), A_lo at [kAcols (MB + mb), +kAcols),
+// D at [2 kAcols MB + 64 mb, +64); allocation = next power of two.
+template <int MB, bool F16>
 struct Cols {
-  static constexpr uint32_t kAlloc = MB == 1 ? 256 : 512;
-  __device__ static uint32_t a_hi(int mb) { return 64u * mb; }
-  __device__ static uint32_t a_lo(int mb) { return 64u * MB + 64u * mb; }
-  __device__ static uint32_t d(int mb) { return 128u * MB + 64u * mb; }
+  static constexpr int kA = Fmt<F16>::kAcols;
+  static constexpr uint32_t kUsed = (uint32_t)(2 * kA * MB + 64 * MB);
+  static constexpr uint32_t kAlloc = kUsed <= 128 ? 128 : (kUsed <= 256 ? 256 : 512);
+  __device__ static uint32_t a_hi(int mb) { return (uint32_t)(kA * mb); }
+  __device__ static uint32_t a_lo(int mb) { return (uint32_t)(kA * (MB + mb)); }
+  __device__ static uint32_t d(int mb) { return (uint32_t)(2 * kA * MB + 64 * mb); }
 };
 
-// Issue the B load (hi and lo) of stage `st` into buffer `buf`.
+// Issue the B load (hi and lo parts) of stage `st` into buffer `buf`.
+template <bool F16>
 __device__ __forceinline__ void issue_b_load(const float *mats, const DevStage &st, unsigned char *bbuf, int buf,
                                              uint32_t bar) {
-  const float *src = mats + st.mat_begin;
-  const uint32_t dst = smem_u32(bbuf + buf * kBStage);
-  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" :: "r"(bar), "r"(kBStage) : "memory");
+  constexpr int kB = Fmt<F16>::kBBytes;
+  const char *src = reinterpret_cast<const char *>(mats + st.mat_begin);
+  const uint32_t dst = smem_u32(bbuf + buf * 2 * kB);
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" :: "r"(bar), "r"(2 * kB) : "memory");
   asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];"
-               :: "r"(dst), "l"(src), "r"(kBBytes), "r"(bar) : "memory");
+               :: "r"(dst), "l"(src), "r"(kB), "r"(bar) : "memory");
   asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];"
-               :: "r"(dst + kBBytes), "l"(src + kK * kK), "r"(kBBytes), "r"(bar) : "memory");
+               :: "r"(dst + kB), "l"(src + kB), "r"(kB), "r"(bar) : "memory");
 }
 
 // Sum over the CTA of one double per thread, fixed order; red holds one slot per warp
@@ -175,13 +216,63 @@ __device__ __forceinline__ void scale_row(float2 (&v)[kE], float delta, uint32_t
   }
 }
 
-template <int MB>
-__global__ void __launch_bounds__(128 * MB, 1)
+// A (this thread's row) into its TMEM lane: hi and lo parts.  F16: the row is first
+// scaled by 2^(sexp - 127) (returned) so that its largest component lies in [2^6, 2^7).
+template <int MB, bool F16>
+__device__ __forceinline__ int store_a(const float2 (&v)[kE], uint32_t taddr_hi, uint32_t taddr_lo) {
+  if constexpr (!F16) {
+#pragma unroll
+    for (int h = 0; h < 4; ++h) {
+      uint32_t rh[16], rl[16];
+#pragma unroll
+      for (int e = 0; e < 8; ++e) {
+        const float2 z = v[8 * h + e];
+        const float hr = tf32_rn(z.x), hi = tf32_rn(z.y);
+        rh[2 * e] = __float_as_uint(hr);
+        rh[2 * e + 1] = __float_as_uint(hi);
+        rl[2 * e] = __float_as_uint(tf32_rn(z.x - hr));
+        rl[2 * e + 1] = __float_as_uint(tf32_rn(z.y - hi));
+      }
+      SV_TMEM_ST16(taddr_hi + 16 * h, rh);
+      SV_TMEM_ST16(taddr_lo + 16 * h, rl);
+    }
+    return 127;
+  } else {
+    float mx = 0.f;
+#pragma unroll
+    for (int e = 0; e < kE; ++e) mx = fmaxf(mx, fmaxf(fabsf(v[e].x), fabsf(v[e].y)));
+    const int ex = (int)((__float_as_uint(mx) >> 23) & 0xFF);
+    int sexp = 127 + kF16RowExp + 127 - ex;  // biased exponent of the scale 2^(6 - (ex - 127))
+    sexp = sexp < 2 ? 2 : (sexp > 240 ? 240 : sexp);
+    const float sc = __uint_as_float((uint32_t)sexp << 23);
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+      uint32_t rh[16], rl[16];
+#pragma unroll
+      for (int e = 0; e < 16; ++e) {  // amplitude 16h+e -> column 16h+e (re low half, im high)
+        const float2 z = v[16 * h + e];
+        const float xr = z.x * sc, xi = z.y * sc;
+        const float hr = __half2float(__float2half_rn(xr)), hi = __half2float(__float2half_rn(xi));
+        rh[e] = pack_h2(hr, hi);
+        rl[e] = pack_h2(xr - hr, xi - hi);
+      }
+      SV_TMEM_ST16(taddr_hi + 16 * h, rh);
+      SV_TMEM_ST16(taddr_lo + 16 * h, rl);
+    }
+    return sexp;
+  }
+}
+
+template <int MB, bool F16>
+__global__ void __launch_bounds__(128 * MB, F16 ? (MB == 1 ? 3 : 2) : (MB == 1 ? 2 : 1))
 fused_pass_kernel(float2 *__restrict__ psi, DevPlanView plan, int pass_index, uint64_t num_tiles) {
+  using FM = Fmt<F16>;
+  using CL = Cols<MB, F16>;
+  constexpr int kB = FM::kBBytes;
   int *err = plan.err;
   extern __shared__ __align__(1024) unsigned char smem_raw[];
-  unsigned char *bbuf = smem_raw;                                      // 2 x 32 KB
-  float2 *tile = reinterpret_cast<float2 *>(smem_raw + 2 * kBStage);  // 2^m amplitudes
+  unsigned char *bbuf = smem_raw;                                       // 2 x (hi + lo)
+  float2 *tile = reinterpret_cast<float2 *>(smem_raw + 4 * kB);        // 2^m amplitudes
   __shared__ DevPass P;
   __shared__ uint64_t chunk_off[1 << 10];
   __shared__ __align__(8) uint64_t bars[3];  // [0] MMA done, [1],[2] B buffer full
@@ -201,7 +292,7 @@ fused_pass_kernel(float2 *__restrict__ psi, DevPlanView plan, int pass_index, ui
   }
   if (warp == 0) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;"
-                 :: "r"(smem_u32(&tmem_slot)), "r"(Cols<MB>::kAlloc));
+                 :: "r"(smem_u32(&tmem_slot)), "r"(CL::kAlloc));
     asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
   }
   __syncthreads();
@@ -226,7 +317,7 @@ fused_pass_kernel(float2 *__restrict__ psi, DevPlanView plan, int pass_index, ui
   bool mma_out = false;                 // tid 0: MMAs committed and not yet waited for
 
   if (tid == 0 && n_mma > 0 && blockIdx.x < num_tiles) {
-    issue_b_load(plan.mats, plan.stages[P.stage_begin + mma_list[0]], bbuf, 0, smem_u32(&bars[1]));
+    issue_b_load<F16>(plan.mats, plan.stages[P.stage_begin + mma_list[0]], bbuf, 0, smem_u32(&bars[1]));
     ++b_loads_out;
   }
 
@@ -237,7 +328,7 @@ fused_pass_kernel(float2 *__restrict__ psi, DevPlanView plan, int pass_index, ui
     __syncthreads();
     // Every gate of the pass acts inside the tile, so a unitary pass keeps the tile's
     // norm exactly.  The tensor core's fp32 accumulation truncates toward zero and loses
-    // ~0.3 ulp of every output per stage (a systematic norm drift of ~6e-8 per stage);
+    // ~0.3 ulp of every output per stage (a systematic norm drift of ~1e-7 per stage);
     // the tile's norm is measured in the first stage and restored in the last one with
     // unbiased stochastic rounding.
     const bool keep_norm = (P.flags & svp::PF_UNITARY) && n_mma > 0;
@@ -260,26 +351,11 @@ fused_pass_kernel(float2 *__restrict__ psi, DevPlanView plan, int pass_index, ui
           const bool more_here = q + 1 < n_mma;
           if (more_here || !last_tile) {
             const DevStage &nx = plan.stages[P.stage_begin + mma_list[more_here ? q + 1 : 0]];
-            issue_b_load(plan.mats, nx, bbuf, buf ^ 1, smem_u32(&bars[1 + (buf ^ 1)]));
+            issue_b_load<F16>(plan.mats, nx, bbuf, buf ^ 1, smem_u32(&bars[1 + (buf ^ 1)]));
             ++b_loads_out;
           }
         }
-        // A = this thread's row, split into TF32 hi + lo, into its TMEM lane
-#pragma unroll
-        for (int h = 0; h < 4; ++h) {
-          uint32_t rh[16], rl[16];
-#pragma unroll
-          for (int e = 0; e < 8; ++e) {
-            const float2 z = v[8 * h + e];
-            const float hr = tf32_rn(z.x), hi = tf32_rn(z.y);
-            rh[2 * e] = __float_as_uint(hr);
-            rh[2 * e + 1] = __float_as_uint(hi);
-            rl[2 * e] = __float_as_uint(tf32_rn(z.x - hr));
-            rl[2 * e + 1] = __float_as_uint(tf32_rn(z.y - hi));
-          }
-          SV_TMEM_ST16(tmem + lane_off + Cols<MB>::a_hi(mb) + 16 * h, rh);
-          SV_TMEM_ST16(tmem + lane_off + Cols<MB>::a_lo(mb) + 16 * h, rl);
-        }
+        const int sexp = store_a<MB, F16>(v, tmem + lane_off + CL::a_hi(mb), tmem + lane_off + CL::a_lo(mb));
         asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
         asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
         __syncthreads();
@@ -293,20 +369,20 @@ fused_pass_kernel(float2 *__restrict__ psi, DevPlanView plan, int pass_index, ui
           } else {
             --b_loads_out;
             if (buf) b_phase1 ^= 1; else b_phase0 ^= 1;
-            const uint32_t bhi = smem_u32(bbuf + buf * kBStage);
-            const uint64_t dhi = smem_desc(bhi), dlo = smem_desc(bhi + kBBytes);  // +16 per 256 B K step
+            const uint32_t bhi = smem_u32(bbuf + buf * 2 * kB);
+            const uint64_t dhi = smem_desc(bhi, FM::kSBO), dlo = smem_desc(bhi + kB, FM::kSBO);  // +16 per 256 B
 #pragma unroll
             for (int m = 0; m < MB; ++m) {
-              const uint32_t d = tmem + Cols<MB>::d(m);
-              const uint32_t ah = tmem + Cols<MB>::a_hi(m), al = tmem + Cols<MB>::a_lo(m);
+              const uint32_t d = tmem + CL::d(m);
+              const uint32_t ah = tmem + CL::a_hi(m), al = tmem + CL::a_lo(m);
               // small correction terms first, the large hi*hi term last: fewer truncating
               // accumulations at full magnitude
 #pragma unroll
-              for (int kk = 0; kk < kK / 8; ++kk) mma_tf32(d, al + 8 * kk, dhi + 16 * kk, kk > 0);
+              for (int kk = 0; kk < FM::kKsteps; ++kk) mma<F16>(d, al + 8 * kk, dhi + 16 * kk, kk > 0);
 #pragma unroll
-              for (int kk = 0; kk < kK / 8; ++kk) mma_tf32(d, ah + 8 * kk, dlo + 16 * kk, 1);
+              for (int kk = 0; kk < FM::kKsteps; ++kk) mma<F16>(d, ah + 8 * kk, dlo + 16 * kk, 1);
 #pragma unroll
-              for (int kk = 0; kk < kK / 8; ++kk) mma_tf32(d, ah + 8 * kk, dhi + 16 * kk, 1);
+              for (int kk = 0; kk < FM::kKsteps; ++kk) mma<F16>(d, ah + 8 * kk, dhi + 16 * kk, 1);
             }
             asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];"
                          :: "r"(bar_mma) : "memory");
@@ -325,15 +401,23 @@ fused_pass_kernel(float2 *__restrict__ psi, DevPlanView plan, int pass_index, ui
         if (abort_flag) break;
         asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
         {
-          uint32_t r[4][16];
+          // F16: undo the row scale and the 2^8 of B (exact powers of two)
+          const float un = F16 ? __uint_as_float((uint32_t)(127 + 127 - kF16BExp - sexp) << 23) : 1.0f;
 #pragma unroll
-          for (int h = 0; h < 4; ++h) SV_TMEM_LD16(tmem + lane_off + Cols<MB>::d(mb) + 16 * h, r[h]);
-          asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+          for (int hh = 0; hh < 2; ++hh) {  // two halves of the row: 32 registers in flight
+            uint32_t r[2][16];
 #pragma unroll
-          for (int h = 0; h < 4; ++h)
+            for (int h = 0; h < 2; ++h) SV_TMEM_LD16(tmem + lane_off + CL::d(mb) + 32 * hh + 16 * h, r[h]);
+            asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 #pragma unroll
-            for (int e = 0; e < 8; ++e)
-              v[8 * h + e] = make_float2(__uint_as_float(r[h][2 * e]), __uint_as_float(r[h][2 * e + 1]));
+            for (int h = 0; h < 2; ++h)
+#pragma unroll
+              for (int e = 0; e < 8; ++e) {
+                float re = __uint_as_float(r[h][2 * e]), im = __uint_as_float(r[h][2 * e + 1]);
+                if (F16) { re *= un; im *= un; }
+                v[16 * hh + 8 * h + e] = make_float2(re, im);
+              }
+          }
         }
         asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
         ++q;
@@ -372,25 +456,28 @@ fused_pass_kernel(float2 *__restrict__ psi, DevPlanView plan, int pass_index, ui
   asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
   __syncthreads();
   if (warp == 0)
-    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" :: "r"(tmem), "r"(Cols<MB>::kAlloc));
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" :: "r"(tmem), "r"(CL::kAlloc));
 }
 
-template <int MB>
-cudaError_t launch_mb(float2 *psi, int n, const DevPlanView &plan, int pass_index, const svp::DevPass &hp,
-                      cudaStream_t st) {
+template <int MB, bool F16>
+cudaError_t launch_cfg(float2 *psi, int n, const DevPlanView &plan, int pass_index, const svp::DevPass &hp,
+                       cudaStream_t st) {
   static bool configured = false;
-  // m = 12: 32 KB tile + 64 KB B buffers (+9 KB static): two CTAs per SM, never three
-  // (2 x 256 TMEM columns); m = 13: 64 KB tile, one CTA per SM (512 columns).
-  const size_t smem = (size_t)(2 * kBStage) + (sizeof(float2) << (MB == 1 ? 12 : 13));
+  // dynamic shared memory: two B buffers (hi + lo each) and the tile.  CTAs per SM are
+  // set by the TMEM allocation (512 columns per SM) and the launch bounds:
+  //   TF32 m=12: 2 x 256 columns; TF32 m=13: 1 x 512; F16 m=12: 3 x 128; F16 m=13: 2 x 256.
+  const size_t smem = (size_t)(4 * Fmt<F16>::kBBytes) + (sizeof(float2) << (MB == 1 ? 12 : 13));
   if (!configured) {
-    cudaError_t e = cudaFuncSetAttribute(fused_pass_kernel<MB>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    cudaError_t e =
+        cudaFuncSetAttribute(fused_pass_kernel<MB, F16>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     configured = true;
   }
+  const int per_sm = F16 ? (MB == 1 ? 3 : 2) : (MB == 1 ? 2 : 1);
   const uint64_t tiles = 1ull << (n - hp.m);
-  uint64_t grid = (uint64_t)device_sm_count() * (MB == 1 ? 2 : 1);
+  uint64_t grid = (uint64_t)device_sm_count() * per_sm;
   if (grid > tiles) grid = tiles;
-  fused_pass_kernel<MB><<<(unsigned)grid, 128 * MB, smem, st>>>(psi, plan, pass_index, tiles);
+  fused_pass_kernel<MB, F16><<<(unsigned)grid, 128 * MB, smem, st>>>(psi, plan, pass_index, tiles);
   return cudaGetLastError();
 }
 
@@ -409,9 +496,11 @@ bool fused_supported() {
 }
 
 cudaError_t launch_fused_pass(float2 *psi, int n, const DevPlanView &plan, int pass_index, const svp::DevPass &hp,
-                              cudaStream_t st) {
-  if (hp.m == 12) return launch_mb<1>(psi, n, plan, pass_index, hp, st);
-  if (hp.m == 13) return launch_mb<2>(psi, n, plan, pass_index, hp, st);
+                              cudaStream_t st, bool f16) {
+  if (hp.m == 12) return f16 ? launch_cfg<1, true>(psi, n, plan, pass_index, hp, st)
+                             : launch_cfg<1, false>(psi, n, plan, pass_index, hp, st);
+  if (hp.m == 13) return f16 ? launch_cfg<2, true>(psi, n, plan, pass_index, hp, st)
+                             : launch_cfg<2, false>(psi, n, plan, pass_index, hp, st);
   return cudaErrorInvalidValue;
 }
 
@@ -419,8 +508,7 @@ cudaError_t launch_fused_pass(float2 *psi, int n, const DevPlanView &plan, int p
 
 namespace svc {
 
-// Nearest TF32 value of a finite float, ties away from zero (the host twin of
-// cvt.rna.tf32.f32): add half a TF32 ulp to the magnitude bits, clear the 13 low bits.
+// Nearest TF32 value of a finite float, ties away from zero (the host twin of tf32_rn).
 static float tf32_round_host(float x) {
   uint32_t b;
   std::memcpy(&b, &x, 4);
@@ -430,11 +518,15 @@ static float tf32_round_host(float x) {
   return y;
 }
 
-// Stage unitaries as split-TF32 B operands in the kernel's shared-memory layout.
-sv_status build_stage_mats(svp::Plan *P, const std::vector<svp::Gate> &g, int r) {
-  if (r != 5) return svc::fail(SV_ERR_ARG, "fused path: fuse_k must be 5");
+// Stage unitaries as split B operands in the kernel's shared-memory layout: per stage the
+// hi part then the lo part, each 64 x 64 (TF32: fp32 words; F16: fp16 halves, B x 2^8).
+sv_status build_stage_mats(svp::Plan *P, const std::vector<svp::Gate> &g, int r, bool f16) {
+  if (r != 5) return fail(SV_ERR_ARG, "fused path: fuse_k must be 5");
   P->mats.clear();
   std::vector<double> u;
+  const int part_bytes = f16 ? svk::Fmt<true>::kBBytes : svk::Fmt<false>::kBBytes;
+  const size_t stage_floats = (size_t)2 * part_bytes / 4;
+  const double bscale = f16 ? std::ldexp(1.0, svk::kF16BExp) : 1.0;
   for (size_t s = 0; s < P->stages.size(); ++s) {
     svp::DevStage &ds = P->stages[s];
     if (P->stage_gates[s].empty()) {
@@ -450,21 +542,30 @@ sv_status build_stage_mats(svp::Plan *P, const std::vector<svp::Gate> &g, int r)
     svp::stage_unitary(*P, g, (int)s, 5, &u);
     const size_t off = P->mats.size();
     ds.mat_begin = (uint32_t)off;
-    P->mats.resize(off + 2 * svk::kK * svk::kK, 0.f);
-    float *hi = P->mats.data() + off;
-    float *lo = hi + svk::kK * svk::kK;
+    P->mats.resize(off + stage_floats, 0.f);
+    char *hi = reinterpret_cast<char *>(P->mats.data() + off);
+    char *lo = hi + part_bytes;
     for (int t = 0; t < 32; ++t) {
       for (int sidx = 0; sidx < 32; ++sidx) {
         const double ur = u[2 * ((size_t)t * 32 + sidx)], ui = u[2 * ((size_t)t * 32 + sidx) + 1];
         const double b[2][2] = {{ur, -ui}, {ui, ur}};  // [c'][c]
         for (int cp = 0; cp < 2; ++cp) {
           for (int c = 0; c < 2; ++c) {
-            const double x = b[cp][c];
-            const float h = tf32_round_host((float)x);
-            const float l = tf32_round_host((float)(x - (double)h));
-            const uint32_t o = svk::kmaj_off(2 * t + cp, 2 * sidx + c) / 4;
-            hi[o] = h;
-            lo[o] = l;
+            const double x = b[cp][c] * bscale;
+            const int row = 2 * t + cp, col = 2 * sidx + c;
+            if (f16) {
+              const __half h = __float2half_rn((float)x);
+              const __half l = __float2half_rn((float)(x - (double)__half2float(h)));
+              const uint32_t o = svk::Fmt<true>::b_off(row, col);
+              std::memcpy(hi + o, &h, 2);
+              std::memcpy(lo + o, &l, 2);
+            } else {
+              const float h = tf32_round_host((float)x);
+              const float l = tf32_round_host((float)(x - (double)h));
+              const uint32_t o = svk::Fmt<false>::b_off(row, col);
+              std::memcpy(hi + o, &h, 4);
+              std::memcpy(lo + o, &l, 4);
+            }
           }
         }
       }

@@ -32,8 +32,9 @@ cudaError_t launch_tile_pass(float2 *psi, int n, const DevPlanView &plan, int pa
                              const svp::DevPass &host_pass, cudaStream_t st);
 
 // K4 fused tensor-core tile pass (tcgen05, split-TF32).
+// tile_bits 12 or 13; f16: F16x3 operands, else TF32x3
 cudaError_t launch_fused_pass(float2 *psi, int n, const DevPlanView &plan, int pass_index,
-                              const svp::DevPass &host_pass, cudaStream_t st);  // tile_bits 12 or 13
+                              const svp::DevPass &host_pass, cudaStream_t st, bool f16);
 bool fused_supported();
 
 // Per-gate sweeps (K2 one-qubit pair update, K3 diagonal factor on a bit pattern).

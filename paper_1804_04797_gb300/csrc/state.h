@@ -41,10 +41,10 @@ svp::Options plan_options(const sv_options &o);
 sv_status check_options(const sv_options &o);
 sv_status convert_gates(int n, const sv_gate *g, size_t count, bool inverse, std::vector<svp::Gate> *out);
 sv_status upload_plan(sv_state *s, const svp::Plan &P, svk::DevPlanView *view);
-sv_status run_plan(sv_state *s, const svp::Plan &P, const svk::DevPlanView &view, bool fused);
+sv_status run_plan(sv_state *s, const svp::Plan &P, const svk::DevPlanView &view, bool fused, bool f16 = false);
 // Plan and run an internal gate list (kinds may include K_PEQ) on the state.
 sv_status apply_gates(sv_state *s, const std::vector<svp::Gate> &g);
 // Fused path: the stage unitaries as split-TF32 operands (see k_fused.cu).
-sv_status build_stage_mats(svp::Plan *P, const std::vector<svp::Gate> &g, int r);
+sv_status build_stage_mats(svp::Plan *P, const std::vector<svp::Gate> &g, int r, bool f16);
 
 }  // namespace svc

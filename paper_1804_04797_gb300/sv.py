@@ -17,7 +17,7 @@ c_int, c_uint8, c_uint32, c_uint64, c_size_t, c_double, c_void_p = (
 
 SV_OK, SV_ERR_ARG, SV_ERR_OOM, SV_ERR_CUDA, SV_ERR_TIMEOUT, SV_ERR_STATE = range(6)
 SV_H, SV_T, SV_SX, SV_SY, SV_CZ, SV_P0, SV_P1, SV_Z, SV_TDG, SV_SXDG, SV_SYDG = range(11)
-SV_PREC_PLAIN, SV_PREC_TF32X3, SV_PREC_PERGATE = 0, 1, 3
+SV_PREC_PLAIN, SV_PREC_TF32X3, SV_PREC_F16X3, SV_PREC_PERGATE = 0, 1, 2, 3
 
 GATE_DTYPE = np.dtype([('kind', 'u1'), ('q0', 'u1'), ('q1', 'u1'), ('pad', 'u1'), ('layer', '<u4')])
 

@@ -44,9 +44,11 @@ def run_gpu(lat, **kw):
 
 
 TC = sv.SV_PREC_TF32X3
+H16 = sv.SV_PREC_F16X3
 MODES = [dict(), dict(tile_bits=10, low_bits=4, fuse_k=5), dict(tile_bits=8, low_bits=2, fuse_k=3),
          dict(tile_bits=12, low_bits=5, fuse_k=4), dict(precision=sv.SV_PREC_PERGATE),
-         dict(precision=TC), dict(precision=TC, tile_bits=12), dict(precision=TC, tile_bits=12, low_bits=3)]
+         dict(precision=TC), dict(precision=TC, tile_bits=12), dict(precision=TC, tile_bits=12, low_bits=3),
+         dict(precision=H16), dict(precision=H16, tile_bits=12)]
 
 
 @pytest.mark.parametrize('kw', MODES)
@@ -74,7 +76,7 @@ def test_sizes_match_oracle(lat):
     n, gates = oracle_gates(lat)
     want = csim.run(n, gates)
     for kw in (dict(), dict(tile_bits=min(13, max(6, n)), low_bits=min(4, n), fuse_k=5), dict(precision=TC),
-               dict(precision=TC, tile_bits=12)):
+               dict(precision=TC, tile_bits=12), dict(precision=H16), dict(precision=H16, tile_bits=12)):
         psi, norm2, _ = run_gpu(lat, **kw)
         assert rel_l2(psi, want) <= REL_L2, kw
         assert abs(norm2 - 1) <= NORM_TOL
@@ -125,7 +127,8 @@ def _oracle_apply(n, gl, psi):
 
 @pytest.mark.parametrize('n,kw', [(7, {}), (13, {}), (18, {}), (18, dict(tile_bits=9, low_bits=3, fuse_k=2)),
                                   (16, dict(precision=sv.SV_PREC_PERGATE)), (12, dict(precision=TC)),
-                                  (17, dict(precision=TC)), (19, dict(precision=TC, tile_bits=12))])
+                                  (17, dict(precision=TC)), (19, dict(precision=TC, tile_bits=12)),
+                                  (17, dict(precision=H16)), (19, dict(precision=H16, tile_bits=12))])
 def test_all_gate_kinds_from_zero_and_loaded_state(n, kw):
     gl = _random_gate_list(n, 120, seed=n)
     # from |0..0> (no H layer: the first pass generates |0..0>)
@@ -163,7 +166,7 @@ def test_projectors_zero_exactly():
     assert np.count_nonzero(psi[~dead]) == np.count_nonzero(~dead)
 
 
-@pytest.mark.parametrize('prec', [sv.SV_PREC_PLAIN, TC])
+@pytest.mark.parametrize('prec', [sv.SV_PREC_PLAIN, TC, H16])
 def test_inverse_circuit_returns_to_zero_state(prec):
     lat = inputs.lattice_for(4, 5, 16, seed=21)
     g = sv.sv_generate_circuit(lat)
@@ -224,7 +227,7 @@ def test_branch_amplitudes_small_cut_match_oracle():
     want_full = csim.run(n, gates)[np.array(bits, dtype=np.int64)]
     want_branch = csim.branch_amplitudes(n, gates, half_a, bits)
     assert rel_l2(want_branch, want_full) < 1e-12
-    for kw in (dict(), dict(precision=TC)):
+    for kw in (dict(), dict(precision=TC), dict(precision=H16)):
         got = sv.sv_branch_amplitudes(lat, half_a, bits, sv.options(**kw))
         assert rel_l2(got, want_full) <= REL_L2, kw
 
@@ -292,7 +295,7 @@ def test_many_square_roots_in_one_stage():
     for i in range(200):
         gl.append((('SX', 'SY', 'SXDG')[i % 3], i % 5, -1))
     want = _oracle_apply(n, gl, ov.zero_state(n))
-    for kw in (dict(), dict(precision=TC)):
+    for kw in (dict(), dict(precision=TC), dict(precision=H16)):
         h = sv.sv_create(n, sv.options(**kw))
         try:
             sv.sv_apply_circuit(h, sv.gates_from_tuples([(_CODE[k], a, 0, 1) for (k, a, _b) in gl]))
