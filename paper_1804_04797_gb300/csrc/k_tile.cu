@@ -42,7 +42,7 @@ tile_pass_kernel(float2 *__restrict__ psi, DevPlanView plan, int pass_index, uin
     process_tile_plain(psi, plan, P, chunk_off, tile, tile_id);
 }
 
-int g_tile_blocks_per_sm = 0;
+int g_tile_blocks_per_sm[svp::kMaxTileBits + 1] = {};  // resident CTAs per SM, by tile size
 
 }  // namespace
 
@@ -56,15 +56,17 @@ cudaError_t launch_tile_pass(float2 *psi, int n, const DevPlanView &plan, int pa
     cudaError_t e = cudaFuncSetAttribute(tile_pass_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)(sizeof(float2) << svp::kMaxTileBits));
     if (e != cudaSuccess) return e;
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&g_tile_blocks_per_sm, tile_pass_kernel, kThreads,
-                                                      sizeof(float2) << svp::kMaxTileBits);
-    if (e != cudaSuccess) return e;
-    if (g_tile_blocks_per_sm < 1) g_tile_blocks_per_sm = 1;
     configured = true;
   }
-  const uint64_t tiles = 1ull << (n - m);
   const int threads = 1 << (m - kR);
-  uint64_t grid = (uint64_t)device_sm_count() * (uint64_t)g_tile_blocks_per_sm;
+  if (g_tile_blocks_per_sm[m] == 0) {
+    int per_sm = 0;
+    cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, tile_pass_kernel, threads, smem);
+    if (e != cudaSuccess) return e;
+    g_tile_blocks_per_sm[m] = per_sm < 1 ? 1 : per_sm;
+  }
+  const uint64_t tiles = 1ull << (n - m);
+  uint64_t grid = (uint64_t)device_sm_count() * (uint64_t)g_tile_blocks_per_sm[m];
   if (grid > tiles) grid = tiles;
   tile_pass_kernel<<<(unsigned)grid, threads, smem, st>>>(psi, plan, pass_index, tiles);
   return cudaGetLastError();
