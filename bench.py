@@ -216,13 +216,14 @@ def main():
     ap.add_argument('--steps', type=int, default=5)
     ap.add_argument('--warmup', type=int, default=3)
     ap.add_argument('--impl', default='ours', choices=['ours', 'reference'])
-    ap.add_argument('--qubits', type=int, default=34, help='34 (headline) or a smaller lattice for tests')
+    ap.add_argument('--qubits', type=int, default=34, help='34 (headline); 30, 28 or 16 for smaller cases (profiling, tests)')
     ap.add_argument('--no-fused', action='store_true')
     ap.add_argument('--paths', default='plain,tf32x3,f16x3', help='comma list of plain, tf32x3, f16x3, pergate')
     ap.add_argument('--tile-bits', type=int, default=0, help='tile qubits of the tile passes (0 = default 13)')
     ap.add_argument('--workload', default='34q', choices=['34q', 'batch', 'branch42'],
                     help='34q: the headline circuit; batch: the 512-circuit uneven batch; branch42: the '
                          '42-qubit cut-branch amplitude task (secondary lines)')
+    ap.add_argument('--depth', type=int, default=0, help='override the lattice depth (profiling of smaller cases)')
     ap.add_argument('--no-cpu', action='store_true')
     args = ap.parse_args()
 
@@ -246,7 +247,9 @@ def main():
         import torch.distributed as dist
         dist.init_process_group('nccl', device_id=torch.device('cuda', local))
 
-    lat = {34: inputs.C34, 30: inputs.C30, 16: inputs.C16}.get(args.qubits, inputs.C34)
+    lat = {34: inputs.C34, 30: inputs.C30, 28: inputs.C28, 16: inputs.C16}.get(args.qubits, inputs.C34)
+    if args.depth > 0:
+        lat = inputs.Lattice(lat.rows, lat.cols, lat.removed_mask, args.depth, lat.seed)
     n = lat.n_qubits
     gates = sv.sv_generate_circuit(lat)
     stream = torch.cuda.Stream()
@@ -353,7 +356,8 @@ def main():
         'scaling': 'weak', 'vs_baseline': None, 'dtype': 'c64' if best_name == 'plain' else 'c64/' + best_name,
         'data': 'synthetic',
         'config': {'workload': '34-qubit 6x6-minus-corners lattice circuit, depth 30, seed 0 (478 gates)'
-                   if n == 34 else '%d-qubit lattice circuit' % n,
+                   if lat == inputs.C34 else '%d-qubit %dx%d lattice circuit, depth %d' % (n, lat.rows, lat.cols,
+                                                                                          lat.depth),
                    'state_bytes': 8 * 2 ** n, 'l2': 'state 137 GB >> L2 129 MB, no flush needed',
                    'path': best_name, 'replicas': world},
         'roofline': {'bound': 'hbm', 'kernel': {'plain': 'tile_pass_kernel', 'tf32x3': 'fused_pass_kernel<tf32>',

@@ -48,7 +48,9 @@ svp::Options plan_options(const sv_options &o) {
   p.m = o.tile_bits > 0 ? o.tile_bits : 13;
   p.c = o.low_bits > 0 ? o.low_bits : 4;
   p.fused = o.precision == SV_PREC_TF32X3 || o.precision == SV_PREC_F16X3;
-  p.rk = 5;  // register qubits per thread of the tile kernels
+  p.pack = !p.fused;  // the plain kernel runs packed plans
+  // register qubits per thread of the tile kernels (packed: besides qubit 0)
+  p.rk = p.pack ? svk::tile_pass_register_slots() : 5;
   p.r = std::min(o.fuse_k > 0 ? o.fuse_k : p.rk, p.rk);
   return p;
 }
@@ -253,6 +255,9 @@ sv_status apply_gates(sv_state *s, const std::vector<svp::Gate> &g) {
   // the tensor-core kernel takes 12- or 13-qubit tiles; smaller states use the plain one
   if (po.fused && std::min(po.m, s->n) < 12) {
     po.fused = false;
+    po.pack = true;
+    po.rk = svk::tile_pass_register_slots();
+    po.r = std::min(po.r, po.rk);
   }
   if (!svp::build_plan(s->n, g, po, s->fresh, &P, &err)) return fail(SV_ERR_ARG, err ? err : "planning failed");
   const bool f16 = s->opts.precision == SV_PREC_F16X3;

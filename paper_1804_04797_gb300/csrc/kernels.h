@@ -26,10 +26,12 @@ struct DevPlanView {
 // K0: write |0..0> (uniform == false) or the uniform 2^{-n/2} state.  Write-only.
 cudaError_t launch_init(float2 *psi, int n, bool uniform, float amp, cudaStream_t st);
 
-// K1/K2/K3 plain tile pass: one sweep over all tiles of one pass of the plan.
+// K1/K2/K3 plain tile pass: one sweep over all tiles of one pass of a packed plan.
 // host_pass is the host copy of the same pass (tile shape, flags).
 cudaError_t launch_tile_pass(float2 *psi, int n, const DevPlanView &plan, int pass_index,
                              const svp::DevPass &host_pass, cudaStream_t st);
+// Register slots besides the pack bit of the packed plain kernel (the planner's rk).
+int tile_pass_register_slots();
 
 // K4 fused tensor-core tile pass (tcgen05, split-TF32).
 // tile_bits 12 or 13; f16: F16x3 operands, else TF32x3

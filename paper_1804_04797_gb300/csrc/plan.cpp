@@ -117,6 +117,26 @@ void order_group_bits(int m, const std::vector<int> &nonr, uint8_t *out) {
   for (size_t i = 0; i < all.size(); ++i) out[i] = (uint8_t)all[i];
 }
 
+// Packed tiles: pair index k (tile bits 1..m-1) is stored at 16-byte slot
+// k ^ ((k>>3 ^ k>>6 ^ k>>9) & 7); pair bit i toggles slot bit (i mod 3).  A quarter warp
+// (8 lanes, one 128-byte wavefront of 16-byte accesses) is conflict-free when its three
+// lane bits have distinct residues.
+uint32_t pack_phys(uint32_t k) { return k ^ (((k >> 3) ^ (k >> 6) ^ (k >> 9)) & 7u); }
+uint32_t pack_offset(int tile_bit) { return 16u * pack_phys(1u << (tile_bit - 1)); }
+
+void order_group_bits_packed(const std::vector<int> &nonr, uint8_t *out) {
+  std::vector<int> lanes, rest;
+  bool used_res[3] = {false, false, false};
+  for (int b : nonr) {
+    const int res = (b - 1) % 3;
+    if ((int)lanes.size() < 3 && !used_res[res]) { used_res[res] = true; lanes.push_back(b); }
+    else rest.push_back(b);
+  }
+  std::vector<int> all = lanes;
+  for (int b : rest) all.push_back(b);
+  for (size_t i = 0; i < all.size(); ++i) out[i] = (uint8_t)all[i];
+}
+
 }  // namespace
 
 bool build_plan(int n, const std::vector<Gate> &gates, const Options &opt, bool fresh_state,
@@ -126,9 +146,12 @@ bool build_plan(int n, const std::vector<Gate> &gates, const Options &opt, bool 
   P.n = n;
   const int m = std::min(opt.m, n);
   const int c = std::min(opt.c, m);
-  const int rk = std::min(opt.rk, m);
+  const bool pack = opt.pack;
+  // packed: tile bit 0 is in every stage, besides up to rk register slots
+  const int rk = std::min(opt.rk, pack ? m - 1 : m);
   const int r = std::min(std::min(opt.r, rk), m);
   if (m > kMaxTileBits || rk > kMaxReg || r < 1 || c < 0 || m - rk > 12) { *err = "bad tile shape"; return false; }
+  if (pack && (rk < 1 || m < rk + 1 || c < 1)) { *err = "packed plan needs tiles of >= rk + 1 qubits"; return false; }
 
   // leading layer of H on every qubit of a fresh state -> uniform first pass
   size_t start = 0;
@@ -173,8 +196,9 @@ bool build_plan(int n, const std::vector<Gate> &gates, const Options &opt, bool 
         if (!(S & (1ull << q))) dp.ntq[ni++] = (uint8_t)q;
       dp.nt = (uint8_t)ni;
     }
+    if (pack) dp.flags |= PF_PACKED;
     if (first_pass && fresh_state) {
-      dp.flags = P.init_uniform ? PF_INIT_UNIFORM : PF_INIT_ZERO;
+      dp.flags |= P.init_uniform ? PF_INIT_UNIFORM : PF_INIT_ZERO;
       dp.init_amp = P.init_uniform ? (float)std::pow(2.0, -0.5 * n) : 1.0f;
       P.hbm_bytes += 8.0 * amps;
     } else {
@@ -223,7 +247,11 @@ bool build_plan(int n, const std::vector<Gate> &gates, const Options &opt, bool 
                 locals |= 1u << a;
                 if (!((Rm >> a) & 1u)) all_in = false;
               }
-              if (all_in) { if (inner) inner->push_back(now[i]); }
+              // The tensor-core kernel applies the inner gates as one matrix, so a diagonal
+              // gate on a qubit outside the register set must follow it (a post gate) and
+              // closes its register qubits for the rest of the stage.  The plain kernels
+              // apply it in place as a phase conditioned on the fixed qubit.
+              if (all_in || !opt.fused) { if (inner) inner->push_back(now[i]); }
               else { if (post) post->push_back(now[i]); closed |= locals; }
               placed = true;
             }
@@ -243,11 +271,11 @@ bool build_plan(int n, const std::vector<Gate> &gates, const Options &opt, bool 
     while (left > 0) {
       // register bits by greedy lookahead: add the tile bit that lets the stage place the
       // most non-diagonal gates (then the most gates), up to r bits
-      uint32_t Rm = 0;
+      uint32_t Rm = pack ? 1u : 0u;
       std::pair<int, int> cur;
       {
         std::vector<char> tmp = done;
-        cur = run_stage(0, tmp, nullptr, nullptr);
+        cur = run_stage(Rm, tmp, nullptr, nullptr);
       }
       for (int round = 0; round < r; ++round) {
         int best = -1;
@@ -266,41 +294,54 @@ bool build_plan(int n, const std::vector<Gate> &gates, const Options &opt, bool 
       const std::pair<int, int> placed = run_stage(Rm, done, &inner, &post);
       left -= (size_t)placed.second;
       std::vector<int> R;
-      for (int bb = 0; bb < m; ++bb)
+      for (int bb = pack ? 1 : 0; bb < m; ++bb)
         if ((Rm >> bb) & 1u) R.push_back(bb);
       // device stage
       DevStage ds;
       std::memset(&ds, 0, sizeof(ds));
       ds.r = (uint8_t)R.size();
-      // the kernel holds 2^rk amplitudes per thread: pad the register
+      // the kernel holds 2^rk amplitudes (packed: pairs) per thread: pad the register
       // bits with unused tile bits (the fused kernel uses the first r of them)
       std::vector<int> rb = R;
       const int rpad = rk;
-      for (int b = 0; (int)rb.size() < rpad && b < m; ++b)
+      for (int b = pack ? 1 : 0; (int)rb.size() < rpad && b < m; ++b)
         if (std::find(rb.begin(), rb.end(), b) == rb.end()) rb.push_back(b);
       for (int j = 0; j < rpad; ++j) ds.rbit[j] = (uint8_t)rb[j];
       std::vector<int> nonr;
-      for (int b = 0; b < m; ++b)
+      for (int b = pack ? 1 : 0; b < m; ++b)
         if (std::find(rb.begin(), rb.end(), b) == rb.end()) nonr.push_back(b);
-      order_group_bits(m, nonr, ds.nonr);
-      for (int half = 0; half < kGroupEntries / 16; ++half) {
+      if (pack) order_group_bits_packed(nonr, ds.nonr);
+      else order_group_bits(m, nonr, ds.nonr);
+      const int group_bits = (int)nonr.size();
+      for (int half = 0; half < kRegEntry / 16; ++half) {
         for (int v = 0; v < 16; ++v) {
           DevGroupEntry ge;
           std::memset(&ge, 0, sizeof(ge));
           for (int i = 0; i < 4; ++i) {
             const int gi = 4 * half + i;
-            if (!((v >> i) & 1) || gi >= m - rpad) continue;
-            ge.L |= 1u << ds.nonr[gi];
+            if (!((v >> i) & 1) || gi >= group_bits) continue;
+            ge.L ^= pack ? pack_offset(ds.nonr[gi]) : (1u << ds.nonr[gi]);
             ge.G |= 1ull << dp.tq[ds.nonr[gi]];
           }
           P.gtab.push_back(ge);
         }
+      }
+      for (int e = kRegEntry; e < kGroupEntries; ++e) {
+        DevGroupEntry ge;
+        std::memset(&ge, 0, sizeof(ge));
+        const int j = e - kRegEntry;
+        if (pack && j < rpad) {
+          ge.L = pack_offset(rb[j]);
+          ge.G = 1ull << dp.tq[rb[j]];
+        }
+        P.gtab.push_back(ge);
       }
       ds.op_begin = (uint32_t)P.ops.size();
       ds.diag_only = inner.empty() ? 1 : 0;
       auto reg_of = [&](int q) -> int {
         const int a = local_of[q];
         if (a < 0) return -1;
+        if (pack && a == 0) return kPackSlot;
         for (int j = 0; j < rpad; ++j)
           if (rb[j] == a) return j;
         return -1;
@@ -308,8 +349,30 @@ bool build_plan(int n, const std::vector<Gate> &gates, const Options &opt, bool 
       auto emit = [&](uint8_t act, int j, int k, int arg, uint64_t cm, uint64_t cv) {
         DevOp o;
         std::memset(&o, 0, sizeof(o));
+        if ((act == A_CZ || act == A_PEQ) && j > k) std::swap(j, k);  // both symmetric
         o.act = act; o.j = (uint8_t)(j < 0 ? 0 : j); o.k = (uint8_t)(k < 0 ? 0 : k);
         o.arg = (uint8_t)arg; o.cmask = cm; o.cval = cv;
+        if (pack) {
+          switch (act) {
+            case A_H: o.code = P_PAIR + 0 + o.j; break;
+            case A_SX: o.code = P_PAIR + 6 + o.j; break;
+            case A_SY: o.code = P_PAIR + 12 + o.j; break;
+            case A_SXDG: o.code = P_PAIR + 18 + o.j; break;
+            case A_SYDG: o.code = P_PAIR + 24 + o.j; break;
+            case A_T: o.code = P_DIAG + 0 + o.j; break;
+            case A_TDG: o.code = P_DIAG + 6 + o.j; break;
+            case A_Z: o.code = P_DIAG + 12 + o.j; break;
+            case A_P0: o.code = P_DIAG + 18 + o.j; break;
+            case A_P1: o.code = P_DIAG + 24 + o.j; break;
+            case A_CZ: o.code = P_CZ + 6 * o.j + o.k; break;
+            case A_PEQ: o.code = P_PEQ + 6 * o.j + o.k; break;
+            case A_PHASE: o.code = P_PHASE; break;
+            case A_ZERO: o.code = P_ZERO; break;
+            default: o.code = P_U + o.j; break;
+          }
+          P.ops.push_back(o);
+          return;
+        }
         switch (act) {
           case A_H: o.code = C_PAIR + 0 + o.j; break;
           case A_SX: o.code = C_PAIR + 5 + o.j; break;
@@ -363,6 +426,32 @@ bool build_plan(int n, const std::vector<Gate> &gates, const Options &opt, bool 
       if (!opt.fused)
         for (int gi : inner) lower(gi);
       for (int gi : post) lower(gi);
+      if (pack) {
+        // the packed kernel applies the factors 1/2 of the square roots in bulk: a
+        // P_SCALE after every kMaxDeferred of them, the remainder at the stage's end;
+        // non-diagonal gates, T and two-qubit ops of a packed plan are unconditional
+        std::vector<DevOp> ops(P.ops.begin() + ds.op_begin, P.ops.end());
+        P.ops.resize(ds.op_begin);
+        int pending = 0;
+        for (const DevOp &o : ops) {
+          const bool cond_ok = o.cmask == 0 || o.act == A_Z || o.act == A_P0 || o.act == A_P1 ||
+                               o.act == A_PHASE || o.act == A_ZERO;
+          if (!cond_ok) { *err = "packed plan: conditional op of an unconditional kind"; return false; }
+          P.ops.push_back(o);
+          if (o.act == A_SX || o.act == A_SY || o.act == A_SXDG || o.act == A_SYDG) {
+            if (++pending == kMaxDeferred) {
+              DevOp sc;
+              std::memset(&sc, 0, sizeof(sc));
+              sc.act = A_COUNT;
+              sc.code = P_SCALE;
+              sc.arg = (uint8_t)kMaxDeferred;
+              P.ops.push_back(sc);
+              pending = 0;
+            }
+          }
+        }
+        ds.halves = (uint8_t)pending;
+      }
       if (P.ops.size() - ds.op_begin > 65535) { *err = "stage too large"; return false; }
       ds.op_count = (uint16_t)(P.ops.size() - ds.op_begin);
       P.stages.push_back(ds);

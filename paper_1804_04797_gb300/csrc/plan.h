@@ -58,7 +58,8 @@ struct DevOp {
 };
 
 // Flat dispatch codes: one switch in the kernel selects both the action and the
-// register bit(s), so each op costs one indirect branch.
+// register bit(s), so each op costs one indirect branch.  Code numbers the ops of the
+// unpacked tile kernels (five register slots); PCode those of the packed plain kernel.
 enum Code : uint8_t {
   C_PAIR = 0,     // + 5*g + j, g in {H, SX, SY, SXDG, SYDG}       (0..24)
   C_DIAG = 25,    // + 5*d + j, d in {T, TDG, Z, P0, P1}            (25..49)
@@ -70,15 +71,38 @@ enum Code : uint8_t {
   C_COUNT = 107
 };
 
+// Packed plan (PF_PACKED): a thread holds 32 pairs of amplitudes that differ only in
+// tile bit 0 (the pack bit), each pair as two float2 = (re, re'), (im, im') that the
+// packed f32x2 instructions update together.  Register slots 0..4 are the stage's
+// other register bits, slot 5 is the pack bit.  Two-qubit codes have j < k.
+constexpr int kPackSlot = 5;
+enum PCode : uint8_t {
+  P_PAIR = 0,     // + 6*g + j, g in {H, SX, SY, SXDG, SYDG}       (0..29)
+  P_DIAG = 30,    // + 6*d + j, d in {T, TDG, Z, P0, P1}            (30..59)
+  P_CZ = 60,      // + 6*j + k                                       (60..95)
+  P_PEQ = 96,     // + 6*j + k                                       (96..131)
+  P_PHASE = 132,  // scalar phase w^arg (accumulated, applied once)
+  P_ZERO = 133,   // the whole group becomes zero
+  P_U = 134,      // + j, general 2x2                                 (134..139)
+  P_SCALE = 140,  // every element times 2^-arg (deferred factors 1/2 of square roots)
+  P_COUNT = 141
+};
+// A packed stage defers the factors 1/2 of its square-root gates: at most kMaxDeferred
+// are pending at any point (a P_SCALE op applies them), the rest is DevStage::halves.
+constexpr int kMaxDeferred = 64;
+
 // Stage group addressing: group index g of a thread -> (tile-local index L0, global
-// index offset G0) of its element 0 = entry[g & 15] | entry[16 + ((g >> 4) & 15)] |
-// entry[32 + (g >> 8)]; kGroupEntries per stage.
+// index offset G0) of its element 0 = entry[g & 15] ^ entry[16 + ((g >> 4) & 15)] ^
+// entry[32 + (g >> 8)]; kGroupEntries per stage.  In a packed plan L is the swizzled
+// shared-memory byte offset of the element's pair (the swizzle is linear over XOR), and
+// entries kRegEntry + j hold, in L, the byte-offset mask of register slot j.
 struct DevGroupEntry {
   uint32_t L;
   uint32_t pad;
   uint64_t G;
 };
-constexpr int kGroupEntries = 48;
+constexpr int kGroupEntries = 56;
+constexpr int kRegEntry = 48;
 static_assert(sizeof(DevOp) == 24, "DevOp layout");
 
 constexpr int kMaxTileBits = 13;
@@ -87,7 +111,8 @@ constexpr int kMaxReg = 5;
 struct DevStage {
   uint8_t r;                   // register bits in use (<= kMaxReg); the rest are padding
   uint8_t rbit[kMaxReg];       // tile-local bit of register bit j (all distinct, padded)
-  uint8_t nonr[kMaxTileBits];  // tile-local bits of the group index, lane bits first
+  uint8_t nonr[kMaxTileBits - 1];  // tile-local bits of the group index, lane bits first
+  uint8_t halves;              // packed plan: factors 1/2 left to apply at the stage's end
   uint8_t diag_only;           // no inner gates: nothing for the tensor cores
   uint32_t op_begin;           // into the plan's op array
   uint16_t op_count;
@@ -101,6 +126,7 @@ enum PassFlags : uint8_t {
   PF_INIT_UNIFORM = 1,  // tile content is 2^{-n/2} everywhere; nothing is read
   PF_INIT_ZERO = 2,     // tile content is |0..0>; nothing is read
   PF_UNITARY = 4,       // no projector in the pass: every tile keeps its norm
+  PF_PACKED = 8,        // packed plan: stages of tile bit 0 + up to rk bits, PCode ops
 };
 
 struct DevPass {
@@ -121,6 +147,7 @@ struct Options {
   int r = 5;         // qubits a stage may act on (<= rk)
   int rk = 5;        // register qubits per thread of the kernel that runs the plan
   bool fused = false;
+  bool pack = false; // packed plain kernel: tile bit 0 joins every stage as the pack bit
 };
 
 struct Plan {
@@ -129,7 +156,7 @@ struct Plan {
   std::vector<DevStage> stages;
   std::vector<DevOp> ops;
   std::vector<float> mats;          // 8 floats per A_U matrix (re/im of a,b,c,d)
-  std::vector<DevGroupEntry> gtab;  // 32 entries per stage
+  std::vector<DevGroupEntry> gtab;  // kGroupEntries per stage
   std::vector<int32_t> order;       // executed gate index, in execution order
   std::vector<int32_t> pass_of;     // pass of each executed gate
   std::vector<std::vector<int>> stage_gates;  // per stage: gate indices (inner, in order)

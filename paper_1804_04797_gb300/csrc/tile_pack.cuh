@@ -1,0 +1,481 @@
+// Packed plain tile pass: the register form of the fp32 CUDA-core kernel.
+//
+// A thread holds 32 PAIRS of amplitudes.  The two amplitudes of a pair differ only in
+// tile bit 0 (the pack bit, always qubit 0: two neighbours in memory), and a pair is
+// kept as two float2 registers R = (re, re'), I = (im, im').  Blackwell's packed fp32
+// instructions (FADD2/FMUL2/FFMA2) update both halves at once, so every gate on one of
+// the five other register slots costs half the instructions of the one-amplitude form.
+// A stage acts on six qubits (the pack bit + five), a thread on 64 amplitudes.
+//
+// Shared memory holds the tile as 16-byte pairs (re, re', im, im') at a swizzled slot
+// (see pack_phys); the swizzle is linear over XOR, so a group's 32 slot addresses are
+// the XOR of its base with the register-slot masks the planner stores.  Conditional
+// diagonal ops (a CZ or projector whose other qubit is not a register bit) become a
+// multiplication by a per-thread factor, so no op diverges within a warp.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include "kernels.h"
+
+namespace svk {
+namespace tpk {
+
+using svp::DevOp;
+using svp::DevPass;
+using svp::DevStage;
+
+// Register slots besides the pack bit (the translation unit picks: 5 = 64 amplitudes per
+// thread, 4 = 32).
+#ifndef SV_PACK_R
+#define SV_PACK_R 5
+#endif
+constexpr int kPR = SV_PACK_R;
+static_assert(kPR >= 1 && kPR <= svp::kMaxReg, "pack register slots");
+constexpr int kP = 1 << kPR;       // pairs per thread
+constexpr float kS2 = 0.70710678118654752440f;
+constexpr float kS2lo = 1.21016171e-8f;  // 1/sqrt2 - kS2: v*kS2 + v*kS2lo rounds v/sqrt2 to nearest
+
+__device__ __forceinline__ float2 f2(float a, float b) { return make_float2(a, b); }
+__device__ __forceinline__ float2 add2(float2 a, float2 b) { return __fadd2_rn(a, b); }
+__device__ __forceinline__ float2 mul2(float2 a, float2 b) { return __fmul2_rn(a, b); }
+__device__ __forceinline__ float2 fma2(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
+__device__ __forceinline__ float2 sub2(float2 a, float2 b) {
+  unsigned long long r;
+  asm("sub.rn.f32x2 %0, %1, %2;"
+      : "=l"(r)
+      : "l"(*reinterpret_cast<unsigned long long *>(&a)), "l"(*reinterpret_cast<unsigned long long *>(&b)));
+  return *reinterpret_cast<float2 *>(&r);
+}
+__device__ __forceinline__ float2 rs2x2(float2 v) { return fma2(v, f2(kS2, kS2), mul2(v, f2(kS2lo, kS2lo))); }
+__device__ __forceinline__ float rs2(float v) { return fmaf(v, kS2, v * kS2lo); }
+
+// ---- one-qubit gates: x = (xr, xi), y = (yr, yi), each component a float2 over pairs -----
+// (the same formulas serve the scalar case of the pack slot with float in place of float2)
+template <class T>
+struct Ops;
+template <>
+struct Ops<float2> {
+  __device__ __forceinline__ static float2 add(float2 a, float2 b) { return add2(a, b); }
+  __device__ __forceinline__ static float2 sub(float2 a, float2 b) { return sub2(a, b); }
+  __device__ __forceinline__ static float2 rs(float2 a) { return rs2x2(a); }
+};
+template <>
+struct Ops<float> {
+  __device__ __forceinline__ static float add(float a, float b) { return a + b; }
+  __device__ __forceinline__ static float sub(float a, float b) { return a - b; }
+  __device__ __forceinline__ static float rs(float a) { return rs2(a); }
+};
+
+struct GH {  // (x + y)/sqrt2, (x - y)/sqrt2
+  template <class T>
+  __device__ __forceinline__ static void f(T &xr, T &xi, T &yr, T &yi) {
+    using O = Ops<T>;
+    const T sr = O::add(xr, yr), si = O::add(xi, yi), dr = O::sub(xr, yr), di = O::sub(xi, yi);
+    xr = O::rs(sr); xi = O::rs(si); yr = O::rs(dr); yi = O::rs(di);
+  }
+};
+// The square roots without their factor 1/2 (counted and applied once per stage):
+// X^{1/2}: x' = s + i d, y' = s - i d, with s = x + y, d = x - y
+struct GSX {
+  template <class T>
+  __device__ __forceinline__ static void f(T &xr, T &xi, T &yr, T &yi) {
+    using O = Ops<T>;
+    const T sr = O::add(xr, yr), si = O::add(xi, yi), dr = O::sub(xr, yr), di = O::sub(xi, yi);
+    xr = O::sub(sr, di); xi = O::add(si, dr); yr = O::add(sr, di); yi = O::sub(si, dr);
+  }
+};
+struct GSXDG {  // x' = s - i d, y' = s + i d
+  template <class T>
+  __device__ __forceinline__ static void f(T &xr, T &xi, T &yr, T &yi) {
+    using O = Ops<T>;
+    const T sr = O::add(xr, yr), si = O::add(xi, yi), dr = O::sub(xr, yr), di = O::sub(xi, yi);
+    xr = O::add(sr, di); xi = O::sub(si, dr); yr = O::sub(sr, di); yi = O::add(si, dr);
+  }
+};
+// Y^{1/2}: x' = (1+i) d, y' = (1+i) s
+struct GSY {
+  template <class T>
+  __device__ __forceinline__ static void f(T &xr, T &xi, T &yr, T &yi) {
+    using O = Ops<T>;
+    const T sr = O::add(xr, yr), si = O::add(xi, yi), dr = O::sub(xr, yr), di = O::sub(xi, yi);
+    xr = O::sub(dr, di); xi = O::add(dr, di); yr = O::sub(sr, si); yi = O::add(sr, si);
+  }
+};
+// (Y^{1/2})^dagger: x' = (1-i) s, y' = -(1-i) d = (1-i) e with e = y - x
+struct GSYDG {
+  template <class T>
+  __device__ __forceinline__ static void f(T &xr, T &xi, T &yr, T &yi) {
+    using O = Ops<T>;
+    const T sr = O::add(xr, yr), si = O::add(xi, yi), er = O::sub(yr, xr), ei = O::sub(yi, xi);
+    xr = O::add(sr, si); xi = O::sub(si, sr); yr = O::add(er, ei); yi = O::sub(ei, er);
+  }
+};
+
+// ---- diagonal phases on one element (r, i) ----------------------------------------------
+struct DT {  // times e^{i pi/4}
+  template <class T>
+  __device__ __forceinline__ static void f(T &r, T &i) {
+    using O = Ops<T>;
+    const T a = O::sub(r, i), b = O::add(r, i);
+    r = O::rs(a); i = O::rs(b);
+  }
+};
+struct DTDG {  // times e^{-i pi/4}
+  template <class T>
+  __device__ __forceinline__ static void f(T &r, T &i) {
+    using O = Ops<T>;
+    const T a = O::add(r, i), b = O::sub(i, r);
+    r = O::rs(a); i = O::rs(b);
+  }
+};
+
+// ---- actions on a thread's 32 pairs -------------------------------------------------------
+using Regs = float2[kP];
+
+// gate G on register slot J (pairs p and p | 2^J)
+template <class G, int J>
+__device__ __forceinline__ void pairs(Regs &R, Regs &I) {
+  if constexpr (J >= kPR) return;
+#pragma unroll
+  for (int p = 0; p < kP; ++p)
+    if (!(p & (1 << J))) G::f(R[p], I[p], R[p | (1 << J)], I[p | (1 << J)]);
+}
+// gate G on the pack bit: inside every pair
+template <class G>
+__device__ __forceinline__ void pairs_pack(Regs &R, Regs &I) {
+#pragma unroll
+  for (int p = 0; p < kP; ++p) G::f(R[p].x, I[p].x, R[p].y, I[p].y);
+}
+// phase D where register slot J is 1
+template <class D, int J>
+__device__ __forceinline__ void diag(Regs &R, Regs &I) {
+  if constexpr (J >= kPR) return;
+#pragma unroll
+  for (int p = 0; p < kP; ++p)
+    if (p & (1 << J)) D::f(R[p], I[p]);
+}
+// phase D where the pack bit is 1
+template <class D>
+__device__ __forceinline__ void diag_pack(Regs &R, Regs &I) {
+#pragma unroll
+  for (int p = 0; p < kP; ++p) D::f(R[p].y, I[p].y);
+}
+// factor f (a sign or a 0/1 projector) where register slot J equals B
+template <int J, int B>
+__device__ __forceinline__ void factor(Regs &R, Regs &I, float f) {
+  if constexpr (J >= kPR) return;
+  const float2 ff = f2(f, f);
+#pragma unroll
+  for (int p = 0; p < kP; ++p)
+    if (((p >> J) & 1) == B) { R[p] = mul2(R[p], ff); I[p] = mul2(I[p], ff); }
+}
+// factor f where the pack bit equals B
+template <int B>
+__device__ __forceinline__ void factor_pack(Regs &R, Regs &I, float f) {
+  const float2 ff = B ? f2(1.f, f) : f2(f, 1.f);
+#pragma unroll
+  for (int p = 0; p < kP; ++p) { R[p] = mul2(R[p], ff); I[p] = mul2(I[p], ff); }
+}
+// CZ (EQ false: -1 where slots J and K are both 1) or the branch projector (EQ true:
+// 0 where they differ); J < K, K may be the pack slot
+template <int J, int K, bool EQ>
+__device__ __forceinline__ void two(Regs &R, Regs &I) {
+  if constexpr (J >= kPR || (K >= kPR && K != svp::kPackSlot)) return;
+#pragma unroll
+  for (int p = 0; p < kP; ++p) {
+    const int bj = (p >> J) & 1;
+    float2 ff;
+    if constexpr (K == svp::kPackSlot) {
+      if (EQ) ff = bj ? f2(0.f, 1.f) : f2(1.f, 0.f);
+      else if (bj) ff = f2(1.f, -1.f);
+      else continue;
+    } else {
+      const int bk = (p >> K) & 1;
+      if (EQ) {
+        if (bj == bk) continue;
+        ff = f2(0.f, 0.f);
+      } else {
+        if (!(bj && bk)) continue;
+        ff = f2(-1.f, -1.f);
+      }
+    }
+    R[p] = mul2(R[p], ff);
+    I[p] = mul2(I[p], ff);
+  }
+}
+__device__ __forceinline__ void scale_all(Regs &R, Regs &I, float f) {
+  const float2 ff = f2(f, f);
+#pragma unroll
+  for (int p = 0; p < kP; ++p) { R[p] = mul2(R[p], ff); I[p] = mul2(I[p], ff); }
+}
+
+// every element times w^p, w = e^{i pi/4}
+__device__ __forceinline__ void phase_all(Regs &R, Regs &I, int p) {
+  const float2 m1 = f2(-1.f, -1.f);
+  switch (p & 7) {
+    case 0: break;
+    case 4: scale_all(R, I, -1.f); break;
+    case 2:  // times i: (r, i) -> (-i, r)
+#pragma unroll
+      for (int q = 0; q < kP; ++q) { const float2 r = R[q]; R[q] = mul2(I[q], m1); I[q] = r; }
+      break;
+    case 6:  // times -i: (r, i) -> (i, -r)
+#pragma unroll
+      for (int q = 0; q < kP; ++q) { const float2 r = R[q]; R[q] = I[q]; I[q] = mul2(r, m1); }
+      break;
+    default: {  // odd p: (sr + i si)/sqrt2 with sr, si = +-1
+      const float sr = (p == 1 || p == 7) ? 1.f : -1.f;
+      const float si = (p == 1 || p == 3) ? 1.f : -1.f;
+#pragma unroll
+      for (int q = 0; q < kP; ++q) {
+        const float2 a = fma2(R[q], f2(sr, sr), mul2(I[q], f2(-si, -si)));
+        const float2 b = fma2(I[q], f2(sr, sr), mul2(R[q], f2(si, si)));
+        R[q] = rs2x2(a);
+        I[q] = rs2x2(b);
+      }
+    }
+  }
+}
+
+// One op by its flat code.  `cond`: the op's condition on the thread's fixed qubits.
+// Signs and projectors of conditional diagonal ops become factors (1 where the
+// condition fails); scalar phases and zeroing of the group are only recorded.  The
+// planner makes every other kind of op unconditional in a packed plan and emits no
+// general 2x2 op for the gate set.
+#define SV_P6(M, A) M(A, 0) M(A, 1) M(A, 2) M(A, 3) M(A, 4)
+#define SV_PAIR_CASE(G, J) case svp::P_PAIR + 6 * G##_I + J: pairs<G, J>(R, I); break;
+#define SV_DIAG_CASE(D, J) case svp::P_DIAG + 6 * D##_I + J: diag<D, J>(R, I); break;
+#define SV_Z_CASE(X, J) \
+  case svp::P_DIAG + 12 + J: factor<J, 1>(R, I, fz); break; \
+  case svp::P_DIAG + 18 + J: factor<J, 1>(R, I, f0); break; \
+  case svp::P_DIAG + 24 + J: factor<J, 0>(R, I, f0); break;
+#define SV_TWO_CASE(J, K) \
+  case svp::P_CZ + 6 * J + K: two<J, K, false>(R, I); break; \
+  case svp::P_PEQ + 6 * J + K: two<J, K, true>(R, I); break;
+
+constexpr int GH_I = 0, GSX_I = 1, GSY_I = 2, GSXDG_I = 3, GSYDG_I = 4, DT_I = 0, DTDG_I = 1;
+
+__device__ __forceinline__ void apply_op(Regs &R, Regs &I, const DevOp &op, bool cond, int &ph, bool &zero) {
+  using namespace svp;
+  const float fz = cond ? -1.f : 1.f, f0 = cond ? 0.f : 1.f;
+  switch (op.code) {
+    SV_P6(SV_PAIR_CASE, GH)
+    case P_PAIR + 0 + kPackSlot: pairs_pack<GH>(R, I); break;
+    SV_P6(SV_PAIR_CASE, GSX)
+    case P_PAIR + 6 + kPackSlot: pairs_pack<GSX>(R, I); break;
+    SV_P6(SV_PAIR_CASE, GSY)
+    case P_PAIR + 12 + kPackSlot: pairs_pack<GSY>(R, I); break;
+    SV_P6(SV_PAIR_CASE, GSXDG)
+    case P_PAIR + 18 + kPackSlot: pairs_pack<GSXDG>(R, I); break;
+    SV_P6(SV_PAIR_CASE, GSYDG)
+    case P_PAIR + 24 + kPackSlot: pairs_pack<GSYDG>(R, I); break;
+    SV_P6(SV_DIAG_CASE, DT)
+    case P_DIAG + 0 + kPackSlot: diag_pack<DT>(R, I); break;
+    SV_P6(SV_DIAG_CASE, DTDG)
+    case P_DIAG + 6 + kPackSlot: diag_pack<DTDG>(R, I); break;
+    SV_P6(SV_Z_CASE, 0)
+    case P_DIAG + 12 + kPackSlot: factor_pack<1>(R, I, fz); break;
+    case P_DIAG + 18 + kPackSlot: factor_pack<1>(R, I, f0); break;
+    case P_DIAG + 24 + kPackSlot: factor_pack<0>(R, I, f0); break;
+    SV_TWO_CASE(0, 1) SV_TWO_CASE(0, 2) SV_TWO_CASE(0, 3) SV_TWO_CASE(0, 4) SV_TWO_CASE(0, 5)
+    SV_TWO_CASE(1, 2) SV_TWO_CASE(1, 3) SV_TWO_CASE(1, 4) SV_TWO_CASE(1, 5)
+    SV_TWO_CASE(2, 3) SV_TWO_CASE(2, 4) SV_TWO_CASE(2, 5)
+    SV_TWO_CASE(3, 4) SV_TWO_CASE(3, 5)
+    SV_TWO_CASE(4, 5)
+    case P_PHASE: ph += cond ? op.arg : 0; break;
+    case P_ZERO: zero = zero || cond; break;
+    case P_SCALE: scale_all(R, I, __int_as_float((127 - op.arg) << 23)); break;  // 2^-arg, exact
+    default: break;
+  }
+}
+#undef SV_P6
+#undef SV_PAIR_CASE
+#undef SV_DIAG_CASE
+#undef SV_Z_CASE
+#undef SV_TWO_CASE
+
+// The stage's ops in order; the op after the current one is loaded while it runs.
+__device__ __forceinline__ void apply_ops(Regs &R, Regs &I, const DevOp *ops, const DevStage &st, uint64_t G0) {
+  int ph = 0;
+  bool zero = false;
+  const int count = st.op_count;
+  if (count > 0) {
+    const DevOp *op_ptr = ops + st.op_begin;
+    DevOp op = op_ptr[0];
+    for (int o = 0; o < count; ++o) {
+      const DevOp nxt = op_ptr[o + 1 < count ? o + 1 : o];
+      apply_op(R, I, op, (G0 & op.cmask) == op.cval, ph, zero);
+      op = nxt;
+    }
+  }
+  if (zero) {
+    scale_all(R, I, 0.f);
+  } else {
+    if (st.halves) scale_all(R, I, __int_as_float((127 - st.halves) << 23));  // 2^-halves, exact
+    if (ph & 7) phase_all(R, I, ph & 7);
+  }
+}
+
+// ---- addressing ---------------------------------------------------------------------------
+// 16-byte slot of pair k (tile bits 1..m-1): pair bit i toggles slot bit i mod 3, so the
+// 8 lanes of a quarter warp hit distinct 16-byte bank groups when the planner gives them
+// three pair bits of distinct residues.  Linear over XOR.
+__device__ __forceinline__ uint32_t pack_phys(uint32_t k) { return k ^ (((k >> 3) ^ (k >> 6) ^ (k >> 9)) & 7u); }
+
+// Byte offset of group g's first pair and global index of its element 0.
+__device__ __forceinline__ void group_base(const DevPlanView &plan, uint32_t si, int g, uint64_t base, uint32_t *a0,
+                                           uint64_t *G0) {
+  const svp::DevGroupEntry *t = plan.gtab + svp::kGroupEntries * si;
+  const svp::DevGroupEntry a = t[g & 15], b = t[16 + ((g >> 4) & 15)];
+  *a0 = a.L ^ b.L;
+  *G0 = base | a.G | b.G;
+}
+
+__device__ __forceinline__ void load_group(const float4 *tile, const DevPlanView &plan, uint32_t si, uint32_t a0,
+                                           Regs &R, Regs &I) {
+  const svp::DevGroupEntry *t = plan.gtab + svp::kGroupEntries * si + svp::kRegEntry;
+  uint32_t rx[kPR];
+#pragma unroll
+  for (int j = 0; j < kPR; ++j) rx[j] = t[j].L;
+  const char *tb = reinterpret_cast<const char *>(tile);
+#pragma unroll
+  for (int p = 0; p < kP; ++p) {
+    uint32_t a = a0;
+#pragma unroll
+    for (int j = 0; j < kPR; ++j)
+      if ((p >> j) & 1) a ^= rx[j];
+    const float4 x = *reinterpret_cast<const float4 *>(tb + a);
+    R[p] = f2(x.x, x.y);
+    I[p] = f2(x.z, x.w);
+  }
+}
+
+__device__ __forceinline__ void store_group(float4 *tile, const DevPlanView &plan, uint32_t si, uint32_t a0,
+                                            const Regs &R, const Regs &I) {
+  const svp::DevGroupEntry *t = plan.gtab + svp::kGroupEntries * si + svp::kRegEntry;
+  uint32_t rx[kPR];
+#pragma unroll
+  for (int j = 0; j < kPR; ++j) rx[j] = t[j].L;
+  char *tb = reinterpret_cast<char *>(tile);
+#pragma unroll
+  for (int p = 0; p < kP; ++p) {
+    uint32_t a = a0;
+#pragma unroll
+    for (int j = 0; j < kPR; ++j)
+      if ((p >> j) & 1) a ^= rx[j];
+    *reinterpret_cast<float4 *>(tb + a) = make_float4(R[p].x, R[p].y, I[p].x, I[p].y);
+  }
+}
+
+// Base index of tile `tile_id`: its bits spread over the non-tile qubits.
+__device__ __forceinline__ uint64_t tile_base(const DevPass &P, uint64_t tile_id) {
+  uint64_t base = 0;
+  for (int i = 0; i < P.nt; ++i) base |= ((tile_id >> i) & 1ull) << P.ntq[i];
+  return base;
+}
+
+// chunk_off[h]: bits of chunk index h spread over the tile qubits above the c low ones.
+__device__ __forceinline__ void build_chunk_table(const DevPass &P, uint64_t *chunk_off) {
+  const int nb = P.m - P.c;
+  for (int h = threadIdx.x; h < (1 << nb); h += blockDim.x) {
+    uint64_t off = 0;
+    for (int i = 0; i < nb; ++i)
+      if ((h >> i) & 1) off |= 1ull << P.tq[P.c + i];
+    chunk_off[h] = off;
+  }
+}
+
+// Read the tile into shared memory as swizzled pairs: thread t moves pairs t, t + T, ...
+// (T threads, 32 pairs each), 8 coalesced 16-byte loads in flight.  kL2Only reads
+// through L2 only (for data other CTAs of the same launch wrote).
+template <bool kL2Only = false>
+__device__ __forceinline__ void load_tile(const float2 *__restrict__ psi, float4 *tile, const DevPass &P,
+                                          const uint64_t *chunk_off, uint64_t base) {
+  const uint32_t tid = threadIdx.x, T = blockDim.x;
+  const int cp = P.c - 1;  // pair bits inside a chunk of 2^c amplitudes
+  const uint32_t in_mask = (1u << cp) - 1;
+  constexpr int kBatch = 8;
+#pragma unroll 1
+  for (int it0 = 0; it0 < kP; it0 += kBatch) {
+    float4 buf[kBatch];
+#pragma unroll
+    for (int b = 0; b < kBatch; ++b) {
+      const uint32_t k = tid + (uint32_t)(it0 + b) * T;
+      const float4 *src = reinterpret_cast<const float4 *>(psi + base + chunk_off[k >> cp] + 2 * (k & in_mask));
+      buf[b] = kL2Only ? __ldcg(src) : *src;
+    }
+#pragma unroll
+    for (int b = 0; b < kBatch; ++b) {
+      const uint32_t k = tid + (uint32_t)(it0 + b) * T;
+      tile[pack_phys(k)] = make_float4(buf[b].x, buf[b].z, buf[b].y, buf[b].w);
+    }
+  }
+}
+
+__device__ __forceinline__ void store_tile(float2 *__restrict__ psi, const float4 *tile, const DevPass &P,
+                                           const uint64_t *chunk_off, uint64_t base) {
+  const uint32_t tid = threadIdx.x, T = blockDim.x;
+  const int cp = P.c - 1;
+  const uint32_t in_mask = (1u << cp) - 1;
+#pragma unroll 4
+  for (int it = 0; it < kP; ++it) {
+    const uint32_t k = tid + (uint32_t)it * T;
+    const float4 x = tile[pack_phys(k)];
+    *reinterpret_cast<float4 *>(psi + base + chunk_off[k >> cp] + 2 * (k & in_mask)) =
+        make_float4(x.x, x.z, x.y, x.w);
+  }
+}
+
+// The generated first tile of a fresh state: 2^{-n/2} everywhere, or |0..0>.
+__device__ __forceinline__ void init_regs(Regs &R, Regs &I, const DevPass &P, uint64_t G0) {
+  const float a = (P.flags & svp::PF_INIT_UNIFORM) ? P.init_amp : 0.f;
+#pragma unroll
+  for (int p = 0; p < kP; ++p) { R[p] = f2(a, a); I[p] = f2(0.f, 0.f); }
+  if (!(P.flags & svp::PF_INIT_UNIFORM) && G0 == 0) R[0].x = 1.f;
+}
+
+__device__ __forceinline__ void init_tile(float4 *tile, const DevPass &P, uint64_t base) {
+  const float a = (P.flags & svp::PF_INIT_UNIFORM) ? P.init_amp : 0.f;
+  for (uint32_t k = threadIdx.x; k < (1u << (P.m - 1)); k += blockDim.x)
+    tile[k] = make_float4(a, a, 0.f, 0.f);
+  if (!(P.flags & svp::PF_INIT_UNIFORM) && base == 0 && threadIdx.x == 0) tile[0] = make_float4(1.f, 0.f, 0.f, 0.f);
+}
+
+// One tile of one packed pass: load (or generate), every stage in registers, store.
+// The caller has built chunk_off for P and synchronised; ends with __syncthreads.
+template <bool kL2Only = false>
+__device__ __forceinline__ void process_tile(float2 *__restrict__ psi, const DevPlanView &plan, const DevPass &P,
+                                             const uint64_t *chunk_off, float4 *tile, uint64_t tile_id) {
+  const int tid = threadIdx.x;
+  const uint64_t base = tile_base(P, tile_id);
+  const bool init = (P.flags & (svp::PF_INIT_UNIFORM | svp::PF_INIT_ZERO)) != 0;
+  if (!init) {
+    load_tile<kL2Only>(psi, tile, P, chunk_off, base);
+    __syncthreads();
+  } else if (P.stage_count == 0) {
+    init_tile(tile, P, base);
+    __syncthreads();
+  }
+  for (int s = 0; s < P.stage_count; ++s) {
+    const uint32_t si = P.stage_begin + s;
+    const DevStage &st = plan.stages[si];
+    uint32_t a0;
+    uint64_t G0;
+    group_base(plan, si, tid, base, &a0, &G0);
+    Regs R, I;
+    if (s == 0 && init) init_regs(R, I, P, G0);
+    else load_group(tile, plan, si, a0, R, I);
+    apply_ops(R, I, plan.ops, st, G0);
+    // Recompute the address rather than keeping it live across the ops.
+    asm volatile("" ::: "memory");
+    group_base(plan, si, tid, base, &a0, &G0);
+    store_group(tile, plan, si, a0, R, I);
+    __syncthreads();
+  }
+  store_tile(psi, tile, P, chunk_off, base);
+  __syncthreads();
+}
+
+}  // namespace tpk
+}  // namespace svk
