@@ -432,11 +432,23 @@ bool build_plan(int n, const std::vector<Gate> &gates, const Options &opt, bool 
         // non-diagonal gates, T and two-qubit ops of a packed plan are unconditional
         std::vector<DevOp> ops(P.ops.begin() + ds.op_begin, P.ops.end());
         P.ops.resize(ds.op_begin);
+        // condition word: group index bit i <-> tile bit nonr[i], then one bit per
+        // non-tile qubit (the tile index)
+        int wpos[64];
+        for (int q = 0; q < 64; ++q) wpos[q] = -1;
+        for (int i = 0; i < group_bits; ++i) wpos[dp.tq[ds.nonr[i]]] = i;
+        for (int i = 0; i < dp.nt; ++i) wpos[dp.ntq[i]] = group_bits + i;
         int pending = 0;
-        for (const DevOp &o : ops) {
+        for (DevOp o : ops) {
           const bool cond_ok = o.cmask == 0 || o.act == A_Z || o.act == A_P0 || o.act == A_P1 ||
                                o.act == A_PHASE || o.act == A_ZERO;
           if (!cond_ok) { *err = "packed plan: conditional op of an unconditional kind"; return false; }
+          for (int q = 0; q < n; ++q) {
+            if (!((o.cmask >> q) & 1ull)) continue;
+            if (wpos[q] < 0 || wpos[q] > 31) { *err = "packed plan: condition outside the condition word"; return false; }
+            o.wmask |= 1u << wpos[q];
+            if ((o.cval >> q) & 1ull) o.wval |= 1u << wpos[q];
+          }
           P.ops.push_back(o);
           if (o.act == A_SX || o.act == A_SY || o.act == A_SXDG || o.act == A_SYDG) {
             if (++pending == kMaxDeferred) {
@@ -477,6 +489,12 @@ bool build_plan(int n, const std::vector<Gate> &gates, const Options &opt, bool 
   }
   for (const DevStage &ds : P.stages)
     if (ds.op_count > 65535) { *err = "plan too large"; return false; }
+  // a no-op past the last op: kernels may load the op after a stage's last one
+  DevOp end;
+  std::memset(&end, 0, sizeof(end));
+  end.code = 255;
+  end.act = A_COUNT;
+  P.ops.push_back(end);
   return true;
 }
 

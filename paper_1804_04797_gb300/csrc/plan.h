@@ -49,11 +49,16 @@ enum Act : uint8_t {
 
 // One device op.  It acts only where (G0 & cmask) == cval, G0 being the global index
 // of the group's element 0 (all register bits zero): conditions on qubits that are not
-// register bits of the stage (the other tile qubits and the tile's fixed qubits).
+// register bits of the stage (the other tile qubits and the tile's fixed qubits).  In a
+// packed plan the same condition reads (W & wmask) == wval on the thread's condition
+// word W = tile_id << group_bits | group index (one bit per fixed qubit of the thread),
+// and the first 16 bytes hold all the packed kernel reads.
 struct DevOp {
-  uint8_t act, j, k, arg;
-  uint8_t code;  // flat dispatch code of the plain kernels (see op_code)
+  uint8_t code;  // flat dispatch code of the kernel the plan is built for (Code / PCode)
+  uint8_t arg;
+  uint8_t act, j, k;
   uint8_t pad[3];
+  uint32_t wmask, wval;
   uint64_t cmask, cval;
 };
 
@@ -103,7 +108,7 @@ struct DevGroupEntry {
 };
 constexpr int kGroupEntries = 56;
 constexpr int kRegEntry = 48;
-static_assert(sizeof(DevOp) == 24, "DevOp layout");
+static_assert(sizeof(DevOp) == 32, "DevOp layout");
 
 constexpr int kMaxTileBits = 13;
 constexpr int kMaxReg = 5;

@@ -40,13 +40,8 @@ __device__ __forceinline__ float2 f2(float a, float b) { return make_float2(a, b
 __device__ __forceinline__ float2 add2(float2 a, float2 b) { return __fadd2_rn(a, b); }
 __device__ __forceinline__ float2 mul2(float2 a, float2 b) { return __fmul2_rn(a, b); }
 __device__ __forceinline__ float2 fma2(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
-__device__ __forceinline__ float2 sub2(float2 a, float2 b) {
-  unsigned long long r;
-  asm("sub.rn.f32x2 %0, %1, %2;"
-      : "=l"(r)
-      : "l"(*reinterpret_cast<unsigned long long *>(&a)), "l"(*reinterpret_cast<unsigned long long *>(&b)));
-  return *reinterpret_cast<float2 *>(&r);
-}
+// a - b as b * (-1) + a: exact product, one rounding, the same result as a subtraction
+__device__ __forceinline__ float2 sub2(float2 a, float2 b) { return fma2(b, f2(-1.f, -1.f), a); }
 __device__ __forceinline__ float2 rs2x2(float2 v) { return fma2(v, f2(kS2, kS2), mul2(v, f2(kS2lo, kS2lo))); }
 __device__ __forceinline__ float rs2(float v) { return fmaf(v, kS2, v * kS2lo); }
 
@@ -256,10 +251,12 @@ __device__ __forceinline__ void phase_all(Regs &R, Regs &I, int p) {
 
 constexpr int GH_I = 0, GSX_I = 1, GSY_I = 2, GSXDG_I = 3, GSYDG_I = 4, DT_I = 0, DTDG_I = 1;
 
-__device__ __forceinline__ void apply_op(Regs &R, Regs &I, const DevOp &op, bool cond, int &ph, bool &zero) {
+// The op's code and argument (the first word of its 16-byte head).
+__device__ __forceinline__ void apply_op(Regs &R, Regs &I, uint32_t code, uint32_t arg, bool cond, int &ph,
+                                         bool &zero) {
   using namespace svp;
   const float fz = cond ? -1.f : 1.f, f0 = cond ? 0.f : 1.f;
-  switch (op.code) {
+  switch (code) {
     SV_P6(SV_PAIR_CASE, GH)
     case P_PAIR + 0 + kPackSlot: pairs_pack<GH>(R, I); break;
     SV_P6(SV_PAIR_CASE, GSX)
@@ -283,9 +280,9 @@ __device__ __forceinline__ void apply_op(Regs &R, Regs &I, const DevOp &op, bool
     SV_TWO_CASE(2, 3) SV_TWO_CASE(2, 4) SV_TWO_CASE(2, 5)
     SV_TWO_CASE(3, 4) SV_TWO_CASE(3, 5)
     SV_TWO_CASE(4, 5)
-    case P_PHASE: ph += cond ? op.arg : 0; break;
+    case P_PHASE: ph += cond ? (int)arg : 0; break;
     case P_ZERO: zero = zero || cond; break;
-    case P_SCALE: scale_all(R, I, __int_as_float((127 - op.arg) << 23)); break;  // 2^-arg, exact
+    case P_SCALE: scale_all(R, I, __int_as_float((127 - (int)arg) << 23)); break;  // 2^-arg, exact
     default: break;
   }
 }
@@ -295,19 +292,19 @@ __device__ __forceinline__ void apply_op(Regs &R, Regs &I, const DevOp &op, bool
 #undef SV_Z_CASE
 #undef SV_TWO_CASE
 
-// The stage's ops in order; the op after the current one is loaded while it runs.
-__device__ __forceinline__ void apply_ops(Regs &R, Regs &I, const DevOp *ops, const DevStage &st, uint64_t G0) {
+// The stage's ops in order; the op after the current one is loaded while it runs (the
+// plan ends with a no-op, so the load after a stage's last op stays inside it).  W: the
+// thread's condition word.
+__device__ __forceinline__ void apply_ops(Regs &R, Regs &I, const DevOp *ops, const DevStage &st, uint32_t W) {
   int ph = 0;
   bool zero = false;
-  const int count = st.op_count;
-  if (count > 0) {
-    const DevOp *op_ptr = ops + st.op_begin;
-    DevOp op = op_ptr[0];
-    for (int o = 0; o < count; ++o) {
-      const DevOp nxt = op_ptr[o + 1 < count ? o + 1 : o];
-      apply_op(R, I, op, (G0 & op.cmask) == op.cval, ph, zero);
-      op = nxt;
-    }
+  const uint4 *head = reinterpret_cast<const uint4 *>(ops + st.op_begin);
+  const int stride = sizeof(DevOp) / sizeof(uint4);
+  uint4 h = head[0];
+  for (int o = 0; o < st.op_count; ++o) {
+    const uint4 nxt = head[(o + 1) * stride];
+    apply_op(R, I, h.x & 0xffu, (h.x >> 8) & 0xffu, (W & h.z) == h.w, ph, zero);
+    h = nxt;
   }
   if (zero) {
     scale_all(R, I, 0.f);
@@ -323,13 +320,10 @@ __device__ __forceinline__ void apply_ops(Regs &R, Regs &I, const DevOp *ops, co
 // three pair bits of distinct residues.  Linear over XOR.
 __device__ __forceinline__ uint32_t pack_phys(uint32_t k) { return k ^ (((k >> 3) ^ (k >> 6) ^ (k >> 9)) & 7u); }
 
-// Byte offset of group g's first pair and global index of its element 0.
-__device__ __forceinline__ void group_base(const DevPlanView &plan, uint32_t si, int g, uint64_t base, uint32_t *a0,
-                                           uint64_t *G0) {
+// Byte offset of group g's first pair.
+__device__ __forceinline__ uint32_t group_base(const DevPlanView &plan, uint32_t si, int g) {
   const svp::DevGroupEntry *t = plan.gtab + svp::kGroupEntries * si;
-  const svp::DevGroupEntry a = t[g & 15], b = t[16 + ((g >> 4) & 15)];
-  *a0 = a.L ^ b.L;
-  *G0 = base | a.G | b.G;
+  return t[g & 15].L ^ t[16 + ((g >> 4) & 15)].L;
 }
 
 __device__ __forceinline__ void load_group(const float4 *tile, const DevPlanView &plan, uint32_t si, uint32_t a0,
@@ -427,12 +421,13 @@ __device__ __forceinline__ void store_tile(float2 *__restrict__ psi, const float
   }
 }
 
-// The generated first tile of a fresh state: 2^{-n/2} everywhere, or |0..0>.
-__device__ __forceinline__ void init_regs(Regs &R, Regs &I, const DevPass &P, uint64_t G0) {
+// The generated first tile of a fresh state: 2^{-n/2} everywhere, or |0..0> (element 0
+// of group 0 of tile 0, the thread with condition word 0).
+__device__ __forceinline__ void init_regs(Regs &R, Regs &I, const DevPass &P, uint32_t W) {
   const float a = (P.flags & svp::PF_INIT_UNIFORM) ? P.init_amp : 0.f;
 #pragma unroll
   for (int p = 0; p < kP; ++p) { R[p] = f2(a, a); I[p] = f2(0.f, 0.f); }
-  if (!(P.flags & svp::PF_INIT_UNIFORM) && G0 == 0) R[0].x = 1.f;
+  if (!(P.flags & svp::PF_INIT_UNIFORM) && W == 0) R[0].x = 1.f;
 }
 
 __device__ __forceinline__ void init_tile(float4 *tile, const DevPass &P, uint64_t base) {
@@ -457,20 +452,18 @@ __device__ __forceinline__ void process_tile(float2 *__restrict__ psi, const Dev
     init_tile(tile, P, base);
     __syncthreads();
   }
+  // condition word: the group index below the tile index (n - 1 - kPR <= 32 bits)
+  const uint32_t W = ((uint32_t)tile_id << (P.m - 1 - kPR)) | (uint32_t)tid;
   for (int s = 0; s < P.stage_count; ++s) {
     const uint32_t si = P.stage_begin + s;
     const DevStage &st = plan.stages[si];
-    uint32_t a0;
-    uint64_t G0;
-    group_base(plan, si, tid, base, &a0, &G0);
     Regs R, I;
-    if (s == 0 && init) init_regs(R, I, P, G0);
-    else load_group(tile, plan, si, a0, R, I);
-    apply_ops(R, I, plan.ops, st, G0);
+    if (s == 0 && init) init_regs(R, I, P, W);
+    else load_group(tile, plan, si, group_base(plan, si, tid), R, I);
+    apply_ops(R, I, plan.ops, st, W);
     // Recompute the address rather than keeping it live across the ops.
     asm volatile("" ::: "memory");
-    group_base(plan, si, tid, base, &a0, &G0);
-    store_group(tile, plan, si, a0, R, I);
+    store_group(tile, plan, si, group_base(plan, si, tid), R, I);
     __syncthreads();
   }
   store_tile(psi, tile, P, chunk_off, base);
