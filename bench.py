@@ -291,7 +291,7 @@ def main():
     results = {}
     bits = np.array(inputs.bitstrings(n, 64, seed=2), dtype=np.uint64)
     known = {'plain': sv.SV_PREC_PLAIN, 'tf32x3': sv.SV_PREC_TF32X3, 'f16x3': sv.SV_PREC_F16X3,
-             'pergate': sv.SV_PREC_PERGATE}
+             'pergate': sv.SV_PREC_PERGATE, 'plain_interp': sv.SV_PREC_PLAIN}
     modes = [(p, known[p]) for p in args.paths.split(',') if p in known]
     if args.no_fused:
         modes = [m for m in modes if m[0] != 'tf32x3']
@@ -300,7 +300,8 @@ def main():
     try:
         for name, prec in modes:
             try:
-                sv.sv_set_options(h, sv.options(precision=prec, stream=stream.cuda_stream, tile_bits=args.tile_bits))
+                sv.sv_set_options(h, sv.options(precision=prec, stream=stream.cuda_stream, tile_bits=args.tile_bits,
+                                                jit=-1 if name == 'plain_interp' else 0))
                 ms, wall, prof, clocks = timed(h, args.steps, args.warmup, step_device)
             except sv.SvError as e:
                 results[name] = {'unavailable': str(e)}
@@ -318,6 +319,7 @@ def main():
                 'bytes_per_launch': bytes_per_launch, 'achieved_gbs': bytes_per_launch / (per_launch_ms * 1e-3) / 1e9,
                 'norm_err': abs(norm2 - 1.0), 'n_sum_p2': (2.0 ** n) * sp2, 'rel_l2_vs_plain_64amps': agree,
                 'clocks': clocks, 'launches_per_step': prof.launches / args.steps,
+                'plan_kernel_launches': prof.jit_launches,
             }
 
         # end to end through the public API with host buffers: gate list in, amplitudes
@@ -360,7 +362,10 @@ def main():
                                                                                           lat.depth),
                    'state_bytes': 8 * 2 ** n, 'l2': 'state 137 GB >> L2 129 MB, no flush needed',
                    'path': best_name, 'replicas': world},
-        'roofline': {'bound': 'hbm', 'kernel': {'plain': 'tile_pass_kernel', 'tf32x3': 'fused_pass_kernel<tf32>',
+        'roofline': {'bound': 'hbm', 'kernel': {'plain': 'sv_pass (plan-specialised tile pass)'
+                                                if best.get('plan_kernel_launches') else 'tile_pass_kernel',
+                                                'plain_interp': 'tile_pass_kernel',
+                                                'tf32x3': 'fused_pass_kernel<tf32>',
                                                 'f16x3': 'fused_pass_kernel<f16>',
                                                 'pergate': 'gate1q_kernel/diag_kernel'}[best_name],
                      'achieved': achieved, 'peak': hbm_peak, 'unit': 'GB/s', 'frac': achieved / hbm_peak,

@@ -72,6 +72,9 @@ typedef struct {
   void *stream;   /* cudaStream_t used by the handle                      [legacy 0]    */
   int tile_bits;  /* qubits per gathered tile, fuse_k+5..13               [13]          */
   int low_bits;   /* contiguous low qubits in every tile (coalescing)     [4]           */
+  int jit;        /* plain path: run each plan on kernels compiled for it at run time */
+                  /* (NVRTC; cached in memory and in the library's directory):       */
+                  /* 1 = always (error if NVRTC fails), -1 = never, 0 = for n >= 24 [0] */
 } sv_options;
 
 /* An R x C lattice circuit: bit r*cols+c of removed_mask drops site (r,c); kept sites
@@ -244,7 +247,15 @@ typedef struct {
   double h2d_bytes;   /* host-to-device bytes copied by the library (plans, indices) */
   double d2h_bytes;   /* device-to-host bytes copied by the library (results)     */
   int other_launches; /* other kernels (reductions, gathers, init)               */
+  int jit_launches;   /* tile passes run on plan-specialised (run-time compiled) kernels */
 } sv_profile;
+
+/* Compile the plan-specialised kernels of a gate list for sm_103a without a device
+ * (NVRTC only; no cache is read or written): a check of the code generator.  log (may
+ * be NULL) receives up to log_cap bytes of the compiler's messages, NUL-terminated.
+ * SV_ERR_CUDA when NVRTC is missing or the compile fails. */
+sv_status sv_jit_check(int n_qubits, const sv_gate *gates, size_t n_gates, const sv_options *opts,
+                       int fresh_state, char *log, size_t log_cap);
 
 sv_status sv_set_profiling(sv_state *s, int on);
 sv_status sv_get_profile(sv_state *s, sv_profile *out);

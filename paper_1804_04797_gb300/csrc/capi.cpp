@@ -9,6 +9,7 @@
 
 #include "../../include/sv.h"
 #include "capi_util.h"
+#include "jit.h"
 #include "kernels.h"
 #include "plan.h"
 #include "state.h"
@@ -63,6 +64,7 @@ sv_status check_options(const sv_options &o) {
   if (o.tile_bits != 0 && (o.tile_bits < 6 || o.tile_bits > svp::kMaxTileBits))
     return fail(SV_ERR_ARG, "options: tile_bits must be 0 or 6..13");
   if (o.low_bits < 0 || o.low_bits > 13) return fail(SV_ERR_ARG, "options: low_bits must be 0..13");
+  if (o.jit < -1 || o.jit > 1) return fail(SV_ERR_ARG, "options: jit must be -1, 0 or 1");
   const int m = o.tile_bits > 0 ? o.tile_bits : 13;
   const int c = o.low_bits > 0 ? o.low_bits : 4;
   if (c > m || m - c > 10) return fail(SV_ERR_ARG, "options: need low_bits <= tile_bits <= low_bits + 10");
@@ -222,15 +224,18 @@ sv_status upload_plan(sv_state *s, const svp::Plan &P, svk::DevPlanView *view) {
   return SV_OK;
 }
 
-sv_status run_plan(sv_state *s, const svp::Plan &P, const svk::DevPlanView &view, bool fused, bool f16) {
+sv_status run_plan(sv_state *s, const svp::Plan &P, const svk::DevPlanView &view, bool fused, bool f16,
+                   const svj::Module *jit) {
   const double amps = std::ldexp(1.0, s->n);
   for (size_t p = 0; p < P.passes.size(); ++p) {
     const svp::DevPass &hp = P.passes[p];
     const double bytes = (hp.flags & (svp::PF_INIT_UNIFORM | svp::PF_INIT_ZERO)) ? 8.0 * amps : 16.0 * amps;
     prof_begin(s);
     cudaError_t e = fused ? svk::launch_fused_pass(s->psi, s->n, view, (int)p, hp, s->stream, f16)
+                    : jit ? svj::launch_pass(jit, s->psi, s->n, view, (int)p, hp, s->stream)
                           : svk::launch_tile_pass(s->psi, s->n, view, (int)p, hp, s->stream);
     prof_end(s, bytes);
+    if (jit && s->prof) s->jit_launches += 1;
     if (e != cudaSuccess) { s->broken = true; return cuda_fail(e, "tile pass kernel"); }
   }
   return SV_OK;
@@ -265,9 +270,16 @@ sv_status apply_gates(sv_state *s, const std::vector<svp::Gate> &g) {
   if (po.fused)
     for (const svp::DevPass &dp : P.passes)
       if (dp.stage_count > 256) return fail(SV_ERR_ARG, "fused path: more than 256 stages in one pass");
+  // plain path: kernels compiled for this plan where they pay (or where asked for)
+  const svj::Module *jit = nullptr;
+  if (!po.fused && s->opts.jit >= 0 && (s->opts.jit == 1 || s->n >= kJitMinQubits)) {
+    std::string jerr;
+    jit = svj::get_module(P, po.rk, &jerr);
+    if (!jit && s->opts.jit == 1) return fail(SV_ERR_CUDA, jerr.c_str());
+  }
   svk::DevPlanView view;
   if ((st = upload_plan(s, P, &view)) != SV_OK) return st;
-  if ((st = run_plan(s, P, view, po.fused, f16)) != SV_OK) return st;
+  if ((st = run_plan(s, P, view, po.fused, f16, jit)) != SV_OK) return st;
   s->fresh = false;
   if (po.fused) {
     // a fused pass whose bounded wait gave up leaves a non-zero error word
@@ -508,7 +520,7 @@ sv_status sv_plan(int n_qubits, const sv_gate *gates, size_t n_gates, const sv_o
   if (summary) {
     summary->passes = (int)P.passes.size();
     summary->stages = (int)P.stages.size();
-    summary->ops = (int)P.ops.size();
+    summary->ops = (int)P.ops.size() - 1;  // without the closing no-op
     summary->init_uniform = P.init_uniform ? 1 : 0;
     summary->hbm_bytes = P.hbm_bytes;
   }
@@ -524,6 +536,39 @@ sv_status sv_plan(int n_qubits, const sv_gate *gates, size_t n_gates, const sv_o
   return SV_OK;
 }
 
+sv_status sv_jit_check(int n_qubits, const sv_gate *gates, size_t n_gates, const sv_options *opts, int fresh_state,
+                       char *log, size_t log_cap) {
+  clear_error();
+  if (log && log_cap) log[0] = 0;
+  if (n_qubits < 6 || n_qubits > 34) return fail(SV_ERR_ARG, "sv_jit_check: n_qubits must be 6..34");
+  sv_options o;
+  std::memset(&o, 0, sizeof(o));
+  if (opts) o = *opts;
+  sv_status st = check_options(o);
+  if (st != SV_OK) return st;
+  std::vector<svp::Gate> g;
+  if ((st = convert_gates(n_qubits, gates, n_gates, false, &g)) != SV_OK) return st;
+  svp::Options po = plan_options(o);
+  po.fused = false;
+  po.pack = true;
+  po.rk = svk::tile_pass_register_slots();
+  po.r = std::min(po.r, po.rk);
+  svp::Plan P;
+  const char *err = nullptr;
+  if (!svp::build_plan(n_qubits, g, po, fresh_state != 0, &P, &err))
+    return fail(SV_ERR_ARG, err ? err : "planning failed");
+  std::vector<std::string> cubins;
+  std::string lg;
+  const bool ok = svj::compile_plan(P, po.rk, "sm_103a", &cubins, &lg, "");
+  if (log && log_cap) {
+    const size_t k = std::min(lg.size(), log_cap - 1);
+    std::memcpy(log, lg.data(), k);
+    log[k] = 0;
+  }
+  if (!ok) return fail(SV_ERR_CUDA, "sv_jit_check: NVRTC compile failed");
+  return SV_OK;
+}
+
 sv_status sv_set_profiling(sv_state *s, int on) {
   clear_error();
   if (!s) return fail(SV_ERR_ARG, "NULL state");
@@ -532,6 +577,7 @@ sv_status sv_set_profiling(sv_state *s, int on) {
   s->ev_bytes.clear();
   s->h2d = s->d2h = 0;
   s->other_launches = 0;
+  s->jit_launches = 0;
   return SV_OK;
 }
 
@@ -546,6 +592,7 @@ sv_status sv_get_profile(sv_state *s, sv_profile *out) {
   out->h2d_bytes = s->h2d;
   out->d2h_bytes = s->d2h;
   out->other_launches = s->other_launches;
+  out->jit_launches = s->jit_launches;
   for (size_t i = 0; i + 1 < s->ev_used; i += 2) {
     float ms = 0;
     if (cudaEventElapsedTime(&ms, s->events[i], s->events[i + 1]) == cudaSuccess) out->ms += ms;

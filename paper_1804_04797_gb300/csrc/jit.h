@@ -1,0 +1,45 @@
+// Plan-specialised tile-pass kernels compiled at run time (NVRTC).
+//
+// The packed tile kernel interprets a plan: one indirect branch per op picks the op's
+// code.  For a plan that runs more than once (or on a large state) the library instead
+// writes one kernel per pass in which every stage's ops are straight-line calls of the
+// same device functions (tile_pack.cuh) with the register slots, conditions and scale
+// factors as constants, compiles it for the device with NVRTC and keeps the module.
+// The arithmetic is the interpreter's, op for op: the results are bitwise identical.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <string>
+#include <vector>
+
+#include "plan.h"
+#include "plan_dev.h"
+
+namespace svj {
+
+// CUDA source of the kernel ("sv_pass") of one pass of a packed plan.  kpr: register
+// slots besides the pack bit (the plan's rk).
+std::string pass_source(const svp::Plan &P, int kpr, int pass);
+
+// Compile CUDA source for an architecture ("sm_103a") to a cubin with NVRTC; the
+// device headers are compiled into the library.  Returns false with *log set.
+bool compile(const std::string &src, const char *arch, std::string *cubin, std::string *log);
+
+// Compile the kernels of every pass of a plan (one NVRTC program per pass, in parallel
+// threads).  cache: a directory of cubins by source hash ("" = none).
+bool compile_plan(const svp::Plan &P, int kpr, const char *arch, std::vector<std::string> *cubins,
+                  std::string *log, const std::string &cache);
+
+struct Module;
+
+// The compiled kernels of plan P on the current device, from the in-process cache, the
+// on-disk cache (the library's build directory, subdirectory jit) or a fresh compile.
+// nullptr with *err set if NVRTC or the module load fails.
+const Module *get_module(const svp::Plan &P, int kpr, std::string *err);
+
+// Launch pass `pass` of a module on the plan's device copy.
+cudaError_t launch_pass(const Module *M, float2 *psi, int n, const svk::DevPlanView &view, int pass,
+                        const svp::DevPass &hp, cudaStream_t st);
+
+}  // namespace svj

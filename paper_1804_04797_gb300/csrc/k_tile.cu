@@ -22,12 +22,11 @@ namespace {
 
 using namespace tpk;
 
-constexpr int kThreads = 1 << (svp::kMaxTileBits - 1 - kPR);  // one group of 32 pairs per thread
+constexpr int kThreads = 1 << (svp::kMaxTileBits - 1 - kPR);  // one group of 2^kPR pairs per thread
 
 __global__ void __launch_bounds__(kThreads, 2)
 tile_pass_kernel(float2 *__restrict__ psi, DevPlanView plan, int pass_index, uint64_t num_tiles) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  float4 *tile = reinterpret_cast<float4 *>(smem_raw);
   __shared__ DevPass P;
   __shared__ uint64_t chunk_off[1 << 10];
 
@@ -36,9 +35,7 @@ tile_pass_kernel(float2 *__restrict__ psi, DevPlanView plan, int pass_index, uin
   __syncthreads();
   build_chunk_table(P, chunk_off);
   __syncthreads();
-
-  for (uint64_t tile_id = blockIdx.x; tile_id < num_tiles; tile_id += gridDim.x)
-    process_tile(psi, plan, P, chunk_off, tile, tile_id);
+  sweep_tiles(psi, plan, P, chunk_off, reinterpret_cast<float4 *>(smem_raw), blockIdx.x, gridDim.x, num_tiles);
 }
 
 int g_tile_blocks_per_sm[svp::kMaxTileBits + 1] = {};  // resident CTAs per SM, by tile size
@@ -62,10 +59,10 @@ cudaError_t launch_tile_pass(float2 *psi, int n, const DevPlanView &plan, int pa
   }
   const int threads = 1 << (m - 1 - kPR);
   if (g_tile_blocks_per_sm[m] == 0) {
-    int per_sm = 0;
-    cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, tile_pass_kernel, threads, smem);
+    int q = 0;
+    cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&q, tile_pass_kernel, threads, smem);
     if (e != cudaSuccess) return e;
-    g_tile_blocks_per_sm[m] = per_sm < 1 ? 1 : per_sm;
+    g_tile_blocks_per_sm[m] = q < 1 ? 1 : q;
   }
   const uint64_t tiles = 1ull << (n - m);
   uint64_t grid = (uint64_t)device_sm_count() * (uint64_t)g_tile_blocks_per_sm[m];

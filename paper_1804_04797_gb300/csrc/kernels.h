@@ -13,15 +13,6 @@ struct Mat2 {
   float v[8];  // a, b, c, d as (re, im)
 };
 
-// Plan as laid out in device memory (one allocation, arrays back to back).
-struct DevPlanView {
-  const svp::DevPass *passes;
-  const svp::DevStage *stages;
-  const svp::DevOp *ops;
-  const float *mats;
-  int *err;  // error word of the plan (0 = ok; set by a kernel whose bounded wait gave up)
-  const svp::DevGroupEntry *gtab;  // 32 group-addressing entries per stage
-};
 
 // K0: write |0..0> (uniform == false) or the uniform 2^{-n/2} state.  Write-only.
 cudaError_t launch_init(float2 *psi, int n, bool uniform, float amp, cudaStream_t st);

@@ -31,9 +31,19 @@ struct sv_state {
   std::vector<double> ev_bytes;
   double h2d = 0, d2h = 0;
   int other_launches = 0;
+  int jit_launches = 0;
 };
 
+namespace svj {
+struct Module;
+}
+
 namespace svc {
+
+// States of at least this many qubits run the plain path on plan-specialised kernels
+// (sv_options.jit == 0): there a compile (about a second, once per circuit) is small
+// against one run.
+constexpr int kJitMinQubits = 24;
 
 sv_status cuda_fail(cudaError_t e, const char *what);
 sv_status ensure_device_buffer(void **buf, size_t *cap, size_t need);
@@ -41,7 +51,8 @@ svp::Options plan_options(const sv_options &o);
 sv_status check_options(const sv_options &o);
 sv_status convert_gates(int n, const sv_gate *g, size_t count, bool inverse, std::vector<svp::Gate> *out);
 sv_status upload_plan(sv_state *s, const svp::Plan &P, svk::DevPlanView *view);
-sv_status run_plan(sv_state *s, const svp::Plan &P, const svk::DevPlanView &view, bool fused, bool f16 = false);
+sv_status run_plan(sv_state *s, const svp::Plan &P, const svk::DevPlanView &view, bool fused, bool f16 = false,
+                   const svj::Module *jit = nullptr);
 // Plan and run an internal gate list (kinds may include K_PEQ) on the state.
 sv_status apply_gates(sv_state *s, const std::vector<svp::Gate> &g);
 // Fused path: the stage unitaries as split-TF32 operands (see k_fused.cu).

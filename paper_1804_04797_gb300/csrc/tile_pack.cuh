@@ -14,9 +14,11 @@
 // multiplication by a per-thread factor, so no op diverges within a warp.
 #pragma once
 
+#ifndef __CUDACC_RTC__
 #include <cuda_runtime.h>
+#endif
 
-#include "kernels.h"
+#include "plan_dev.h"
 
 namespace svk {
 namespace tpk {
@@ -131,10 +133,11 @@ using Regs = float2[kP];
 // gate G on register slot J (pairs p and p | 2^J)
 template <class G, int J>
 __device__ __forceinline__ void pairs(Regs &R, Regs &I) {
-  if constexpr (J >= kPR) return;
+  if constexpr (J < kPR) {
 #pragma unroll
-  for (int p = 0; p < kP; ++p)
-    if (!(p & (1 << J))) G::f(R[p], I[p], R[p | (1 << J)], I[p | (1 << J)]);
+    for (int p = 0; p < kP; ++p)
+      if (!(p & (1 << J))) G::f(R[p], I[p], R[p | (1 << J)], I[p | (1 << J)]);
+  }
 }
 // gate G on the pack bit: inside every pair
 template <class G>
@@ -145,10 +148,11 @@ __device__ __forceinline__ void pairs_pack(Regs &R, Regs &I) {
 // phase D where register slot J is 1
 template <class D, int J>
 __device__ __forceinline__ void diag(Regs &R, Regs &I) {
-  if constexpr (J >= kPR) return;
+  if constexpr (J < kPR) {
 #pragma unroll
-  for (int p = 0; p < kP; ++p)
-    if (p & (1 << J)) D::f(R[p], I[p]);
+    for (int p = 0; p < kP; ++p)
+      if (p & (1 << J)) D::f(R[p], I[p]);
+  }
 }
 // phase D where the pack bit is 1
 template <class D>
@@ -159,11 +163,12 @@ __device__ __forceinline__ void diag_pack(Regs &R, Regs &I) {
 // factor f (a sign or a 0/1 projector) where register slot J equals B
 template <int J, int B>
 __device__ __forceinline__ void factor(Regs &R, Regs &I, float f) {
-  if constexpr (J >= kPR) return;
-  const float2 ff = f2(f, f);
+  if constexpr (J < kPR) {
+    const float2 ff = f2(f, f);
 #pragma unroll
-  for (int p = 0; p < kP; ++p)
-    if (((p >> J) & 1) == B) { R[p] = mul2(R[p], ff); I[p] = mul2(I[p], ff); }
+    for (int p = 0; p < kP; ++p)
+      if (((p >> J) & 1) == B) { R[p] = mul2(R[p], ff); I[p] = mul2(I[p], ff); }
+  }
 }
 // factor f where the pack bit equals B
 template <int B>
@@ -176,29 +181,31 @@ __device__ __forceinline__ void factor_pack(Regs &R, Regs &I, float f) {
 // 0 where they differ); J < K, K may be the pack slot
 template <int J, int K, bool EQ>
 __device__ __forceinline__ void two(Regs &R, Regs &I) {
-  if constexpr (J >= kPR || (K >= kPR && K != svp::kPackSlot)) return;
+  if constexpr (J < kPR && (K < kPR || K == svp::kPackSlot)) {
 #pragma unroll
-  for (int p = 0; p < kP; ++p) {
-    const int bj = (p >> J) & 1;
-    float2 ff;
-    if constexpr (K == svp::kPackSlot) {
-      if (EQ) ff = bj ? f2(0.f, 1.f) : f2(1.f, 0.f);
-      else if (bj) ff = f2(1.f, -1.f);
-      else continue;
-    } else {
-      const int bk = (p >> K) & 1;
-      if (EQ) {
-        if (bj == bk) continue;
-        ff = f2(0.f, 0.f);
+    for (int p = 0; p < kP; ++p) {
+      const int bj = (p >> J) & 1;
+      float2 ff;
+      if constexpr (K == svp::kPackSlot) {
+        if (EQ) ff = bj ? f2(0.f, 1.f) : f2(1.f, 0.f);
+        else if (bj) ff = f2(1.f, -1.f);
+        else continue;
       } else {
-        if (!(bj && bk)) continue;
-        ff = f2(-1.f, -1.f);
+        const int bk = (p >> K) & 1;
+        if (EQ) {
+          if (bj == bk) continue;
+          ff = f2(0.f, 0.f);
+        } else {
+          if (!(bj && bk)) continue;
+          ff = f2(-1.f, -1.f);
+        }
       }
+      R[p] = mul2(R[p], ff);
+      I[p] = mul2(I[p], ff);
     }
-    R[p] = mul2(R[p], ff);
-    I[p] = mul2(I[p], ff);
   }
 }
+
 __device__ __forceinline__ void scale_all(Regs &R, Regs &I, float f) {
   const float2 ff = f2(f, f);
 #pragma unroll
@@ -233,6 +240,7 @@ __device__ __forceinline__ void phase_all(Regs &R, Regs &I, int p) {
   }
 }
 
+#ifndef SV_PLAN_KERNELS  // the interpreter: not needed by the kernels compiled for one plan
 // One op by its flat code.  `cond`: the op's condition on the thread's fixed qubits.
 // Signs and projectors of conditional diagonal ops become factors (1 where the
 // condition fails); scalar phases and zeroing of the group are only recorded.  The
@@ -314,6 +322,8 @@ __device__ __forceinline__ void apply_ops(Regs &R, Regs &I, const DevOp *ops, co
   }
 }
 
+#endif  // SV_PLAN_KERNELS
+
 // ---- addressing ---------------------------------------------------------------------------
 // 16-byte slot of pair k (tile bits 1..m-1): pair bit i toggles slot bit i mod 3, so the
 // 8 lanes of a quarter warp hit distinct 16-byte bank groups when the planner gives them
@@ -362,6 +372,45 @@ __device__ __forceinline__ void store_group(float4 *tile, const DevPlanView &pla
   }
 }
 
+// The same with the register-slot masks given (the kernels compiled for one plan pass
+// them as constants).
+__device__ __forceinline__ void load_group_rx(const float4 *tile, uint32_t a0, const uint32_t (&rx)[kPR], Regs &R,
+                                              Regs &I) {
+  const char *tb = reinterpret_cast<const char *>(tile);
+#pragma unroll
+  for (int p = 0; p < kP; ++p) {
+    uint32_t a = a0;
+#pragma unroll
+    for (int j = 0; j < kPR; ++j)
+      if ((p >> j) & 1) a ^= rx[j];
+    const float4 x = *reinterpret_cast<const float4 *>(tb + a);
+    R[p] = f2(x.x, x.y);
+    I[p] = f2(x.z, x.w);
+  }
+}
+__device__ __forceinline__ void store_group_rx(float4 *tile, uint32_t a0, const uint32_t (&rx)[kPR], const Regs &R,
+                                               const Regs &I) {
+  char *tb = reinterpret_cast<char *>(tile);
+#pragma unroll
+  for (int p = 0; p < kP; ++p) {
+    uint32_t a = a0;
+#pragma unroll
+    for (int j = 0; j < kPR; ++j)
+      if ((p >> j) & 1) a ^= rx[j];
+    *reinterpret_cast<float4 *>(tb + a) = make_float4(R[p].x, R[p].y, I[p].x, I[p].y);
+  }
+}
+
+// End of a stage's ops: the recorded zeroing, deferred factors 1/2 and scalar phase.
+__device__ __forceinline__ void end_stage(Regs &R, Regs &I, int halves, int ph, bool zero) {
+  if (zero) {
+    scale_all(R, I, 0.f);
+  } else {
+    if (halves) scale_all(R, I, __int_as_float((127 - halves) << 23));  // 2^-halves, exact
+    if (ph & 7) phase_all(R, I, ph & 7);
+  }
+}
+
 // Base index of tile `tile_id`: its bits spread over the non-tile qubits.
 __device__ __forceinline__ uint64_t tile_base(const DevPass &P, uint64_t tile_id) {
   uint64_t base = 0;
@@ -380,30 +429,36 @@ __device__ __forceinline__ void build_chunk_table(const DevPass &P, uint64_t *ch
   }
 }
 
-// Read the tile into shared memory as swizzled pairs: thread t moves pairs t, t + T, ...
-// (T threads, 32 pairs each), 8 coalesced 16-byte loads in flight.  kL2Only reads
-// through L2 only (for data other CTAs of the same launch wrote).
-template <bool kL2Only = false>
-__device__ __forceinline__ void load_tile(const float2 *__restrict__ psi, float4 *tile, const DevPass &P,
-                                          const uint64_t *chunk_off, uint64_t base) {
+// Shared memory holds pair k at slot pack_phys(k) as (re, re', im, im').  Thread t moves
+// pairs t, t + T, ... (T threads, kP pairs each) in coalesced 16-byte vectors.
+
+// Asynchronous read (cp.async through L2, no register staging) of the pairs as they are
+// in memory, (re, im, re', im'), one commit group.  L2 is coherent, so the copies also see
+// data that other CTAs of the same launch wrote.  finish_tile_load() waits for the
+// thread's own copies and regroups them (each thread touches only its own slots).
+__device__ __forceinline__ void load_tile_async(const float2 *__restrict__ psi, float4 *tile, const DevPass &P,
+                                                const uint64_t *chunk_off, uint64_t base) {
   const uint32_t tid = threadIdx.x, T = blockDim.x;
   const int cp = P.c - 1;  // pair bits inside a chunk of 2^c amplitudes
   const uint32_t in_mask = (1u << cp) - 1;
-  constexpr int kBatch = 8;
-#pragma unroll 1
-  for (int it0 = 0; it0 < kP; it0 += kBatch) {
-    float4 buf[kBatch];
-#pragma unroll
-    for (int b = 0; b < kBatch; ++b) {
-      const uint32_t k = tid + (uint32_t)(it0 + b) * T;
-      const float4 *src = reinterpret_cast<const float4 *>(psi + base + chunk_off[k >> cp] + 2 * (k & in_mask));
-      buf[b] = kL2Only ? __ldcg(src) : *src;
-    }
-#pragma unroll
-    for (int b = 0; b < kBatch; ++b) {
-      const uint32_t k = tid + (uint32_t)(it0 + b) * T;
-      tile[pack_phys(k)] = make_float4(buf[b].x, buf[b].z, buf[b].y, buf[b].w);
-    }
+  const uint32_t sbase = (uint32_t)__cvta_generic_to_shared(tile);
+#pragma unroll 4
+  for (int it = 0; it < kP; ++it) {
+    const uint32_t k = tid + (uint32_t)it * T;
+    const float2 *src = psi + base + chunk_off[k >> cp] + 2 * (k & in_mask);
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(sbase + 16u * pack_phys(k)), "l"(src)
+                 : "memory");
+  }
+  asm volatile("cp.async.commit_group;" ::: "memory");
+}
+__device__ __forceinline__ void finish_tile_load(float4 *tile) {
+  asm volatile("cp.async.wait_group 0;" ::: "memory");
+  const uint32_t tid = threadIdx.x, T = blockDim.x;
+#pragma unroll 4
+  for (int it = 0; it < kP; ++it) {
+    float4 &x = tile[pack_phys(tid + (uint32_t)it * T)];
+    const float4 y = x;
+    x = make_float4(y.x, y.z, y.y, y.w);
   }
 }
 
@@ -416,8 +471,7 @@ __device__ __forceinline__ void store_tile(float2 *__restrict__ psi, const float
   for (int it = 0; it < kP; ++it) {
     const uint32_t k = tid + (uint32_t)it * T;
     const float4 x = tile[pack_phys(k)];
-    *reinterpret_cast<float4 *>(psi + base + chunk_off[k >> cp] + 2 * (k & in_mask)) =
-        make_float4(x.x, x.z, x.y, x.w);
+    *reinterpret_cast<float4 *>(psi + base + chunk_off[k >> cp] + 2 * (k & in_mask)) = make_float4(x.x, x.z, x.y, x.w);
   }
 }
 
@@ -437,18 +491,15 @@ __device__ __forceinline__ void init_tile(float4 *tile, const DevPass &P, uint64
   if (!(P.flags & svp::PF_INIT_UNIFORM) && base == 0 && threadIdx.x == 0) tile[0] = make_float4(1.f, 0.f, 0.f, 0.f);
 }
 
-// One tile of one packed pass: load (or generate), every stage in registers, store.
-// The caller has built chunk_off for P and synchronised; ends with __syncthreads.
-template <bool kL2Only = false>
+#ifndef SV_PLAN_KERNELS  // the interpreter
+// One tile of one packed pass whose data is in `tile` (or is generated): every stage in
+// registers, then the store.  Ends with __syncthreads.
 __device__ __forceinline__ void process_tile(float2 *__restrict__ psi, const DevPlanView &plan, const DevPass &P,
                                              const uint64_t *chunk_off, float4 *tile, uint64_t tile_id) {
   const int tid = threadIdx.x;
   const uint64_t base = tile_base(P, tile_id);
   const bool init = (P.flags & (svp::PF_INIT_UNIFORM | svp::PF_INIT_ZERO)) != 0;
-  if (!init) {
-    load_tile<kL2Only>(psi, tile, P, chunk_off, base);
-    __syncthreads();
-  } else if (P.stage_count == 0) {
+  if (init && P.stage_count == 0) {
     init_tile(tile, P, base);
     __syncthreads();
   }
@@ -469,6 +520,25 @@ __device__ __forceinline__ void process_tile(float2 *__restrict__ psi, const Dev
   store_tile(psi, tile, P, chunk_off, base);
   __syncthreads();
 }
+
+// A CTA's sweep over its tiles (tile_id = first, first + stride, ...): read, process.
+// (A second buffer with the next tile's read in flight measured slower: it halves the
+// resident CTAs, and this kernel is bound by latency, not by bandwidth.)
+__device__ __forceinline__ void sweep_tiles(float2 *__restrict__ psi, const DevPlanView &plan, const DevPass &P,
+                                            const uint64_t *chunk_off, float4 *tile, uint64_t first, uint64_t stride,
+                                            uint64_t num_tiles) {
+  const bool init = (P.flags & (svp::PF_INIT_UNIFORM | svp::PF_INIT_ZERO)) != 0;
+  for (uint64_t tile_id = first; tile_id < num_tiles; tile_id += stride) {
+    if (!init) {
+      load_tile_async(psi, tile, P, chunk_off, tile_base(P, tile_id));
+      finish_tile_load(tile);
+      __syncthreads();
+    }
+    process_tile(psi, plan, P, chunk_off, tile, tile_id);
+  }
+}
+
+#endif  // SV_PLAN_KERNELS
 
 }  // namespace tpk
 }  // namespace svk

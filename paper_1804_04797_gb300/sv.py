@@ -30,7 +30,7 @@ class SvError(RuntimeError):
 
 class sv_options(ctypes.Structure):
     _fields_ = [('fuse_k', c_int), ('precision', c_int), ('autotune', c_int), ('stream', c_void_p),
-                ('tile_bits', c_int), ('low_bits', c_int)]
+                ('tile_bits', c_int), ('low_bits', c_int), ('jit', c_int)]
 
 
 class sv_lattice(ctypes.Structure):
@@ -49,7 +49,7 @@ class sv_plan_summary(ctypes.Structure):
 
 class sv_profile(ctypes.Structure):
     _fields_ = [('launches', c_int), ('ms', c_double), ('hbm_bytes', c_double), ('h2d_bytes', c_double),
-                ('d2h_bytes', c_double), ('other_launches', c_int)]
+                ('d2h_bytes', c_double), ('other_launches', c_int), ('jit_launches', c_int)]
 
 
 _lib = None
@@ -92,6 +92,7 @@ def lib():
         'sv_norm_noalloc': ([vp, c_int, vp, P(c_double), P(c_double)], c_int),
         'sv_plan': ([c_int, vp, c_size_t, P(sv_options), c_int, P(sv_plan_summary), vp, vp, vp,
                      c_size_t], c_int),
+        'sv_jit_check': ([c_int, vp, c_size_t, P(sv_options), c_int, ctypes.c_char_p, c_size_t], c_int),
         'sv_set_profiling': ([vp, c_int], c_int),
         'sv_get_profile': ([vp, P(sv_profile)], c_int),
     }
@@ -108,8 +109,8 @@ def _check(status):
         raise SvError(status, lib().sv_last_error().decode())
 
 
-def options(precision=SV_PREC_PLAIN, fuse_k=0, tile_bits=0, low_bits=0, stream=None, autotune=0):
-    return sv_options(fuse_k, precision, autotune, stream, tile_bits, low_bits)
+def options(precision=SV_PREC_PLAIN, fuse_k=0, tile_bits=0, low_bits=0, stream=None, autotune=0, jit=0):
+    return sv_options(fuse_k, precision, autotune, stream, tile_bits, low_bits, jit)
 
 
 def lattice(lat):
@@ -275,6 +276,18 @@ def sv_plan(n_qubits, gates, opts=None, fresh_state=True):
                          int(bool(fresh_state)), ctypes.byref(summ), order.ctypes.data,
                          pass_of.ctypes.data, tiles.ctypes.data, tiles.size))
     return summ, order[:n], pass_of[:n], tiles.reshape(-1, 64)[:summ.passes]
+
+
+def sv_jit_check(n_qubits, gates, opts=None, fresh_state=True):
+    """Compile the plan-specialised kernels of a gate list for sm_103a (NVRTC, no device).
+    Returns the compiler log; raises SvError if the compile fails."""
+    g, p, n = _gates(gates)
+    buf = ctypes.create_string_buffer(1 << 16)
+    st = lib().sv_jit_check(n_qubits, p, n, ctypes.byref(opts) if opts is not None else None,
+                            int(bool(fresh_state)), buf, len(buf))
+    if st != SV_OK:
+        raise SvError(st, lib().sv_last_error().decode() + '\n' + buf.value.decode(errors='replace'))
+    return buf.value.decode(errors='replace')
 
 
 def sv_set_profiling(h, on):

@@ -48,7 +48,8 @@ H16 = sv.SV_PREC_F16X3
 MODES = [dict(), dict(tile_bits=10, low_bits=4, fuse_k=5), dict(tile_bits=8, low_bits=2, fuse_k=3),
          dict(tile_bits=12, low_bits=5, fuse_k=4), dict(precision=sv.SV_PREC_PERGATE),
          dict(precision=TC), dict(precision=TC, tile_bits=12), dict(precision=TC, tile_bits=12, low_bits=3),
-         dict(precision=H16), dict(precision=H16, tile_bits=12)]
+         dict(precision=H16), dict(precision=H16, tile_bits=12),
+         dict(jit=1), dict(jit=1, tile_bits=12), dict(jit=1, tile_bits=8, low_bits=2, fuse_k=3), dict(jit=-1)]
 
 
 @pytest.mark.parametrize('kw', MODES)
@@ -76,7 +77,8 @@ def test_sizes_match_oracle(lat):
     n, gates = oracle_gates(lat)
     want = csim.run(n, gates)
     for kw in (dict(), dict(tile_bits=min(13, max(6, n)), low_bits=min(4, n), fuse_k=5), dict(precision=TC),
-               dict(precision=TC, tile_bits=12), dict(precision=H16), dict(precision=H16, tile_bits=12)):
+               dict(precision=TC, tile_bits=12), dict(precision=H16), dict(precision=H16, tile_bits=12),
+               dict(jit=1), dict(jit=-1)):
         psi, norm2, _ = run_gpu(lat, **kw)
         assert rel_l2(psi, want) <= REL_L2, kw
         assert abs(norm2 - 1) <= NORM_TOL
@@ -126,6 +128,7 @@ def _oracle_apply(n, gl, psi):
 
 
 @pytest.mark.parametrize('n,kw', [(7, {}), (13, {}), (18, {}), (18, dict(tile_bits=9, low_bits=3, fuse_k=2)),
+                                  (13, dict(jit=1)), (18, dict(jit=1)), (18, dict(jit=1, tile_bits=9, low_bits=3)),
                                   (16, dict(precision=sv.SV_PREC_PERGATE)), (12, dict(precision=TC)),
                                   (17, dict(precision=TC)), (19, dict(precision=TC, tile_bits=12)),
                                   (17, dict(precision=H16)), (19, dict(precision=H16, tile_bits=12))])
@@ -149,12 +152,13 @@ def test_all_gate_kinds_from_zero_and_loaded_state(n, kw):
         sv.sv_destroy(h)
 
 
-def test_projectors_zero_exactly():
+@pytest.mark.parametrize('jit', [-1, 1])
+def test_projectors_zero_exactly(jit):
     n = 12
     gl = [('H', q, -1) for q in range(n)] + [('SX', 3, -1), ('CZ', 3, 9, -1)]
     codes = sv.gates_from_tuples([(_CODE[k], a, max(b, 0), 0) for (k, a, b, *_r) in gl] +
                                  [(5, 3, 0, 1), (6, 9, 0, 1), (5, 0, 0, 1)])
-    h = sv.sv_create(n)
+    h = sv.sv_create(n, sv.options(jit=jit))
     try:
         sv.sv_apply_circuit(h, codes)
         psi = sv.sv_copy_state(h, n)
@@ -180,6 +184,29 @@ def test_inverse_circuit_returns_to_zero_state(prec):
     e0 = np.zeros(1 << 20, dtype=np.complex128)
     e0[0] = 1
     assert rel_l2(psi, e0) <= 1e-5
+
+
+@pytest.mark.parametrize('lat,gl', [(inputs.lattice_for(4, 5, 18, seed=11), None),
+                                    (None, _random_gate_list(19, 150, seed=77))])
+def test_plan_kernels_bitwise_equal_to_interpreter(lat, gl):
+    """The kernels compiled for a plan run the interpreter's arithmetic op for op."""
+    if lat is not None:
+        n, g = lat.n_qubits, sv.sv_generate_circuit(lat)
+    else:
+        n, g = 19, _to_lib(gl)
+    out = {}
+    for jit in (-1, 1):
+        h = sv.sv_create(n, sv.options(jit=jit))
+        try:
+            sv.sv_set_profiling(h, True)
+            sv.sv_apply_circuit(h, g)
+            prof = sv.sv_get_profile(h)
+            out[jit] = sv.sv_copy_state(h, n)
+        finally:
+            sv.sv_destroy(h)
+        assert (prof.jit_launches > 0) == (jit == 1)
+        assert prof.jit_launches == (prof.launches if jit == 1 else 0)
+    assert np.array_equal(out[-1].view(np.uint32), out[1].view(np.uint32))
 
 
 def test_amplitudes_and_probabilities_gather():

@@ -122,3 +122,40 @@ def test_planner_rejects_invalid_gates():
         sv.sv_plan(8, bad)
     with pytest.raises(sv.SvError):
         sv.sv_plan(8, sv.gates_from_tuples([(0, 1, 0, 0)]), sv.options(tile_bits=14))
+
+
+def _all_kind_gates(n, count, seed):
+    rng = np.random.default_rng(seed)
+    out = []
+    for _ in range(count):
+        k = int(rng.integers(11))
+        if k in (5, 6):  # projectors: keep them rare
+            k = 7
+        a = int(rng.integers(n))
+        b = int(rng.integers(n - 1))
+        b = b + 1 if b >= a else b
+        out.append((k, a, b if k == 4 else 0, 1))
+    return sv.gates_from_tuples(out)
+
+
+@pytest.mark.parametrize('case', ['16q_d10', '30q_d20', 'all_kinds_18q', 'tile9_all_kinds_14q', 'projectors_12q'])
+def test_plan_kernels_compile_without_a_device(case):
+    """The code generator's kernels compile for sm_103a (NVRTC, no GPU needed)."""
+    if case == '16q_d10':
+        n, g, o = 16, sv.sv_generate_circuit(inputs.C16), None
+    elif case == '30q_d20':
+        n, g, o = 30, sv.sv_generate_circuit(inputs.C30), None
+    elif case == 'all_kinds_18q':
+        n, g, o = 18, _all_kind_gates(18, 200, 5), None
+    elif case == 'tile9_all_kinds_14q':
+        n, g, o = 14, _all_kind_gates(14, 120, 6), sv.options(tile_bits=9, low_bits=3, fuse_k=3)
+    else:
+        n = 12
+        g = sv.gates_from_tuples([(0, q, 0, 0) for q in range(n)] + [(5, 3, 0, 1), (6, 9, 0, 1), (4, 2, 7, 1)])
+        o = None
+    try:
+        sv.sv_jit_check(n, g, o)
+    except sv.SvError as e:
+        if 'libnvrtc not found' in str(e):
+            pytest.skip('NVRTC not installed')
+        raise
