@@ -170,6 +170,25 @@ __device__ __forceinline__ void factor(Regs &R, Regs &I, float f) {
       if (((p >> J) & 1) == B) { R[p] = mul2(R[p], ff); I[p] = mul2(I[p], ff); }
   }
 }
+// -1 where register slot J equals B (a plain negation: the compiler may fold it into
+// the next operation's operand)
+template <int J, int B>
+__device__ __forceinline__ void negate(Regs &R, Regs &I) {
+  if constexpr (J < kPR) {
+#pragma unroll
+    for (int p = 0; p < kP; ++p)
+      if (((p >> J) & 1) == B) { R[p] = f2(-R[p].x, -R[p].y); I[p] = f2(-I[p].x, -I[p].y); }
+  }
+}
+// -1 where the pack bit equals B
+template <int B>
+__device__ __forceinline__ void negate_pack(Regs &R, Regs &I) {
+#pragma unroll
+  for (int p = 0; p < kP; ++p) {
+    if (B) { R[p].y = -R[p].y; I[p].y = -I[p].y; }
+    else { R[p].x = -R[p].x; I[p].x = -I[p].x; }
+  }
+}
 // factor f where the pack bit equals B
 template <int B>
 __device__ __forceinline__ void factor_pack(Regs &R, Regs &I, float f) {
@@ -185,23 +204,23 @@ __device__ __forceinline__ void two(Regs &R, Regs &I) {
 #pragma unroll
     for (int p = 0; p < kP; ++p) {
       const int bj = (p >> J) & 1;
-      float2 ff;
       if constexpr (K == svp::kPackSlot) {
-        if (EQ) ff = bj ? f2(0.f, 1.f) : f2(1.f, 0.f);
-        else if (bj) ff = f2(1.f, -1.f);
-        else continue;
+        if (EQ) {
+          if (bj) { R[p].x = 0.f; I[p].x = 0.f; }
+          else { R[p].y = 0.f; I[p].y = 0.f; }
+        } else if (bj) {
+          R[p].y = -R[p].y;
+          I[p].y = -I[p].y;
+        }
       } else {
         const int bk = (p >> K) & 1;
         if (EQ) {
-          if (bj == bk) continue;
-          ff = f2(0.f, 0.f);
-        } else {
-          if (!(bj && bk)) continue;
-          ff = f2(-1.f, -1.f);
+          if (bj != bk) { R[p] = f2(0.f, 0.f); I[p] = f2(0.f, 0.f); }
+        } else if (bj && bk) {
+          R[p] = f2(-R[p].x, -R[p].y);
+          I[p] = f2(-I[p].x, -I[p].y);
         }
       }
-      R[p] = mul2(R[p], ff);
-      I[p] = mul2(I[p], ff);
     }
   }
 }
