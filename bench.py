@@ -36,6 +36,35 @@ def _peaks():
         return 6800.0, 'fallback'
 
 
+# DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) per algorithmic byte of the
+# dominant kernels, from one ncu capture each on a 28-qubit depth-30 pass (2^28
+# amplitudes; profiles/sv_pass_plain_28q_d30.md, profiles/fused_pass_kernel_f16_28q_d30.md);
+# a pass moves each amplitude once in and once out, so traffic scales with the amplitudes.
+TRAFFIC_PER_ALGORITHMIC_BYTE = {
+    'sv_pass': (2.147615e9 + 2.086388e9) / (16.0 * 2 ** 28),
+    'fused_pass_kernel<f16>': (2.147713e9 + 2.096311e9) / (16.0 * 2 ** 28),
+}
+SMS, FP32_LANES_PER_SM = 152, 128
+
+
+def algorithmic_flops_per_amplitude(gates):
+    """Real additions and multiplications the gate list needs per amplitude: a square root
+    of X or Y updates a pair with 8 real adds (4 per amplitude; its 1/2 is an exact
+    power-of-two scale), H with 8 adds + 4 multiplies (6), T and its adjoint multiply half
+    the amplitudes by (1 +- i)/sqrt2 (2 adds + 2 multiplies each: 2 per amplitude); Z, CZ
+    and the projectors change signs or zero and take none.  The leading layer of H on a
+    fresh state is the generated uniform state."""
+    kinds = [int(k) for k in gates['kind']]
+    i = 0
+    seen = set()
+    while i < len(kinds) and kinds[i] == 0 and int(gates['q0'][i]) not in seen:
+        seen.add(int(gates['q0'][i]))
+        i += 1
+    rest = kinds[i:]
+    return 4.0 * sum(k in (2, 3, 9, 10) for k in rest) + 6.0 * sum(k == 0 for k in rest) + \
+        2.0 * sum(k in (1, 8) for k in rest)
+
+
 class Clocks:
     """nvidia-smi sampling during the timed region."""
     FIELDS = ('index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,'
@@ -352,6 +381,14 @@ def main():
         v, dt, cores, desc = _oracle_sample()
         cpu = {'value': v, 'unit': UNIT, 'cores': cores, 'kind': 'oracle', 'sample': desc}
     achieved = best['achieved_gbs']
+    kernel = {'plain': 'sv_pass' if best.get('plan_kernel_launches') else 'tile_pass_kernel',
+              'plain_interp': 'tile_pass_kernel', 'tf32x3': 'fused_pass_kernel<tf32>',
+              'f16x3': 'fused_pass_kernel<f16>', 'pergate': 'gate1q_kernel/diag_kernel'}[best_name]
+    ratio = TRAFFIC_PER_ALGORITHMIC_BYTE.get(kernel)
+    flops = algorithmic_flops_per_amplitude(gates) * 2.0 ** n
+    sm_mhz = (best['clocks'] or {}).get('sm_max_mhz') or 2070.0
+    fp32_peak = SMS * FP32_LANES_PER_SM * sm_mhz * 1e6 / 1e12
+    fp32_achieved = flops / best['s_per_circuit'] / 1e12
     line = {
         'metric': METRIC, 'value': value, 'unit': UNIT, 'n_gpus': world, 'steps': args.steps,
         'warmup': args.warmup, 'ms_per_step': best['s_per_circuit'] * 1e3, 'higher_is_better': False,
@@ -362,15 +399,15 @@ def main():
                                                                                           lat.depth),
                    'state_bytes': 8 * 2 ** n, 'l2': 'state 137 GB >> L2 129 MB, no flush needed',
                    'path': best_name, 'replicas': world},
-        'roofline': {'bound': 'hbm', 'kernel': {'plain': 'sv_pass (plan-specialised tile pass)'
-                                                if best.get('plan_kernel_launches') else 'tile_pass_kernel',
-                                                'plain_interp': 'tile_pass_kernel',
-                                                'tf32x3': 'fused_pass_kernel<tf32>',
-                                                'f16x3': 'fused_pass_kernel<f16>',
-                                                'pergate': 'gate1q_kernel/diag_kernel'}[best_name],
-                     'achieved': achieved, 'peak': hbm_peak, 'unit': 'GB/s', 'frac': achieved / hbm_peak,
-                     'traffic': None, 'peak_kind': peak_kind,
+        'roofline': {'bound': 'hbm', 'kernel': kernel, 'achieved': achieved, 'peak': hbm_peak, 'unit': 'GB/s',
+                     'frac': achieved / hbm_peak,
+                     'traffic': ratio * best['bytes_per_launch'] if ratio else None, 'peak_kind': peak_kind,
                      'bytes_per_launch': best['bytes_per_launch'], 'per_launch_ms': best['per_launch_ms']},
+        # the plain kernel's limit is the FP32 pipe: algorithmic flops of the circuit over
+        # the whole circuit's time, against one add or multiply per FP32 lane per clock
+        'roofline_alu': {'bound': 'alu', 'kernel': kernel, 'achieved': fp32_achieved, 'peak': fp32_peak,
+                         'unit': 'TFLOP/s', 'frac': fp32_achieved / fp32_peak,
+                         'flops_per_circuit': flops, 'peak_kind': '152 SMs x 128 FP32 lanes x max SM clock'},
         'clocks': best['clocks'],
         'e2e': e2e,
         'gpu_launches': int(round(best['launches_per_step'] * args.steps)),
