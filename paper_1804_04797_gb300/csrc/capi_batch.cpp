@@ -101,8 +101,9 @@ sv_status build_batch(const sv_lattice *circs, size_t count, int m_req, Batch *B
   svp::Options po;
   po.m = m;
   po.c = 4;
-  po.r = 5;
-  po.rk = 5;
+  po.pack = true;  // the batch kernel runs the packed interpreter
+  po.rk = svk::tile_pass_register_slots();
+  po.r = po.rk;
   // combined plan
   std::vector<svp::DevPass> passes;
   std::vector<svp::DevStage> stages;

@@ -5,18 +5,20 @@
 // until every tile of pass p-1 of the same circuit is done (a per-circuit-pass counter),
 // with a bounded spin: a wait that gives up sets the error word and the CTA leaves.  The
 // queue holds all circuits' first passes, then all second passes, ..., so the waits are
-// rare and short.  The state is read through L2 only, because other CTAs of the same
-// launch wrote it and L1 is not coherent across SMs.
+// rare and short.  The state is read through L2 only (cp.async.cg), because other CTAs
+// of the same launch wrote it and L1 is not coherent across SMs.  The tile pass is the
+// packed interpreter of the single-circuit path (tile_pack.cuh).
 #include <cuda_runtime.h>
 
 #include "batch.h"
-#define SV_TILE_R 5
-#include "tile_common.cuh"
+#include "kernels.h"
+#define SV_PACK_R 4
+#include "tile_pack.cuh"
 
 namespace svk {
 namespace {
 
-using namespace tile;
+using namespace tpk;
 
 __device__ __forceinline__ unsigned long long now_ns() {
   unsigned long long t;
@@ -35,7 +37,7 @@ batch_kernel(float2 *__restrict__ states, DevPlanView plan, const BatchCP *__res
              const BatchItem *__restrict__ items, uint64_t n_items, unsigned int *words,
              unsigned long long wait_ns) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  float2 *tile = reinterpret_cast<float2 *>(smem_raw);
+  float4 *tile = reinterpret_cast<float4 *>(smem_raw);
   __shared__ DevPass P;
   __shared__ uint64_t chunk_off[1 << 10];
   __shared__ unsigned int s_item;
@@ -75,7 +77,13 @@ batch_kernel(float2 *__restrict__ states, DevPlanView plan, const BatchCP *__res
     }
     __syncthreads();
     if (s_stop) break;
-    process_tile_plain<true>(states + cp.state_off, plan, P, chunk_off, tile, it.tile);
+    float2 *psi = states + cp.state_off;
+    if (!(P.flags & (svp::PF_INIT_UNIFORM | svp::PF_INIT_ZERO))) {
+      load_tile_async(psi, tile, P, chunk_off, tile_base(P, it.tile));
+      finish_tile_load(tile);
+      __syncthreads();
+    }
+    process_tile(psi, plan, P, chunk_off, tile, it.tile);
     __threadfence();  // each thread's stores visible device-wide before the count
     __syncthreads();
     if (tid == 0) atomicAdd(&done[it.cp], 1u);
@@ -123,7 +131,7 @@ __global__ void batch_stats_final(const double *partials, const int *chunk_begin
 
 }  // namespace
 
-int batch_block_threads(int m) { return 1 << (m - kR); }
+int batch_block_threads(int m) { return 1 << (m - 1 - kPR); }
 
 cudaError_t launch_batch(float2 *states, const DevPlanView &plan, const BatchCP *cps, const BatchItem *items,
                          uint64_t n_items, unsigned int *words, int m, cudaStream_t st,
