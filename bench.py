@@ -239,6 +239,34 @@ def run_branch(args, rank, world):
     return 0
 
 
+def run_inner(args, rank, world):
+    """Task 2 by the inner product: amplitudes of the 34-qubit depth-30 circuit cut after
+    layer 15, <U2^dagger x | U1 H^n 0> for 4 bitstrings (one forward state, one backward
+    state per bitstring; two 128 GiB states).  s per amplitude, whole call timed."""
+    import numpy as np
+    import torch
+    from paper_1804_04797_gb300 import inputs, sv
+    torch.cuda.set_device(int(os.environ.get('LOCAL_RANK', '0')))
+    lat = inputs.C34
+    bits = np.array(inputs.bitstrings(lat.n_qubits, 4, seed=2), dtype=np.uint64)
+    for _ in range(max(1, args.warmup)):
+        sv.sv_amplitudes_by_inner_product(lat, 15, bits)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        amps = sv.sv_amplitudes_by_inner_product(lat, 15, bits)
+    torch.cuda.synchronize()
+    dt = (time.perf_counter() - t0) / args.steps
+    if rank == 0:
+        print(json.dumps({
+            'metric': '34q depth-30 amplitude by forward/backward inner product, s per amplitude',
+            'workload': 'inner34', 'value': dt / len(bits), 'unit': 's/amplitude', 'higher_is_better': False,
+            'n_gpus': world, 'steps': args.steps, 'warmup': args.warmup,
+            'config': {'workload': '6x6-minus-corners lattice, depth 30, cut after layer 15, 4 bitstrings (seed 2)'},
+            's_per_call': dt, 'amp0': [float(amps[0].real), float(amps[0].imag)]}), flush=True)
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument('--gpus', type=int, default=1)
@@ -249,7 +277,7 @@ def main():
     ap.add_argument('--no-fused', action='store_true')
     ap.add_argument('--paths', default='plain,tf32x3,f16x3', help='comma list of plain, tf32x3, f16x3, pergate')
     ap.add_argument('--tile-bits', type=int, default=0, help='tile qubits of the tile passes (0 = default 13)')
-    ap.add_argument('--workload', default='34q', choices=['34q', 'batch', 'branch42'],
+    ap.add_argument('--workload', default='34q', choices=['34q', 'batch', 'branch42', 'inner34'],
                     help='34q: the headline circuit; batch: the 512-circuit uneven batch; branch42: the '
                          '42-qubit cut-branch amplitude task (secondary lines)')
     ap.add_argument('--depth', type=int, default=0, help='override the lattice depth (profiling of smaller cases)')
@@ -265,6 +293,8 @@ def main():
         return run_batch(args, rank, world)
     if args.workload == 'branch42':
         return run_branch(args, rank, world)
+    if args.workload == 'inner34':
+        return run_inner(args, rank, world)
 
     import numpy as np
     import torch

@@ -250,6 +250,24 @@ typedef struct {
   int jit_launches;   /* tile passes run on plan-specialised (run-time compiled) kernels */
 } sv_profile;
 
+/* The basis state |x> (1 at index x, 0 elsewhere).  SV_ERR_ARG if x has bits >= n. */
+sv_status sv_set_basis_state(sv_state *s, uint64_t x);
+
+/* <a|b> = sum_i conj(a_i) b_i of two states of the same size on the same device, into
+ * out_re_im[0..1] (fp64 accumulation of fp32 products: 8 products per fp32 chunk, chunk
+ * sums in fp64).  Waits for b's stream, runs on a's and synchronises it. */
+sv_status sv_inner_product(sv_state *a, sv_state *b, double *out_re_im);
+
+/* Task 2 by the inner product of two states (§2 "Calculating one or a few amplitudes",
+ * the equation alpha_x = <phi|psi>): the lattice circuit U = U2 U1 is cut after layer
+ * split_layer (U1 = layers 0..split_layer, the H layer included; U2 = the rest),
+ * |psi> = U1 H^n |0> is computed once, and for every bitstring x, |phi_x> = U2^dagger |x>
+ * and alpha_x = <phi_x|psi>.  Two n-qubit states are allocated (2 x 8 x 2^n bytes, at
+ * most n = 34 on GB300) and freed on return; out_re_im receives 2m doubles.  A
+ * split_layer at or beyond the depth gives the plain amplitudes of the full state. */
+sv_status sv_amplitudes_by_inner_product(const sv_lattice *lat, int split_layer, const uint64_t *bits, size_t m,
+                                         const sv_options *opts, double *out_re_im);
+
 /* Compile the plan-specialised kernels of a gate list for sm_103a without a device
  * (NVRTC only; no cache is read or written): a check of the code generator.  log (may
  * be NULL) receives up to log_cap bytes of the compiler's messages, NUL-terminated.

@@ -19,6 +19,9 @@ What each function follows
     two product terms, so alpha_x = sum_l <x_A|A_l> <x_B|B_l> over l in {0,1}^t.
   * norm2 / sum_p2: sum |alpha|^2 and sum |alpha|^4 (Porter-Thomas statistic, §3
     final figure: for chaotic states N * sum p^2 -> 2).
+  * amplitudes_inner_product: Task 2 by the inner product (§2 "Calculating one or a few
+    amplitudes"): U = U2 U1, |psi> = U1 H^n |0>, |phi> = U2^dagger |x>, alpha_x =
+    <phi|psi>.
 
 Gate matrices (the paper names the gates but prints no matrices; reading):
   H = (1/sqrt2)[[1,1],[1,-1]], T = diag(1, e^{i pi/4}),
@@ -209,3 +212,18 @@ def branch_amplitudes(n, gates, half_a_mask, bitstrings):
         acc += A[xa] * B[xb]
     return acc
 
+
+
+def amplitudes_inner_product(n, gates, split_layer, bitstrings):
+    """alpha_x = <phi_x|psi> with psi = (gates of layers <= split_layer) |0..0> (the H
+    layer is layer 0) and phi_x = (gates of later layers)^dagger |x>."""
+    g1 = [g for g in gates if g[3] <= split_layer]
+    g2 = [g for g in gates if g[3] > split_layer]
+    psi = run(n, g1)
+    out = np.zeros(len(bitstrings), dtype=np.complex128)
+    for j, x in enumerate(bitstrings):
+        e = np.zeros(1 << n, dtype=np.complex128)
+        e[int(x)] = 1.0
+        phi = run_adjoint(n, g2, e)
+        out[j] = np.vdot(phi, psi)  # conj(phi) . psi
+    return out

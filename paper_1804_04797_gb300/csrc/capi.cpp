@@ -101,7 +101,7 @@ using namespace svc;
 
 // ---------------------------------------------------------------------------------------
 
-namespace {
+namespace svc {
 
 sv_status set_device(sv_state *s) {
   cudaError_t e = cudaSetDevice(s->device);
@@ -116,6 +116,10 @@ sv_status materialize(sv_state *s) {
   s->fresh = false;
   return SV_OK;
 }
+
+}  // namespace svc
+
+namespace {
 
 void prof_begin(sv_state *s) {
   if (!s->prof) return;

@@ -1,4 +1,5 @@
-// C ABI of the few-amplitude task: amplitudes by the cut decomposition (K6).
+// C ABI of the few-amplitude task: amplitudes by the cut decomposition (K6) and by the
+// inner product of a forward and a backward state.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -121,5 +122,80 @@ extern "C" sv_status sv_branch_amplitudes(const sv_lattice *lat, const sv_cut *c
     e = cudaMemcpyAsync(out_re_im, d_out, 2 * m * sizeof(double), cudaMemcpyDeviceToHost, s->stream);
   if (e == cudaSuccess) e = cudaStreamSynchronize(s->stream);
   if (e != cudaSuccess) return cuda_fail(e, "sv_branch_amplitudes");
+  return SV_OK;
+}
+
+extern "C" sv_status sv_set_basis_state(sv_state *s, uint64_t x) {
+  clear_error();
+  if (!s) return fail(SV_ERR_ARG, "sv_set_basis_state: NULL state");
+  if (s->n < 64 && (x >> s->n)) return fail(SV_ERR_ARG, "sv_set_basis_state: x has bits >= n");
+  sv_status st = set_device(s);
+  if (st != SV_OK) return st;
+  const cudaError_t e = svk::launch_basis_state(s->psi, s->n, x, s->stream);
+  if (e != cudaSuccess) { s->broken = true; return cuda_fail(e, "sv_set_basis_state"); }
+  s->fresh = false;
+  s->broken = false;
+  if (s->prof) s->other_launches += 1;
+  return SV_OK;
+}
+
+extern "C" sv_status sv_inner_product(sv_state *a, sv_state *b, double *out_re_im) {
+  clear_error();
+  if (!a || !b || !out_re_im) return fail(SV_ERR_ARG, "sv_inner_product: NULL argument");
+  if (a->n != b->n) return fail(SV_ERR_ARG, "sv_inner_product: states of different sizes");
+  if (a->device != b->device) return fail(SV_ERR_ARG, "sv_inner_product: states on different devices");
+  if (a->broken || b->broken) return fail(SV_ERR_STATE, "state is unusable after an earlier failure");
+  sv_status st = set_device(a);
+  if (st != SV_OK) return st;
+  if ((st = materialize(a)) != SV_OK) return st;
+  if ((st = materialize(b)) != SV_OK) return st;
+  const size_t need = (size_t)(svk::reduce_partials_needed() + 2) * 2 * sizeof(double);
+  if ((st = ensure_device_buffer(&a->d_scratch, &a->d_scratch_cap, need)) != SV_OK) return st;
+  double *partials = static_cast<double *>(a->d_scratch);
+  double *res = partials + 2 * svk::reduce_partials_needed();
+  double h[2] = {0, 0};
+  // b's pending work first (the handles may use different streams)
+  cudaError_t e = b->stream == a->stream ? cudaSuccess : cudaStreamSynchronize(b->stream);
+  if (e == cudaSuccess) e = svk::launch_inner(a->psi, b->psi, a->n, partials, res, a->stream);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(h, res, sizeof(h), cudaMemcpyDeviceToHost, a->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(a->stream);
+  if (e != cudaSuccess) return cuda_fail(e, "sv_inner_product");
+  if (a->prof) {
+    a->d2h += sizeof(h);
+    a->other_launches += a->n < 2 ? 1 : 2;
+  }
+  out_re_im[0] = h[0];
+  out_re_im[1] = h[1];
+  return SV_OK;
+}
+
+extern "C" sv_status sv_amplitudes_by_inner_product(const sv_lattice *lat, int split_layer, const uint64_t *bits,
+                                                    size_t m, const sv_options *opts, double *out_re_im) {
+  clear_error();
+  if (!lat || (m && (!bits || !out_re_im))) return fail(SV_ERR_ARG, "sv_amplitudes_by_inner_product: NULL argument");
+  if (split_layer < 0) return fail(SV_ERR_ARG, "sv_amplitudes_by_inner_product: split_layer must be >= 0");
+  std::vector<sv_gate> g;
+  sv_status st = generate(lat, &g);
+  if (st != SV_OK) return st;
+  const int n = lattice_qubits(lat);
+  for (size_t j = 0; j < m; ++j)
+    if (n < 64 && (bits[j] >> n)) return fail(SV_ERR_ARG, "sv_amplitudes_by_inner_product: bitstring has bits >= n");
+  // U1 = layers 0..split_layer (the H layer included), U2 = the layers after it
+  std::vector<sv_gate> g1, g2;
+  for (const sv_gate &x : g) ((int)x.layer <= split_layer ? g1 : g2).push_back(x);
+  sv_options o;
+  std::memset(&o, 0, sizeof(o));
+  if (opts) o = *opts;
+  Holder A, B;
+  if ((st = sv_create(n, &o, &A.s)) != SV_OK) return st;
+  if ((st = sv_apply_circuit(A.s, g1.data(), g1.size())) != SV_OK) return st;  // |psi> = U1 H|0>
+  if (m == 0) return SV_OK;
+  if ((st = sv_create(n, &o, &B.s)) != SV_OK) return st;
+  for (size_t j = 0; j < m; ++j) {
+    // |phi_x> = U2^dagger |x>;  alpha_x = <phi_x|psi>
+    if ((st = sv_set_basis_state(B.s, bits[j])) != SV_OK) return st;
+    if ((st = sv_apply_circuit_inverse(B.s, g2.data(), g2.size())) != SV_OK) return st;
+    if ((st = sv_inner_product(B.s, A.s, out_re_im + 2 * j)) != SV_OK) return st;
+  }
   return SV_OK;
 }

@@ -170,6 +170,58 @@ __global__ void norm_small_kernel(const float2 *psi, uint64_t count, double *out
   out2[1] = s4;
 }
 
+// <a|b> = sum_i conj(a_i) b_i, level 1: as the norm, 8 products summed in fp32 per
+// chunk (the terms have random phases: the fp32 chunk error is relative to the chunk),
+// chunk sums in fp64.  partials[2k] = real part, partials[2k+1] = imaginary part.
+__global__ void inner_partial_kernel(const float4 *a4, const float4 *b4, uint64_t n4, double *partials) {
+  double sr = 0.0, si = 0.0;
+  const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+  uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x;
+  for (; i + 3 * stride < n4; i += 4 * stride) {
+    float4 a[4], b[4];
+#pragma unroll
+    for (int k = 0; k < 4; ++k) { a[k] = a4[i + k * stride]; b[k] = b4[i + k * stride]; }
+    float cr = 0.f, ci = 0.f;
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+      cr = fmaf(a[k].x, b[k].x, fmaf(a[k].y, b[k].y, fmaf(a[k].z, b[k].z, fmaf(a[k].w, b[k].w, cr))));
+      ci = fmaf(a[k].x, b[k].y, fmaf(-a[k].y, b[k].x, fmaf(a[k].z, b[k].w, fmaf(-a[k].w, b[k].z, ci))));
+    }
+    sr += cr;
+    si += ci;
+  }
+  for (; i < n4; i += stride) {
+    const float4 a = a4[i], b = b4[i];
+    sr += (double)fmaf(a.x, b.x, fmaf(a.y, b.y, fmaf(a.z, b.z, a.w * b.w)));
+    si += (double)fmaf(a.x, b.y, fmaf(-a.y, b.x, fmaf(a.z, b.w, -a.w * b.z)));
+  }
+  __shared__ double rr[kBlock / 32], ri[kBlock / 32];
+  sr = warp_sum(sr);
+  si = warp_sum(si);
+  const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+  if (l == 0) { rr[w] = sr; ri[w] = si; }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double a = 0, b = 0;
+    for (int k = 0; k < kBlock / 32; ++k) { a += rr[k]; b += ri[k]; }
+    partials[2 * blockIdx.x] = a;
+    partials[2 * blockIdx.x + 1] = b;
+  }
+}
+
+// Small states (n = 1): plain loop in one thread.
+__global__ void inner_small_kernel(const float2 *a, const float2 *b, uint64_t count, double *out2) {
+  double sr = 0, si = 0;
+  for (uint64_t i = 0; i < count; ++i) {
+    sr += (double)a[i].x * b[i].x + (double)a[i].y * b[i].y;
+    si += (double)a[i].x * b[i].y - (double)a[i].y * b[i].x;
+  }
+  out2[0] = sr;
+  out2[1] = si;
+}
+
+__global__ void set_one_kernel(float2 *psi, uint64_t x) { psi[x] = make_float2(1.f, 0.f); }
+
 __global__ void gather_kernel(const float2 *psi, const uint64_t *bits, int64_t m, double *out) {
   for (int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; j < m; j += (int64_t)gridDim.x * blockDim.x) {
     const float2 z = psi[bits[j]];
@@ -242,6 +294,27 @@ cudaError_t launch_norm(const float2 *psi, int n, double *partials, double *out2
   if (blocks > (uint64_t)kReduceBlocks) blocks = kReduceBlocks;
   norm_partial_kernel<<<(unsigned)blocks, kBlock, 0, st>>>(reinterpret_cast<const float4 *>(psi), n4, partials);
   norm_final_kernel<<<1, kBlock, 0, st>>>(partials, (int)blocks, out2);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_inner(const float2 *a, const float2 *b, int n, double *partials, double *out2, cudaStream_t st) {
+  if (n < 2) {
+    inner_small_kernel<<<1, 1, 0, st>>>(a, b, 1ull << n, out2);
+    return cudaGetLastError();
+  }
+  const uint64_t n4 = 1ull << (n - 1);
+  uint64_t blocks = (n4 + kBlock - 1) / kBlock;
+  if (blocks > (uint64_t)kReduceBlocks) blocks = kReduceBlocks;
+  inner_partial_kernel<<<(unsigned)blocks, kBlock, 0, st>>>(reinterpret_cast<const float4 *>(a),
+                                                              reinterpret_cast<const float4 *>(b), n4, partials);
+  norm_final_kernel<<<1, kBlock, 0, st>>>(partials, (int)blocks, out2);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_basis_state(float2 *psi, int n, uint64_t x, cudaStream_t st) {
+  cudaError_t e = cudaMemsetAsync(psi, 0, sizeof(float2) << n, st);
+  if (e != cudaSuccess) return e;
+  set_one_kernel<<<1, 1, 0, st>>>(psi, x);
   return cudaGetLastError();
 }
 

@@ -53,4 +53,10 @@ cudaError_t launch_branch_sum(const float2 *A, int nA, const float2 *B, int nB, 
 
 int device_sm_count();
 
+// <a|b> = sum conj(a_i) b_i of two 2^n states: out2 = (re, im), fp64 (partials: 2 *
+// reduce_partials_needed() doubles of scratch).
+cudaError_t launch_inner(const float2 *a, const float2 *b, int n, double *partials, double *out2, cudaStream_t st);
+// The basis state |x>: zero everywhere, 1 at index x.
+cudaError_t launch_basis_state(float2 *psi, int n, uint64_t x, cudaStream_t st);
+
 }  // namespace svk

@@ -55,6 +55,9 @@ sv_status run_plan(sv_state *s, const svp::Plan &P, const svk::DevPlanView &view
                    const svj::Module *jit = nullptr);
 // Plan and run an internal gate list (kinds may include K_PEQ) on the state.
 sv_status apply_gates(sv_state *s, const std::vector<svp::Gate> &g);
+sv_status set_device(sv_state *s);
+// Write |0..0> if the state is still the never-written initial one.
+sv_status materialize(sv_state *s);
 // Fused path: the stage unitaries as split-TF32 operands (see k_fused.cu).
 sv_status build_stage_mats(svp::Plan *P, const std::vector<svp::Gate> &g, int r, bool f16);
 

@@ -93,6 +93,9 @@ def lib():
         'sv_plan': ([c_int, vp, c_size_t, P(sv_options), c_int, P(sv_plan_summary), vp, vp, vp,
                      c_size_t], c_int),
         'sv_jit_check': ([c_int, vp, c_size_t, P(sv_options), c_int, ctypes.c_char_p, c_size_t], c_int),
+        'sv_set_basis_state': ([vp, c_uint64], c_int),
+        'sv_inner_product': ([vp, vp, vp], c_int),
+        'sv_amplitudes_by_inner_product': ([P(sv_lattice), c_int, vp, c_size_t, P(sv_options), vp], c_int),
         'sv_set_profiling': ([vp, c_int], c_int),
         'sv_get_profile': ([vp, P(sv_profile)], c_int),
     }
@@ -276,6 +279,28 @@ def sv_plan(n_qubits, gates, opts=None, fresh_state=True):
                          int(bool(fresh_state)), ctypes.byref(summ), order.ctypes.data,
                          pass_of.ctypes.data, tiles.ctypes.data, tiles.size))
     return summ, order[:n], pass_of[:n], tiles.reshape(-1, 64)[:summ.passes]
+
+
+def sv_set_basis_state(h, x):
+    _check(lib().sv_set_basis_state(h, int(x)))
+
+
+def sv_inner_product(a, b):
+    """<a|b> (complex)."""
+    out = np.zeros(2, dtype=np.float64)
+    _check(lib().sv_inner_product(a, b, out.ctypes.data))
+    return complex(out[0], out[1])
+
+
+def sv_amplitudes_by_inner_product(lat, split_layer, bitstrings, opts=None):
+    """Amplitudes alpha_x = <U2^dagger x | U1 H^n 0> of a lattice circuit cut after split_layer."""
+    bits = np.ascontiguousarray(bitstrings, dtype=np.uint64)
+    out = np.zeros(2 * bits.size, dtype=np.float64)
+    L = lattice(lat)
+    _check(lib().sv_amplitudes_by_inner_product(ctypes.byref(L), int(split_layer), bits.ctypes.data, bits.size,
+                                                ctypes.byref(opts) if opts is not None else None,
+                                                out.ctypes.data))
+    return out[0::2] + 1j * out[1::2]
 
 
 def sv_jit_check(n_qubits, gates, opts=None, fresh_state=True):

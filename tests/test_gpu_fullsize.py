@@ -6,7 +6,9 @@
 size: norm, the Porter-Thomas statistic N * sum p^2 ~ 2, the inverse circuit returning
 |0...0>, and agreement of the plain and tensor-core paths on sampled amplitudes.  42 qubits
 (6x7, depth 10, cut between rows 2 and 3, t = 10): the cut-branch amplitudes against the
-oracle's own split-and-sum (complex128, all 1024 branches on the host cores).
+oracle's own split-and-sum (complex128, all 1024 branches on the host cores).  The
+34-qubit amplitudes by the inner product of a forward and a backward state against the
+forward state's.
 """
 import numpy as np
 import pytest
@@ -73,6 +75,22 @@ def test_34q_depth30_invariants():
         assert abs(a0 - 1) <= 1e-5
     finally:
         sv.sv_destroy(h)
+
+
+def test_34q_amplitudes_by_inner_product_match_full_state():
+    """Task 2 by the inner product on the headline circuit (two 128 GiB states), cut after
+    layer 15, against the forward full state's amplitudes."""
+    lat = inputs.C34
+    n = lat.n_qubits
+    bits = inputs.bitstrings(n, 4, seed=2)
+    h = sv.sv_create(n)
+    try:
+        sv.sv_apply_circuit(h, sv.sv_generate_circuit(lat))
+        full = sv.sv_get_amplitudes(h, bits)
+    finally:
+        sv.sv_destroy(h)
+    got = sv.sv_amplitudes_by_inner_product(lat, 15, bits)
+    assert rel_l2(got, full) <= REL_L2
 
 
 def test_42q_cut_branch_amplitudes_match_oracle():

@@ -331,3 +331,49 @@ def test_many_square_roots_in_one_stage():
             sv.sv_destroy(h)
         assert np.all(np.isfinite(got))
         assert rel_l2(got, want) <= REL_L2, kw
+
+
+@pytest.mark.parametrize('kw', [dict(), dict(jit=1), dict(precision=TC), dict(precision=H16)])
+def test_amplitudes_by_inner_product_match_oracle(kw):
+    """Task 2 by <U2^dagger x | U1 H^n 0>: equals the oracle's full-state amplitudes."""
+    lat = inputs.lattice_for(4, 5, 14, seed=5)
+    n, gates = oracle_gates(lat)
+    want = csim.run(n, gates)
+    bits = inputs.bitstrings(n, 16, seed=2) + [0, (1 << n) - 1]
+    sel = want[np.array(bits, dtype=np.int64)]
+    for split in (0, 6, 14):
+        got = sv.sv_amplitudes_by_inner_product(lat, split, bits, sv.options(**kw))
+        assert rel_l2(got, sel) <= REL_L2, (split, kw)
+
+
+def test_inner_product_and_basis_state():
+    n = 17
+    rng = np.random.default_rng(8)
+    a = (rng.normal(size=1 << n) + 1j * rng.normal(size=1 << n)).astype(np.complex64)
+    b = (rng.normal(size=1 << n) + 1j * rng.normal(size=1 << n)).astype(np.complex64)
+    ha, hb = sv.sv_create(n), sv.sv_create(n)
+    try:
+        sv.sv_load_state(ha, a)
+        sv.sv_load_state(hb, b)
+        want = np.vdot(a.astype(np.complex128), b.astype(np.complex128))
+        got = sv.sv_inner_product(ha, hb)
+        assert abs(got - want) <= 1e-6 * np.linalg.norm(a) * np.linalg.norm(b)
+        self_ip = sv.sv_inner_product(ha, ha)
+        n2, _ = sv.sv_norm(ha)
+        assert abs(self_ip.imag) <= 1e-6 * n2 and abs(self_ip.real - n2) <= 1e-6 * n2
+        sv.sv_set_basis_state(hb, 12345)
+        e = sv.sv_copy_state(hb, n)
+        assert e[12345] == 1 and np.count_nonzero(e) == 1
+        assert sv.sv_inner_product(ha, hb) == pytest.approx(complex(np.conj(a[12345])), rel=1e-6)
+        with pytest.raises(sv.SvError):
+            sv.sv_set_basis_state(hb, 1 << n)
+    finally:
+        sv.sv_destroy(ha)
+        sv.sv_destroy(hb)
+    h3, h4 = sv.sv_create(3), sv.sv_create(4)
+    try:
+        with pytest.raises(sv.SvError):
+            sv.sv_inner_product(h3, h4)
+    finally:
+        sv.sv_destroy(h3)
+        sv.sv_destroy(h4)

@@ -13,6 +13,7 @@ import pytest
 from oracle import circuit as oc
 from oracle import csim
 from oracle import statevec as ov
+from paper_1804_04797_gb300 import inputs
 
 GOLDEN = os.path.join(os.path.dirname(__file__), 'golden')
 X = np.array([[0, 1], [1, 0]], dtype=np.complex128)
@@ -339,3 +340,31 @@ def test_cut_crossing_counts():
     assert sorted(set(g[i][3] for i in cr)) == [2, 6, 10]
     _n, g = oc.generate(4, 7, 0, 10, 0)
     assert len(oc.cut_crossings(g, (1 << 14) - 1)) == 7
+
+
+@pytest.mark.parametrize('rows,cols,depth,split', [(3, 3, 8, 3), (3, 4, 10, 5), (2, 5, 9, 0), (3, 3, 8, 8),
+                                                   (3, 3, 8, 20)])
+def test_inner_product_amplitudes_equal_the_full_state(rows, cols, depth, split):
+    """Task 2 by <U2^dagger x | U1 H^n 0> (cut after any layer, including before every
+    layer but layer 0 and after the last) equals the forward state's amplitude."""
+    lat = inputs.lattice_for(rows, cols, depth, seed=17)
+    n, gates = oc.generate(lat.rows, lat.cols, lat.removed_mask, lat.depth, lat.seed)
+    want = ov.run(n, gates)
+    bits = inputs.bitstrings(n, 12, seed=3) + [0, (1 << n) - 1]
+    got = ov.amplitudes_inner_product(n, gates, split, bits)
+    np.testing.assert_allclose(got, want[np.array(bits)], rtol=0, atol=1e-13)
+
+
+def test_inner_product_detects_a_missing_adjoint():
+    """A planted mistake (U2 applied forward instead of as its adjoint) fails."""
+    lat = inputs.lattice_for(3, 3, 8, seed=17)
+    n, gates = oc.generate(lat.rows, lat.cols, lat.removed_mask, lat.depth, lat.seed)
+    want = ov.run(n, gates)
+    g1 = [g for g in gates if g[3] <= 3]
+    g2 = [g for g in gates if g[3] > 3]
+    psi = ov.run(n, g1)
+    x = 5
+    e = np.zeros(1 << n, dtype=np.complex128)
+    e[x] = 1.0
+    wrong = np.vdot(ov.run(n, g2, e), psi)
+    assert abs(wrong - want[x]) > 1e-3 * abs(want[x])
