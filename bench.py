@@ -213,22 +213,26 @@ def run_batch(args, rank, world):
 
 def run_branch(args, rank, world):
     """The amplitude task: 64 amplitudes of the 42-qubit 6x7 depth-10 circuit by the cut
-    decomposition (t = 10 crossing CZs, 1024 branches, two 31-qubit batched half-states)."""
+    decomposition (t = 10 crossing CZs).  Default: the last layer's 3 crossings are output
+    signs and 2 are implicit, so the halves are 21 + 7 and 21 + 5 qubits and 2^5 terms are
+    summed per amplitude; full_decomposition: two 31-qubit batched half-states, 2^10
+    terms."""
     import torch
     from paper_1804_04797_gb300 import inputs, sv
     torch.cuda.set_device(int(os.environ.get('LOCAL_RANK', '0')))
     lat = inputs.C42
     bits = inputs.bitstrings(lat.n_qubits, 64, seed=2)
     out = {}
-    for name, prec in (('plain', sv.SV_PREC_PLAIN), ('tf32x3', sv.SV_PREC_TF32X3)):
+    for name, prec, full in (('plain', sv.SV_PREC_PLAIN, False), ('tf32x3', sv.SV_PREC_TF32X3, False),
+                             ('plain_full_decomposition', sv.SV_PREC_PLAIN, True)):
         o = sv.options(precision=prec)
         for _ in range(max(1, args.warmup)):
-            sv.sv_branch_amplitudes(lat, inputs.C42_HALF_A, bits, o)
+            sv.sv_branch_amplitudes(lat, inputs.C42_HALF_A, bits, o, full_decomposition=full)
         t0 = time.perf_counter()
         for _ in range(args.steps):
-            amps = sv.sv_branch_amplitudes(lat, inputs.C42_HALF_A, bits, o)
-        out[name] = {'s_per_task': (time.perf_counter() - t0) / args.steps, 'amp0': [amps[0].real, amps[0].imag]}
-    # each half-state: (21 + 10) qubits, 16 GiB; passes read and write it once
+            amps = sv.sv_branch_amplitudes(lat, inputs.C42_HALF_A, bits, o, full_decomposition=full)
+        out[name] = {'s_per_task': (time.perf_counter() - t0) / args.steps, 'amp0': [amps[0].real, amps[0].imag],
+                     'counts': sv.sv_branch_counts(lat, inputs.C42_HALF_A, full)}
     line = {'metric': '42q cut-branch amplitude task, s per 64 amplitudes', 'workload': 'branch42',
             'value': min(v['s_per_task'] for v in out.values()), 'unit': 's/task', 'higher_is_better': False,
             'n_gpus': world, 'steps': args.steps, 'warmup': args.warmup,

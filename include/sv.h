@@ -86,9 +86,12 @@ typedef struct {
   uint64_t seed;
 } sv_lattice;
 
-/* A cut of the qubits into halves A (bits set) and B. */
+/* A cut of the qubits into halves A (bits set) and B.  full_decomposition = 1 expands
+ * every crossing CZ into both product terms (no implicit decomposition, no phase
+ * absorption; the plain reading of Eq. 1). */
 typedef struct {
   uint64_t half_a_mask;
+  int full_decomposition;
 } sv_cut;
 
 typedef struct sv_state sv_state;
@@ -184,12 +187,21 @@ sv_status sv_get_probabilities(sv_state *s, const uint64_t *bits, size_t m, doub
 
 /* alpha_x for m bitstrings of the lattice circuit by the cut decomposition (§2, Fig. 2
  * and Eq. 1): every CZ with one qubit in each half is replaced by its two product terms
- * (P_l on the half-A qubit, Z^l on the half-B qubit); all 2^t branches of both halves run
- * as one batched state (branch bits are extra index bits), and
- * alpha_x = sum_l A_l[x_A] * B_l[x_B] is summed in fp64.  Halves of at most 30 qubits,
- * half bits + t <= 34.  out_re_im: 2m doubles.  opts may be NULL. */
+ * (P_l on one qubit, Z^l on the other); all branches of a half run as one batched state
+ * (branch bits are extra index bits), and alpha_x = sum_l A_l[x_A] * B_l[x_B] is summed
+ * in fp64.  Unless cut->full_decomposition: a crossing CZ after which neither qubit meets
+ * a non-diagonal gate is a sign (-1)^{x_a x_b} of the output (§3: the last layer's CZs
+ * only change phases) and is not expanded; one after which only one qubit stays in its
+ * basis state gets the projector on that qubit, and that half needs no branch bit for it
+ * (§2.1 implicit decomposition: its branch index is the qubit's output bit).  Halves plus
+ * their branch bits of at most 34 qubits.  out_re_im: 2m doubles.  opts may be NULL. */
 sv_status sv_branch_amplitudes(const sv_lattice *lat, const sv_cut *cut, const uint64_t *bits,
                                size_t m, const sv_options *opts, double *out_re_im);
+
+/* The decomposition sv_branch_amplitudes runs for a cut (host only): counts[0] = CZs
+ * crossing the cut, [1] = those absorbed as output signs, [2] = branch bits of half A,
+ * [3] = of half B, [4] = branch bits summed over (2^counts[4] terms per amplitude). */
+sv_status sv_branch_counts(const sv_lattice *lat, const sv_cut *cut, int counts[5]);
 
 /* --- batch ------------------------------------------------------------------------------ */
 

@@ -19,6 +19,12 @@ What each function follows
     two product terms, so alpha_x = sum_l <x_A|A_l> <x_B|B_l> over l in {0,1}^t.
   * norm2 / sum_p2: sum |alpha|^2 and sum |alpha|^4 (Porter-Thomas statistic, §3
     final figure: for chaotic states N * sum p^2 -> 2).
+  * branch_amplitudes_reduced: the same sum with the paper's two savings written out
+    per branch: a crossing CZ after which neither qubit meets a non-diagonal gate only
+    multiplies the output by (-1)^{x_a x_b} (the last layer's CZs change phases only,
+    §3); a crossing CZ after which one qubit q stays a basis state is decomposed
+    implicitly (§2.1, Fig. 4 discussion): the projector goes on q and its branch index
+    equals x_q, so that half needs no sum over it.
   * amplitudes_inner_product: Task 2 by the inner product (§2 "Calculating one or a few
     amplitudes"): U = U2 U1, |psi> = U1 H^n |0>, |phi> = U2^dagger |x>, alpha_x =
     <phi|psi>.
@@ -226,4 +232,69 @@ def amplitudes_inner_product(n, gates, split_layer, bitstrings):
         e[int(x)] = 1.0
         phi = run_adjoint(n, g2, e)
         out[j] = np.vdot(phi, psi)  # conj(phi) . psi
+    return out
+
+
+NON_DIAGONAL = ('H', 'SX', 'SY')
+
+
+def branch_amplitudes_reduced(n, gates, half_a_mask, bitstrings):
+    """alpha_x with absorbed output signs and implicit decompositions (see the module
+    docstring); one pair of half-state runs per branch of the remaining CZs."""
+    in_a = [bool((half_a_mask >> q) & 1) for q in range(n)]
+    last_nd = [-1] * n
+    for i, (kind, q0, _q1, _l) in enumerate(gates):
+        if kind in NON_DIAGONAL:
+            last_nd[q0] = i
+    roles = []  # per crossing CZ: ('full' | 'sign' | 'implicit_a' | 'implicit_b', qa, qb)
+    for i, (kind, q0, q1, _l) in enumerate(gates):
+        if kind == 'CZ' and in_a[q0] != in_a[q1]:
+            qa, qb = (q0, q1) if in_a[q0] else (q1, q0)
+            quiet_a, quiet_b = last_nd[qa] < i, last_nd[qb] < i
+            role = 'sign' if quiet_a and quiet_b else 'implicit_a' if quiet_a else 'implicit_b' if quiet_b \
+                else 'full'
+            roles.append((role, qa, qb))
+    qa_list, qb_list, ga, gb, t = split_halves(n, gates, half_a_mask)
+    full = [j for j, r in enumerate(roles) if r[0] == 'full']
+    out = np.zeros(len(bitstrings), dtype=np.complex128)
+    for k, x in enumerate(bitstrings):
+        x = int(x)
+        sign = 1.0
+        for role, qa, qb in roles:
+            if role == 'sign' and (x >> qa) & 1 and (x >> qb) & 1:
+                sign = -sign
+        xa = _compress(x, qa_list)
+        xb = _compress(x, qb_list)
+        acc = 0.0 + 0.0j
+        for lf in range(1 << len(full)):
+            # branch index of every crossing CZ: summed (full), fixed by x (implicit)
+            def half(side, gl):
+                res = []
+                for g in gl:
+                    if g[0] != 'CUT':
+                        res.append(g)
+                        continue
+                    _k, q, j, layer = g
+                    role, qa, qb = roles[j]
+                    if role == 'sign':
+                        continue
+                    if role == 'full':
+                        lj = (lf >> full.index(j)) & 1
+                        proj_side = 'A'
+                    elif role == 'implicit_a':   # projector on qa, l = x_qa: A drops it
+                        lj = (x >> qa) & 1
+                        proj_side = 'A'
+                    else:                       # projector on qb, l = x_qb: B drops it
+                        lj = (x >> qb) & 1
+                        proj_side = 'B'
+                    if side == proj_side:
+                        if role == 'full':
+                            res.append(('P1' if lj else 'P0', q, -1, layer))
+                    elif lj:
+                        res.append(('Z', q, -1, layer))
+                return res
+            A = run(len(qa_list), half('A', ga))
+            B = run(len(qb_list), half('B', gb))
+            acc += A[xa] * B[xb]
+        out[k] = sign * acc
     return out

@@ -37,72 +37,157 @@ int lattice_qubits(const sv_lattice *lat) {
   return n;
 }
 
+
+// How a cut is decomposed: the half gate lists (branch bits appended as qubits) and, per
+// crossing CZ, its role.
+struct CutPlan {
+  int n = 0, na = 0, nb = 0;
+  int local[64];
+  bool in_a[64];
+  int t = 0;          // crossing CZs
+  int absorbed = 0;   // expanded into an output sign instead
+  int tf = 0;         // branch bits in both halves (summed over)
+  int ta = 0, tb = 0; // branch bits of half A / half B (tf + implicit ones of the other side)
+  std::vector<svp::Gate> ga, gb;
+  // output signs (-1)^{x_a x_b} of absorbed CZs; bits of x fixing implicit branch bits
+  std::vector<std::pair<int, int>> signs;
+  std::vector<std::pair<int, int>> fix_a;  // (branch bit index in A above na + tf, qubit of x)
+  std::vector<std::pair<int, int>> fix_b;
+};
+
+sv_status plan_cut(const sv_lattice *lat, const sv_cut *cut, CutPlan *C) {
+  std::vector<sv_gate> g;
+  sv_status st = generate(lat, &g);
+  if (st != SV_OK) return st;
+  const int n = C->n = lattice_qubits(lat);
+  int &na = C->na, &nb = C->nb;
+  na = nb = 0;
+  for (int q = 0; q < n; ++q) {
+    C->in_a[q] = (cut->half_a_mask >> q) & 1ull;
+    C->local[q] = C->in_a[q] ? na++ : nb++;
+  }
+  if (na < 1 || nb < 1) return fail(SV_ERR_ARG, "sv_branch_amplitudes: both halves need qubits");
+  // last non-diagonal gate of each qubit (H, square roots)
+  std::vector<long> last_nd(n, -1);
+  for (size_t i = 0; i < g.size(); ++i) {
+    const int k = g[i].kind;
+    if (k == SV_H || k == SV_SX || k == SV_SY || k == SV_SXDG || k == SV_SYDG) last_nd[g[i].q0] = (long)i;
+  }
+  // roles: 0 = full (projector on A, Z on B), 1 = absorbed sign, 2 = implicit on A (A's
+  // qubit stays a basis state: no branch bit in A), 3 = implicit on B
+  std::vector<int> role;
+  for (size_t i = 0; i < g.size(); ++i) {
+    const sv_gate &x = g[i];
+    if (x.kind != SV_CZ || C->in_a[x.q0] == C->in_a[x.q1]) continue;
+    const int qa = C->in_a[x.q0] ? x.q0 : x.q1, qb = C->in_a[x.q0] ? x.q1 : x.q0;
+    const bool qa_quiet = last_nd[qa] < (long)i, qb_quiet = last_nd[qb] < (long)i;
+    int r = 0;
+    if (!cut->full_decomposition) r = (qa_quiet && qb_quiet) ? 1 : qa_quiet ? 2 : qb_quiet ? 3 : 0;
+    role.push_back(r);
+  }
+  C->t = (int)role.size();
+  int n_full = 0, n_impl_a = 0, n_impl_b = 0;
+  for (int r : role) {
+    if (r == 0) ++n_full;
+    if (r == 1) ++C->absorbed;
+    if (r == 2) ++n_impl_a;
+    if (r == 3) ++n_impl_b;
+  }
+  C->tf = n_full;
+  C->ta = n_full + n_impl_b;  // A carries the Z^l side of CZs implicit on B
+  C->tb = n_full + n_impl_a;
+  if (na + C->ta > 34 || nb + C->tb > 34)
+    return fail(SV_ERR_ARG, "sv_branch_amplitudes: half qubits + branch bits must be <= 34");
+  // Half gate lists: every qubit, branch bits included, starts with H, so each branch
+  // slice holds its half's state times 2^{-t_half/2}.  Branch bit numbering: the full
+  // ones first (shared order), then the implicit ones of the other side.
+  for (int q = 0; q < na + C->ta; ++q) C->ga.push_back(svp::Gate{svp::K_H, (uint8_t)q, 0});
+  for (int q = 0; q < nb + C->tb; ++q) C->gb.push_back(svp::Gate{svp::K_H, (uint8_t)q, 0});
+  int jf = 0, ja = 0, jb = 0, c = 0;
+  for (const sv_gate &x : g) {
+    if (x.kind == SV_H && x.layer == 0) continue;  // already the leading H layer
+    if (x.kind == SV_CZ && C->in_a[x.q0] != C->in_a[x.q1]) {
+      const int qa = C->in_a[x.q0] ? x.q0 : x.q1, qb = C->in_a[x.q0] ? x.q1 : x.q0;
+      switch (role[c++]) {
+        case 0:  // P_{l} on qa (zero where x_qa != l), Z^{l} on qb (a CZ with the branch bit)
+          C->ga.push_back(svp::Gate{svp::K_PEQ, (uint8_t)C->local[qa], (uint8_t)(na + jf)});
+          C->gb.push_back(svp::Gate{svp::K_CZ, (uint8_t)C->local[qb], (uint8_t)(nb + jf)});
+          ++jf;
+          break;
+        case 1:  // a sign of the output only
+          C->signs.push_back({qa, qb});
+          break;
+        case 2: {  // projector on qa, implicit: l = x_qa; B keeps Z^{l} with its own bit
+          const int bit = n_full + ja++;
+          C->gb.push_back(svp::Gate{svp::K_CZ, (uint8_t)C->local[qb], (uint8_t)(nb + bit)});
+          C->fix_b.push_back({bit, qa});
+          break;
+        }
+        default: {  // projector on qb, implicit: l = x_qb; A keeps Z^{l}
+          const int bit = n_full + jb++;
+          C->ga.push_back(svp::Gate{svp::K_CZ, (uint8_t)C->local[qa], (uint8_t)(na + bit)});
+          C->fix_a.push_back({bit, qb});
+          break;
+        }
+      }
+      continue;
+    }
+    std::vector<svp::Gate> &dst = C->in_a[x.q0] ? C->ga : C->gb;
+    dst.push_back(svp::Gate{x.kind, (uint8_t)C->local[x.q0], (uint8_t)(x.kind == SV_CZ ? C->local[x.q1] : 0)});
+  }
+  return SV_OK;
+}
+
 }  // namespace
+
+extern "C" sv_status sv_branch_counts(const sv_lattice *lat, const sv_cut *cut, int counts[5]) {
+  clear_error();
+  if (!lat || !cut || !counts) return fail(SV_ERR_ARG, "sv_branch_counts: NULL argument");
+  CutPlan C;
+  sv_status st = plan_cut(lat, cut, &C);
+  if (st != SV_OK) return st;
+  counts[0] = C.t;
+  counts[1] = C.absorbed;
+  counts[2] = C.ta;
+  counts[3] = C.tb;
+  counts[4] = C.tf;
+  return SV_OK;
+}
 
 extern "C" sv_status sv_branch_amplitudes(const sv_lattice *lat, const sv_cut *cut, const uint64_t *bits,
                                           size_t m, const sv_options *opts, double *out_re_im) {
   clear_error();
   if (!lat || !cut || (m && (!bits || !out_re_im)))
     return fail(SV_ERR_ARG, "sv_branch_amplitudes: NULL argument");
-  std::vector<sv_gate> g;
-  sv_status st = generate(lat, &g);
+  CutPlan C;
+  sv_status st = plan_cut(lat, cut, &C);
   if (st != SV_OK) return st;
-  const int n = lattice_qubits(lat);
-  // split the qubits: local numbering ascending within each half
-  int local[64], na = 0, nb = 0;
-  bool in_a[64];
-  for (int q = 0; q < n; ++q) {
-    in_a[q] = (cut->half_a_mask >> q) & 1ull;
-    local[q] = in_a[q] ? na++ : nb++;
-  }
-  if (na < 1 || nb < 1) return fail(SV_ERR_ARG, "sv_branch_amplitudes: both halves need qubits");
+  const int n = C.n, na = C.na, nb = C.nb;
   for (size_t j = 0; j < m; ++j)
     if (n < 64 && (bits[j] >> n)) return fail(SV_ERR_ARG, "sv_branch_amplitudes: bitstring has bits >= n");
-  // count the crossing CZs
-  int t = 0;
-  for (const sv_gate &x : g)
-    if (x.kind == SV_CZ && in_a[x.q0] != in_a[x.q1]) ++t;
-  if (na + t > 34 || nb + t > 34)
-    return fail(SV_ERR_ARG, "sv_branch_amplitudes: half qubits + crossing CZs must be <= 34");
-  // Half gate lists on (n_half + t) qubits: branch bit j is qubit n_half + j.  Every
-  // qubit (branch bits included) starts with H, so each branch slice holds its half's
-  // state times 2^{-t/2}; the sum is rescaled by 2^t.  Crossing CZ j becomes the
-  // projector P_{l_j} on the half-A qubit (zero where x_a != l_j) and Z^{l_j} on the
-  // half-B qubit (a CZ with branch bit j).
-  std::vector<svp::Gate> ga, gb;
-  for (int q = 0; q < na + t; ++q) ga.push_back(svp::Gate{svp::K_H, (uint8_t)q, 0});
-  for (int q = 0; q < nb + t; ++q) gb.push_back(svp::Gate{svp::K_H, (uint8_t)q, 0});
-  int j = 0;
-  for (const sv_gate &x : g) {
-    if (x.kind == SV_H && x.layer == 0) continue;  // already the leading H layer
-    if (x.kind == SV_CZ && in_a[x.q0] != in_a[x.q1]) {
-      const int qa = in_a[x.q0] ? x.q0 : x.q1, qb = in_a[x.q0] ? x.q1 : x.q0;
-      ga.push_back(svp::Gate{svp::K_PEQ, (uint8_t)local[qa], (uint8_t)(na + j)});
-      gb.push_back(svp::Gate{svp::K_CZ, (uint8_t)local[qb], (uint8_t)(nb + j)});
-      ++j;
-      continue;
-    }
-    std::vector<svp::Gate> &dst = in_a[x.q0] ? ga : gb;
-    dst.push_back(svp::Gate{x.kind, (uint8_t)local[x.q0], (uint8_t)(x.kind == SV_CZ ? local[x.q1] : 0)});
-  }
   sv_options o;
   std::memset(&o, 0, sizeof(o));
   if (opts) o = *opts;
   Holder A, B;
-  if ((st = sv_create(na + t, &o, &A.s)) != SV_OK) return st;
-  if ((st = sv_create(nb + t, &o, &B.s)) != SV_OK) return st;
-  if ((st = apply_gates(A.s, ga)) != SV_OK) return st;
-  if ((st = apply_gates(B.s, gb)) != SV_OK) return st;
+  if ((st = sv_create(na + C.ta, &o, &A.s)) != SV_OK) return st;
+  if ((st = sv_create(nb + C.tb, &o, &B.s)) != SV_OK) return st;
+  if ((st = apply_gates(A.s, C.ga)) != SV_OK) return st;
+  if ((st = apply_gates(B.s, C.gb)) != SV_OK) return st;
   if (m == 0) return SV_OK;
-  // bitstring -> half indices
+  // bitstring -> half indices, with the implicit branch bits fixed by the output bits
   std::vector<uint64_t> xab(2 * m);
+  std::vector<double> sign(m, 1.0);
   for (size_t k = 0; k < m; ++k) {
     uint64_t xa = 0, xb = 0;
     for (int q = 0; q < n; ++q) {
       const uint64_t b = (bits[k] >> q) & 1ull;
-      if (in_a[q]) xa |= b << local[q];
-      else xb |= b << local[q];
+      if (C.in_a[q]) xa |= b << C.local[q];
+      else xb |= b << C.local[q];
     }
+    for (const auto &f : C.fix_a) xa |= ((bits[k] >> f.second) & 1ull) << (na + f.first);
+    for (const auto &f : C.fix_b) xb |= ((bits[k] >> f.second) & 1ull) << (nb + f.first);
+    for (const auto &sg : C.signs)
+      if (((bits[k] >> sg.first) & 1ull) && ((bits[k] >> sg.second) & 1ull)) sign[k] = -sign[k];
     xab[k] = xa;
     xab[m + k] = xb;
   }
@@ -112,16 +197,21 @@ extern "C" sv_status sv_branch_amplitudes(const sv_lattice *lat, const sv_cut *c
   uint64_t *d_x = static_cast<uint64_t *>(s->d_scratch);
   double *d_out = reinterpret_cast<double *>(static_cast<char *>(s->d_scratch) +
                                              ((2 * m * sizeof(uint64_t) + 255) & ~(size_t)255));
+  // each slice carries 2^{-t_half/2}: the sum is rescaled by 2^{(ta + tb)/2}
+  const double scale = std::pow(2.0, 0.5 * (C.ta + C.tb));
   cudaError_t e = cudaStreamSynchronize(B.s->stream);
   if (e == cudaSuccess)
     e = cudaMemcpyAsync(d_x, xab.data(), 2 * m * sizeof(uint64_t), cudaMemcpyHostToDevice, s->stream);
   if (e == cudaSuccess)
-    e = svk::launch_branch_sum(A.s->psi, na, B.s->psi, nb, t, d_x, d_x + m, (int)m, std::ldexp(1.0, t), d_out,
-                               s->stream);
+    e = svk::launch_branch_sum(A.s->psi, na, B.s->psi, nb, C.tf, d_x, d_x + m, (int)m, scale, d_out, s->stream);
   if (e == cudaSuccess)
     e = cudaMemcpyAsync(out_re_im, d_out, 2 * m * sizeof(double), cudaMemcpyDeviceToHost, s->stream);
   if (e == cudaSuccess) e = cudaStreamSynchronize(s->stream);
   if (e != cudaSuccess) return cuda_fail(e, "sv_branch_amplitudes");
+  for (size_t k = 0; k < m; ++k) {
+    out_re_im[2 * k] *= sign[k];
+    out_re_im[2 * k + 1] *= sign[k];
+  }
   return SV_OK;
 }
 

@@ -39,7 +39,7 @@ class sv_lattice(ctypes.Structure):
 
 
 class sv_cut(ctypes.Structure):
-    _fields_ = [('half_a_mask', c_uint64)]
+    _fields_ = [('half_a_mask', c_uint64), ('full_decomposition', c_int)]
 
 
 class sv_plan_summary(ctypes.Structure):
@@ -85,6 +85,7 @@ def lib():
         'sv_get_probabilities': ([vp, vp, c_size_t, vp], c_int),
         'sv_norm': ([vp, P(c_double), P(c_double)], c_int),
         'sv_branch_amplitudes': ([P(sv_lattice), P(sv_cut), vp, c_size_t, P(sv_options), vp], c_int),
+        'sv_branch_counts': ([P(sv_lattice), P(sv_cut), vp], c_int),
         'sv_apply_batch': ([vp, c_size_t, P(sv_options), vp], c_int),
         'sv_batch_amplitudes': ([c_size_t, vp, c_size_t, vp], c_int),
         'sv_batch_free': ([], c_int),
@@ -226,14 +227,23 @@ def sv_norm(h):
     return a.value, b.value
 
 
-def sv_branch_amplitudes(lat, half_a_mask, bits, opts=None):
+def sv_branch_amplitudes(lat, half_a_mask, bits, opts=None, full_decomposition=False):
     L = lat if isinstance(lat, sv_lattice) else lattice(lat)
-    cut = sv_cut(half_a_mask)
+    cut = sv_cut(half_a_mask, int(bool(full_decomposition)))
     b = np.ascontiguousarray(bits, dtype=np.uint64)
     out = np.zeros(2 * b.size, dtype=np.float64)
     _check(lib().sv_branch_amplitudes(ctypes.byref(L), ctypes.byref(cut), b.ctypes.data, b.size,
                                       ctypes.byref(opts) if opts is not None else None, out.ctypes.data))
     return out.view(np.complex128)
+
+
+def sv_branch_counts(lat, half_a_mask, full_decomposition=False):
+    """(crossing CZs, absorbed signs, branch bits of A, of B, summed branch bits)."""
+    L = lat if isinstance(lat, sv_lattice) else lattice(lat)
+    cut = sv_cut(half_a_mask, int(bool(full_decomposition)))
+    out = np.zeros(5, dtype=np.int32)
+    _check(lib().sv_branch_counts(ctypes.byref(L), ctypes.byref(cut), out.ctypes.data))
+    return tuple(int(v) for v in out)
 
 
 def sv_apply_batch(lats, opts=None):

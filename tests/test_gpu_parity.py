@@ -254,9 +254,11 @@ def test_branch_amplitudes_small_cut_match_oracle():
     want_full = csim.run(n, gates)[np.array(bits, dtype=np.int64)]
     want_branch = csim.branch_amplitudes(n, gates, half_a, bits)
     assert rel_l2(want_branch, want_full) < 1e-12
-    for kw in (dict(), dict(precision=TC), dict(precision=H16)):
-        got = sv.sv_branch_amplitudes(lat, half_a, bits, sv.options(**kw))
-        assert rel_l2(got, want_full) <= REL_L2, kw
+    assert rel_l2(ov.branch_amplitudes_reduced(n, gates, half_a, bits), want_full) < 1e-12
+    for kw in (dict(), dict(precision=TC), dict(precision=H16), dict(jit=1)):
+        for full in (False, True):
+            got = sv.sv_branch_amplitudes(lat, half_a, bits, sv.options(**kw), full_decomposition=full)
+            assert rel_l2(got, want_full) <= REL_L2, (kw, full)
 
 
 def test_branch_amplitudes_28q_check_against_full_state():
@@ -266,6 +268,8 @@ def test_branch_amplitudes_28q_check_against_full_state():
     n, gates = oracle_gates(lat)
     bits = inputs.bitstrings(n, 64, seed=2)
     got = sv.sv_branch_amplitudes(lat, inputs.C28_HALF_A, bits)
+    got_full = sv.sv_branch_amplitudes(lat, inputs.C28_HALF_A, bits, full_decomposition=True)
+    assert rel_l2(got_full, got) <= REL_L2
     h = sv.sv_create(n)
     try:
         sv.sv_apply_circuit(h, sv.sv_generate_circuit(lat))

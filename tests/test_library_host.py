@@ -159,3 +159,39 @@ def test_plan_kernels_compile_without_a_device(case):
         if 'libnvrtc not found' in str(e):
             pytest.skip('NVRTC not installed')
         raise
+
+
+@pytest.mark.parametrize('lat,half_a', [(inputs.C42, inputs.C42_HALF_A), (inputs.C28, inputs.C28_HALF_A),
+                                        (inputs.lattice_for(4, 4, 9, seed=31), (1 << 8) - 1)])
+def test_branch_decomposition_counts(lat, half_a):
+    """The cut plan's absorbed signs and implicit decompositions, recounted from the
+    oracle's own gate list."""
+    n, gates = oc.generate(lat.rows, lat.cols, lat.removed_mask, lat.depth, lat.seed)
+    in_a = [bool((half_a >> q) & 1) for q in range(n)]
+    last_nd = [-1] * n
+    for i, (k, q0, _q1, _l) in enumerate(gates):
+        if k in ('H', 'SX', 'SY'):
+            last_nd[q0] = i
+    t = absorbed = full = impl_a = impl_b = 0
+    for i, (k, q0, q1, _l) in enumerate(gates):
+        if k != 'CZ' or in_a[q0] == in_a[q1]:
+            continue
+        t += 1
+        qa, qb = (q0, q1) if in_a[q0] else (q1, q0)
+        qa_q, qb_q = last_nd[qa] < i, last_nd[qb] < i
+        if qa_q and qb_q:
+            absorbed += 1
+        elif qa_q:
+            impl_a += 1
+        elif qb_q:
+            impl_b += 1
+        else:
+            full += 1
+    assert sv.sv_branch_counts(lat, half_a) == (t, absorbed, full + impl_b, full + impl_a, full)
+    assert sv.sv_branch_counts(lat, half_a, full_decomposition=True) == (t, 0, t, t, t)
+
+
+def test_42q_decomposition_sizes():
+    """42 qubits cut 2|3: the last layer's 3 crossing CZs become output signs, so the
+    halves hold 21 + 7 and 21 + 5 qubits instead of 21 + 10 each."""
+    assert sv.sv_branch_counts(inputs.C42, inputs.C42_HALF_A) == (10, 3, 7, 5, 5)

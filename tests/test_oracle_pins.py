@@ -368,3 +368,36 @@ def test_inner_product_detects_a_missing_adjoint():
     e[x] = 1.0
     wrong = np.vdot(ov.run(n, g2, e), psi)
     assert abs(wrong - want[x]) > 1e-3 * abs(want[x])
+
+
+@pytest.mark.parametrize('rows,cols,depth,cut_rows', [(4, 4, 9, 2), (3, 4, 12, 1), (4, 3, 10, 2)])
+def test_reduced_branch_sum_equals_the_full_state(rows, cols, depth, cut_rows):
+    """Absorbed output signs and implicit decompositions give the exact amplitudes."""
+    lat = inputs.lattice_for(rows, cols, depth, seed=31)
+    n, gates = oc.generate(lat.rows, lat.cols, lat.removed_mask, lat.depth, lat.seed)
+    half_a = (1 << (cut_rows * cols)) - 1
+    bits = inputs.bitstrings(n, 10, seed=4) + [0, (1 << n) - 1]
+    want = ov.run(n, gates)[np.array(bits)]
+    np.testing.assert_allclose(ov.branch_amplitudes_reduced(n, gates, half_a, bits), want, rtol=0, atol=1e-12)
+    np.testing.assert_allclose(ov.branch_amplitudes(n, gates, half_a, bits), want, rtol=0, atol=1e-12)
+
+
+def test_implicit_branch_slices_vanish():
+    """§2.1: after the last non-diagonal gate on the projector's qubit q, the branch with
+    l != x_q is identically zero -- the fact implicit decomposition rests on."""
+    lat = inputs.lattice_for(4, 4, 9, seed=31)
+    n, gates = oc.generate(lat.rows, lat.cols, lat.removed_mask, lat.depth, lat.seed)
+    half_a = (1 << 8) - 1
+    qa, qb, ga, gb, t = ov.split_halves(n, gates, half_a)
+    last_nd = [-1] * len(qa)
+    for i, g in enumerate(ga):
+        if g[0] in ov.NON_DIAGONAL:
+            last_nd[g[1]] = i
+    quiet = [(i, g) for i, g in enumerate(ga) if g[0] == 'CUT' and last_nd[g[1]] < i]
+    assert quiet, 'the case needs a quiet crossing'
+    for _i, (_k, q, j, _layer) in quiet:
+        for l in range(1 << t):
+            A = ov.run(len(qa), ov._branch_gates(ga, l, 'A'))
+            lj = (l >> j) & 1
+            idx = np.arange(A.size)
+            assert np.all(A[((idx >> q) & 1) != lj] == 0)
