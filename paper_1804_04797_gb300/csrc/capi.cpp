@@ -46,6 +46,8 @@ sv_status ensure_device_buffer(void **buf, size_t *cap, size_t need) {
 
 svp::Options plan_options(const sv_options &o) {
   svp::Options p;
+  // the interpreting and tensor-core kernels take up to 13-qubit tiles; 14 only with
+  // tile_bits = 14 or for plan-specialised kernels (apply_gates)
   p.m = o.tile_bits > 0 ? o.tile_bits : 13;
   p.c = o.low_bits > 0 ? o.low_bits : 4;
   p.fused = o.precision == SV_PREC_TF32X3 || o.precision == SV_PREC_F16X3;
@@ -62,7 +64,10 @@ sv_status check_options(const sv_options &o) {
     return fail(SV_ERR_ARG, "options: unknown precision mode");
   if (o.fuse_k < 0 || o.fuse_k > svp::kMaxReg) return fail(SV_ERR_ARG, "options: fuse_k must be 0 or 1..5");
   if (o.tile_bits != 0 && (o.tile_bits < 6 || o.tile_bits > svp::kMaxTileBits))
-    return fail(SV_ERR_ARG, "options: tile_bits must be 0 or 6..13");
+    return fail(SV_ERR_ARG, "options: tile_bits must be 0 or 6..14");
+  const bool fused = o.precision == SV_PREC_TF32X3 || o.precision == SV_PREC_F16X3;
+  if (o.tile_bits == 14 && (fused || o.jit < 0))
+    return fail(SV_ERR_ARG, "options: 14-qubit tiles need the plain path's plan-specialised kernels");
   if (o.low_bits < 0 || o.low_bits > 13) return fail(SV_ERR_ARG, "options: low_bits must be 0..13");
   if (o.jit < -1 || o.jit > 1) return fail(SV_ERR_ARG, "options: jit must be -1, 0 or 1");
   const int m = o.tile_bits > 0 ? o.tile_bits : 13;
@@ -268,19 +273,30 @@ sv_status apply_gates(sv_state *s, const std::vector<svp::Gate> &g) {
     po.rk = svk::tile_pass_register_slots();
     po.r = std::min(po.r, po.rk);
   }
+  // plain path: kernels compiled for this plan where they pay (or where asked for); they
+  // also take 14-qubit tiles (tile_bits = 14: one pass fewer on 34 qubits, but one CTA
+  // per SM, measured 7 % slower than 13-qubit tiles)
+  const bool want_jit = !po.fused && s->opts.jit >= 0 &&
+                        (s->opts.jit == 1 || s->n >= kJitMinQubits || std::min(po.m, s->n) > svk::tile_pass_max_bits());
   if (!svp::build_plan(s->n, g, po, s->fresh, &P, &err)) return fail(SV_ERR_ARG, err ? err : "planning failed");
+  const svj::Module *jit = nullptr;
+  if (want_jit) {
+    std::string jerr;
+    jit = svj::get_module(P, po.rk, &jerr);
+    if (!jit && s->opts.jit == 1) return fail(SV_ERR_CUDA, jerr.c_str());
+    if (!jit && std::min(po.m, s->n) > svk::tile_pass_max_bits()) {
+      // no compiler: the interpreting kernel, on tiles it takes
+      po.m = svk::tile_pass_max_bits();
+      P = svp::Plan();
+      if (!svp::build_plan(s->n, g, po, s->fresh, &P, &err))
+        return fail(SV_ERR_ARG, err ? err : "planning failed");
+    }
+  }
   const bool f16 = s->opts.precision == SV_PREC_F16X3;
   if (po.fused && (st = build_stage_mats(&P, g, std::min(po.r, std::min(po.m, s->n)), f16)) != SV_OK) return st;
   if (po.fused)
     for (const svp::DevPass &dp : P.passes)
       if (dp.stage_count > 256) return fail(SV_ERR_ARG, "fused path: more than 256 stages in one pass");
-  // plain path: kernels compiled for this plan where they pay (or where asked for)
-  const svj::Module *jit = nullptr;
-  if (!po.fused && s->opts.jit >= 0 && (s->opts.jit == 1 || s->n >= kJitMinQubits)) {
-    std::string jerr;
-    jit = svj::get_module(P, po.rk, &jerr);
-    if (!jit && s->opts.jit == 1) return fail(SV_ERR_CUDA, jerr.c_str());
-  }
   svk::DevPlanView view;
   if ((st = upload_plan(s, P, &view)) != SV_OK) return st;
   if ((st = run_plan(s, P, view, po.fused, f16, jit)) != SV_OK) return st;

@@ -96,7 +96,7 @@ sv_status build_batch(const sv_lattice *circs, size_t count, int m_req, Batch *B
     if ((st = sv_generate_circuit(&circs[i], g.data(), ng, &ng)) != SV_OK) return st;
     if ((st = convert_gates(n, g.data(), ng, false, &gates[i])) != SV_OK) return st;
   }
-  const int m = std::min(m_req, n_min);
+  const int m = std::min(std::min(m_req, svk::tile_pass_max_bits()), n_min);
   B->m = m;
   svp::Options po;
   po.m = m;

@@ -138,7 +138,7 @@ cudaError_t launch_batch(float2 *states, const DevPlanView &plan, const BatchCP 
                          unsigned long long wait_ns, int max_grid) {
   static bool configured = false;
   static int per_sm = 1;
-  const size_t smem = sizeof(float2) << svp::kMaxTileBits;
+  const size_t smem = sizeof(float2) << 13;  // tiles of <= 13 qubits (capi_batch)
   if (!configured) {
     cudaError_t e = cudaFuncSetAttribute(batch_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;

@@ -22,7 +22,8 @@ namespace {
 
 using namespace tpk;
 
-constexpr int kThreads = 1 << (svp::kMaxTileBits - 1 - kPR);  // one group of 2^kPR pairs per thread
+constexpr int kMaxBits = 13;  // tiles of this kernel: 64 KiB, two CTAs per SM
+constexpr int kThreads = 1 << (kMaxBits - 1 - kPR);  // one group of 2^kPR pairs per thread
 
 __global__ void __launch_bounds__(kThreads, 2)
 tile_pass_kernel(float2 *__restrict__ psi, DevPlanView plan, int pass_index, uint64_t num_tiles) {
@@ -38,22 +39,23 @@ tile_pass_kernel(float2 *__restrict__ psi, DevPlanView plan, int pass_index, uin
   sweep_tiles(psi, plan, P, chunk_off, reinterpret_cast<float4 *>(smem_raw), blockIdx.x, gridDim.x, num_tiles);
 }
 
-int g_tile_blocks_per_sm[svp::kMaxTileBits + 1] = {};  // resident CTAs per SM, by tile size
+int g_tile_blocks_per_sm[kMaxBits + 1] = {};  // resident CTAs per SM, by tile size
 
 }  // namespace
 
 int tile_pass_register_slots() { return kPR; }
+int tile_pass_max_bits() { return kMaxBits; }
 
 cudaError_t launch_tile_pass(float2 *psi, int n, const DevPlanView &plan, int pass_index,
                              const svp::DevPass &hp, cudaStream_t st) {
   const int m = hp.m;
-  if (!(hp.flags & svp::PF_PACKED) || m < kPR + 1 || m > svp::kMaxTileBits || hp.c < 1 || m - hp.c > 10)
+  if (!(hp.flags & svp::PF_PACKED) || m < kPR + 1 || m > kMaxBits || hp.c < 1 || m - hp.c > 10)
     return cudaErrorInvalidValue;
   const size_t smem = sizeof(float2) << m;
   static bool configured = false;
   if (!configured) {
     cudaError_t e = cudaFuncSetAttribute(tile_pass_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)(sizeof(float2) << svp::kMaxTileBits));
+                                         (int)(sizeof(float2) << kMaxBits));
     if (e != cudaSuccess) return e;
     configured = true;
   }

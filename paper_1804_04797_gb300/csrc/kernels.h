@@ -23,6 +23,9 @@ cudaError_t launch_tile_pass(float2 *psi, int n, const DevPlanView &plan, int pa
                              const svp::DevPass &host_pass, cudaStream_t st);
 // Register slots besides the pack bit of the packed plain kernel (the planner's rk).
 int tile_pass_register_slots();
+// Largest tile (qubits) of the interpreting plain kernel; the plan-specialised kernels
+// take up to svp::kMaxTileBits.
+int tile_pass_max_bits();
 
 // K4 fused tensor-core tile pass (tcgen05, split-TF32).
 // tile_bits 12 or 13; f16: F16x3 operands, else TF32x3

@@ -91,13 +91,13 @@ constexpr int kGroupEntries = 56;
 constexpr int kRegEntry = 48;
 static_assert(sizeof(DevOp) == 32, "DevOp layout");
 
-constexpr int kMaxTileBits = 13;
+constexpr int kMaxTileBits = 14;  // the plan-specialised kernels; the others take <= 13
 constexpr int kMaxReg = 5;
 
 struct DevStage {
   uint8_t r;                   // register bits in use (<= kMaxReg); the rest are padding
   uint8_t rbit[kMaxReg];       // tile-local bit of register bit j (all distinct, padded)
-  uint8_t nonr[kMaxTileBits - 1];  // tile-local bits of the group index, lane bits first
+  uint8_t nonr[12];            // tile-local bits of the group index, lane bits first
   uint8_t halves;              // packed plan: factors 1/2 left to apply at the stage's end
   uint8_t diag_only;           // no inner gates: nothing for the tensor cores
   uint32_t op_begin;           // into the plan's op array
@@ -123,7 +123,6 @@ struct DevPass {
   uint16_t stage_count;
   uint32_t stage_begin;       // into the plan's stage array
   float init_amp;             // uniform amplitude for PF_INIT_UNIFORM
-  uint32_t pad;
 };
 static_assert(sizeof(DevPass) == 96, "DevPass layout");
 

@@ -352,7 +352,7 @@ __device__ __forceinline__ uint32_t pack_phys(uint32_t k) { return k ^ (((k >> 3
 // Byte offset of group g's first pair.
 __device__ __forceinline__ uint32_t group_base(const DevPlanView &plan, uint32_t si, int g) {
   const svp::DevGroupEntry *t = plan.gtab + svp::kGroupEntries * si;
-  return t[g & 15].L ^ t[16 + ((g >> 4) & 15)].L;
+  return t[g & 15].L ^ t[16 + ((g >> 4) & 15)].L ^ t[32 + ((g >> 8) & 15)].L;
 }
 
 __device__ __forceinline__ void load_group(const float4 *tile, const DevPlanView &plan, uint32_t si, uint32_t a0,

@@ -45,7 +45,7 @@ def run_gpu(lat, **kw):
 
 TC = sv.SV_PREC_TF32X3
 H16 = sv.SV_PREC_F16X3
-MODES = [dict(), dict(tile_bits=10, low_bits=4, fuse_k=5), dict(tile_bits=8, low_bits=2, fuse_k=3),
+MODES = [dict(), dict(tile_bits=14), dict(tile_bits=10, low_bits=4, fuse_k=5), dict(tile_bits=8, low_bits=2, fuse_k=3),
          dict(tile_bits=12, low_bits=5, fuse_k=4), dict(precision=sv.SV_PREC_PERGATE),
          dict(precision=TC), dict(precision=TC, tile_bits=12), dict(precision=TC, tile_bits=12, low_bits=3),
          dict(precision=H16), dict(precision=H16, tile_bits=12),
@@ -189,14 +189,15 @@ def test_inverse_circuit_returns_to_zero_state(prec):
 @pytest.mark.parametrize('lat,gl', [(inputs.lattice_for(4, 5, 18, seed=11), None),
                                     (None, _random_gate_list(19, 150, seed=77))])
 def test_plan_kernels_bitwise_equal_to_interpreter(lat, gl):
-    """The kernels compiled for a plan run the interpreter's arithmetic op for op."""
+    """The kernels compiled for a plan run the interpreter's arithmetic op for op (the same
+    plan: 13-qubit tiles, the largest the interpreter takes)."""
     if lat is not None:
         n, g = lat.n_qubits, sv.sv_generate_circuit(lat)
     else:
         n, g = 19, _to_lib(gl)
     out = {}
     for jit in (-1, 1):
-        h = sv.sv_create(n, sv.options(jit=jit))
+        h = sv.sv_create(n, sv.options(jit=jit, tile_bits=13))
         try:
             sv.sv_set_profiling(h, True)
             sv.sv_apply_circuit(h, g)

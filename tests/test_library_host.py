@@ -121,7 +121,13 @@ def test_planner_rejects_invalid_gates():
     with pytest.raises(sv.SvError):
         sv.sv_plan(8, bad)
     with pytest.raises(sv.SvError):
-        sv.sv_plan(8, sv.gates_from_tuples([(0, 1, 0, 0)]), sv.options(tile_bits=14))
+        sv.sv_plan(8, sv.gates_from_tuples([(0, 1, 0, 0)]), sv.options(tile_bits=15))
+    # 14-qubit tiles only for the plan-specialised plain kernels
+    with pytest.raises(sv.SvError):
+        sv.sv_plan(16, sv.gates_from_tuples([(0, 1, 0, 0)]), sv.options(tile_bits=14, jit=-1))
+    with pytest.raises(sv.SvError):
+        sv.sv_plan(16, sv.gates_from_tuples([(0, 1, 0, 0)]), sv.options(tile_bits=14, precision=sv.SV_PREC_F16X3))
+    sv.sv_plan(16, sv.gates_from_tuples([(0, 1, 0, 0)]), sv.options(tile_bits=14))
 
 
 def _all_kind_gates(n, count, seed):
