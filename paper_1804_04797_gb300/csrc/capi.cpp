@@ -278,15 +278,21 @@ sv_status apply_gates(sv_state *s, const std::vector<svp::Gate> &g) {
   // per SM, measured 7 % slower than 13-qubit tiles)
   const bool want_jit = !po.fused && s->opts.jit >= 0 &&
                         (s->opts.jit == 1 || s->n >= kJitMinQubits || std::min(po.m, s->n) > svk::tile_pass_max_bits());
+  if (want_jit) {
+    po.rk = svj::register_slots();
+    po.r = std::min(po.r, po.rk);
+  }
   if (!svp::build_plan(s->n, g, po, s->fresh, &P, &err)) return fail(SV_ERR_ARG, err ? err : "planning failed");
   const svj::Module *jit = nullptr;
   if (want_jit) {
     std::string jerr;
     jit = svj::get_module(P, po.rk, &jerr);
     if (!jit && s->opts.jit == 1) return fail(SV_ERR_CUDA, jerr.c_str());
-    if (!jit && std::min(po.m, s->n) > svk::tile_pass_max_bits()) {
-      // no compiler: the interpreting kernel, on tiles it takes
-      po.m = svk::tile_pass_max_bits();
+    if (!jit) {
+      // no compiler: the interpreting kernel, with its register width, on tiles it takes
+      po.m = std::min(po.m, svk::tile_pass_max_bits());
+      po.rk = svk::tile_pass_register_slots();
+      po.r = std::min(plan_options(s->opts).r, po.rk);
       P = svp::Plan();
       if (!svp::build_plan(s->n, g, po, s->fresh, &P, &err))
         return fail(SV_ERR_ARG, err ? err : "planning failed");
@@ -571,7 +577,7 @@ sv_status sv_jit_check(int n_qubits, const sv_gate *gates, size_t n_gates, const
   svp::Options po = plan_options(o);
   po.fused = false;
   po.pack = true;
-  po.rk = svk::tile_pass_register_slots();
+  po.rk = svj::register_slots();
   po.r = std::min(po.r, po.rk);
   svp::Plan P;
   const char *err = nullptr;

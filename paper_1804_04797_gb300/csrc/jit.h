@@ -18,6 +18,13 @@
 
 namespace svj {
 
+// Register slots besides the pack bit of the plan-specialised kernels (plans for them
+// are built with this rk).  Measured on 34 qubits: 4 slots 0.75 s, 3 slots 0.83 s; a
+// second tile buffer with the next tile's read in flight was slower at either width
+// (0.87 s, 0.96 s): it halves the resident CTAs, and the stages need every warp.
+constexpr int kRegisterSlots = 4;
+int register_slots();
+
 // CUDA source of the kernel ("sv_pass") of one pass of a packed plan.  kpr: register
 // slots besides the pack bit (the plan's rk).
 std::string pass_source(const svp::Plan &P, int kpr, int pass);

@@ -189,15 +189,17 @@ def test_inverse_circuit_returns_to_zero_state(prec):
 @pytest.mark.parametrize('lat,gl', [(inputs.lattice_for(4, 5, 18, seed=11), None),
                                     (None, _random_gate_list(19, 150, seed=77))])
 def test_plan_kernels_bitwise_equal_to_interpreter(lat, gl):
-    """The kernels compiled for a plan run the interpreter's arithmetic op for op (the same
-    plan: 13-qubit tiles, the largest the interpreter takes)."""
+    """The kernels compiled for a plan run the interpreter's arithmetic op for op.  Same
+    stages for both: 13-qubit tiles (the largest the interpreter takes) and stages of
+    qubit 0 + 3 (fuse_k = 3; the two kernels differ only in how many qubits a thread
+    holds, which changes no amplitude's sequence of operations)."""
     if lat is not None:
         n, g = lat.n_qubits, sv.sv_generate_circuit(lat)
     else:
         n, g = 19, _to_lib(gl)
     out = {}
     for jit in (-1, 1):
-        h = sv.sv_create(n, sv.options(jit=jit, tile_bits=13))
+        h = sv.sv_create(n, sv.options(jit=jit, tile_bits=13, fuse_k=3))
         try:
             sv.sv_set_profiling(h, True)
             sv.sv_apply_circuit(h, g)
