@@ -243,6 +243,39 @@ def run_branch(args, rank, world):
     return 0
 
 
+def run_tensor(args, rank, world):
+    """The full 28-qubit state (4x7 lattice, depth 10) from the cut decomposition in tensor
+    form: two batched half-states (14 + t qubits) and the branch sum of their outer
+    products, a complex (2^14 x 2^t) x (2^t x 2^14) product written as 2^28 amplitudes."""
+    import torch
+    from paper_1804_04797_gb300 import inputs, sv
+    torch.cuda.set_device(int(os.environ.get('LOCAL_RANK', '0')))
+    lat = inputs.C28
+    n = lat.n_qubits
+    h = sv.sv_create(n)
+    try:
+        for _ in range(max(1, args.warmup)):
+            sv.sv_branch_full_state(lat, inputs.C28_HALF_A, h)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for _ in range(args.steps):
+            sv.sv_branch_full_state(lat, inputs.C28_HALF_A, h)
+        torch.cuda.synchronize()
+        dt = (time.perf_counter() - t0) / args.steps
+        norm2, _ = sv.sv_norm(h)
+    finally:
+        sv.sv_destroy(h)
+    if rank == 0:
+        print(json.dumps({
+            'metric': '28q full state by the tensor form of the cut decomposition, s per state',
+            'workload': 'tensor28', 'value': dt, 'unit': 's/state', 'higher_is_better': False,
+            'n_gpus': world, 'steps': args.steps, 'warmup': args.warmup,
+            'config': {'workload': '4x7 lattice, depth 10, cut rows 1|2',
+                       'counts': sv.sv_branch_counts(lat, inputs.C28_HALF_A)},
+            'norm_err': abs(norm2 - 1)}), flush=True)
+    return 0
+
+
 def run_inner(args, rank, world):
     """Task 2 by the inner product: amplitudes of the 34-qubit depth-30 circuit cut after
     layer 15, <U2^dagger x | U1 H^n 0> for 4 bitstrings (one forward state, one backward
@@ -281,7 +314,7 @@ def main():
     ap.add_argument('--no-fused', action='store_true')
     ap.add_argument('--paths', default='plain,tf32x3,f16x3', help='comma list of plain, tf32x3, f16x3, pergate')
     ap.add_argument('--tile-bits', type=int, default=0, help='tile qubits of the tile passes (0 = default 13)')
-    ap.add_argument('--workload', default='34q', choices=['34q', 'batch', 'branch42', 'inner34'],
+    ap.add_argument('--workload', default='34q', choices=['34q', 'batch', 'branch42', 'inner34', 'tensor28'],
                     help='34q: the headline circuit; batch: the 512-circuit uneven batch; branch42: the '
                          '42-qubit cut-branch amplitude task (secondary lines)')
     ap.add_argument('--depth', type=int, default=0, help='override the lattice depth (profiling of smaller cases)')
@@ -299,6 +332,8 @@ def main():
         return run_branch(args, rank, world)
     if args.workload == 'inner34':
         return run_inner(args, rank, world)
+    if args.workload == 'tensor28':
+        return run_tensor(args, rank, world)
 
     import numpy as np
     import torch

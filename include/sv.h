@@ -198,6 +198,16 @@ sv_status sv_get_probabilities(sv_state *s, const uint64_t *bits, size_t m, doub
 sv_status sv_branch_amplitudes(const sv_lattice *lat, const sv_cut *cut, const uint64_t *bits,
                                size_t m, const sv_options *opts, double *out_re_im);
 
+/* The full state from the cut decomposition in tensor form (§2, Eqs. 6-7): the two
+ * halves' batched branch states A (n_A + t qubits) and B (n_B + t) give
+ * psi[x_A + (x_B << n_A)] = sum_l A_l[x_A] B_l[x_B], a complex matrix product over the
+ * 2^t branches, written into out (an n-qubit handle on the same device; fp32
+ * accumulation).  Crossing CZs that only sign the output are applied to the result as
+ * CZ gates; the others are fully decomposed (an implicit decomposition fixes a branch by
+ * an output bit, which a product over all outputs cannot).  Half A must be qubits
+ * 0..n_A-1 (a cut between lattice rows).  SV_ERR_ARG otherwise. */
+sv_status sv_branch_full_state(const sv_lattice *lat, const sv_cut *cut, const sv_options *opts, sv_state *out);
+
 /* The decomposition sv_branch_amplitudes runs for a cut (host only): counts[0] = CZs
  * crossing the cut, [1] = those absorbed as output signs, [2] = branch bits of half A,
  * [3] = of half B, [4] = branch bits summed over (2^counts[4] terms per amplitude). */

@@ -55,7 +55,9 @@ struct CutPlan {
   std::vector<std::pair<int, int>> fix_b;
 };
 
-sv_status plan_cut(const sv_lattice *lat, const sv_cut *cut, CutPlan *C) {
+// allow_implicit: may a crossing CZ be decomposed implicitly (an amplitude sum can fix
+// the branch index by the output bit; a full-state product cannot)
+sv_status plan_cut(const sv_lattice *lat, const sv_cut *cut, CutPlan *C, bool allow_implicit = true) {
   std::vector<sv_gate> g;
   sv_status st = generate(lat, &g);
   if (st != SV_OK) return st;
@@ -82,7 +84,7 @@ sv_status plan_cut(const sv_lattice *lat, const sv_cut *cut, CutPlan *C) {
     const int qa = C->in_a[x.q0] ? x.q0 : x.q1, qb = C->in_a[x.q0] ? x.q1 : x.q0;
     const bool qa_quiet = last_nd[qa] < (long)i, qb_quiet = last_nd[qb] < (long)i;
     int r = 0;
-    if (!cut->full_decomposition) r = (qa_quiet && qb_quiet) ? 1 : qa_quiet ? 2 : qb_quiet ? 3 : 0;
+    if (!cut->full_decomposition) r = (qa_quiet && qb_quiet) ? 1 : !allow_implicit ? 0 : qa_quiet ? 2 : qb_quiet ? 3 : 0;
     role.push_back(r);
   }
   C->t = (int)role.size();
@@ -287,5 +289,43 @@ extern "C" sv_status sv_amplitudes_by_inner_product(const sv_lattice *lat, int s
     if ((st = sv_apply_circuit_inverse(B.s, g2.data(), g2.size())) != SV_OK) return st;
     if ((st = sv_inner_product(B.s, A.s, out_re_im + 2 * j)) != SV_OK) return st;
   }
+  return SV_OK;
+}
+
+extern "C" sv_status sv_branch_full_state(const sv_lattice *lat, const sv_cut *cut, const sv_options *opts,
+                                          sv_state *out) {
+  clear_error();
+  if (!lat || !cut || !out) return fail(SV_ERR_ARG, "sv_branch_full_state: NULL argument");
+  CutPlan C;
+  sv_status st = plan_cut(lat, cut, &C, false);
+  if (st != SV_OK) return st;
+  if (out->n != C.n) return fail(SV_ERR_ARG, "sv_branch_full_state: output state has the wrong size");
+  if (cut->half_a_mask != (C.na >= 64 ? ~0ull : (1ull << C.na) - 1))
+    return fail(SV_ERR_ARG, "sv_branch_full_state: half A must be qubits 0..n_A-1");
+  if (out->broken) return fail(SV_ERR_STATE, "state is unusable after an earlier failure");
+  sv_options o;
+  std::memset(&o, 0, sizeof(o));
+  if (opts) o = *opts;
+  Holder A, B;
+  if ((st = sv_create(C.na + C.ta, &o, &A.s)) != SV_OK) return st;
+  if ((st = sv_create(C.nb + C.tb, &o, &B.s)) != SV_OK) return st;
+  if ((st = apply_gates(A.s, C.ga)) != SV_OK) return st;
+  if ((st = apply_gates(B.s, C.gb)) != SV_OK) return st;
+  if ((st = set_device(out)) != SV_OK) return st;
+  cudaError_t e = cudaStreamSynchronize(A.s->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(B.s->stream);
+  // each branch slice carries 2^{-t/2} per half
+  const float scale = std::ldexp(1.0f, C.tf);
+  if (e == cudaSuccess)
+    e = svk::launch_outer_sum(A.s->psi, C.na, B.s->psi, C.nb, C.tf, scale, out->psi, out->stream);
+  if (e != cudaSuccess) { out->broken = true; return cuda_fail(e, "sv_branch_full_state"); }
+  out->fresh = false;
+  if (out->prof) out->other_launches += 1;
+  // the crossing CZs taken as output signs act on the product state like any CZ
+  std::vector<svp::Gate> signs;
+  for (const auto &sg : C.signs) signs.push_back(svp::Gate{svp::K_CZ, (uint8_t)sg.first, (uint8_t)sg.second});
+  if (!signs.empty() && (st = apply_gates(out, signs)) != SV_OK) return st;
+  e = cudaStreamSynchronize(out->stream);
+  if (e != cudaSuccess) return cuda_fail(e, "sv_branch_full_state");
   return SV_OK;
 }

@@ -43,7 +43,71 @@ __global__ void branch_sum_kernel(const float2 *__restrict__ A, int nA, const fl
   }
 }
 
+// The tensor form of the same sum (§2, Eqs. 6-7: the full state is a sum over branches
+// of outer products phi_l (x) xi_l): out[x_A + (x_B << nA)] = scale * sum_l
+// A[x_A + (l << nA)] * B[x_B + (l << nB)], a complex matrix product (2^nB x 2^t) *
+// (2^t x 2^nA).  64 x 64 outputs per CTA, 16 branches per shared-memory step, 4 x 4
+// outputs per thread, fp32 accumulation.
+constexpr int kTile = 64, kStep = 16;
+
+__global__ void __launch_bounds__(256) outer_sum_kernel(const float2 *__restrict__ A, int nA,
+                                                        const float2 *__restrict__ B, int nB, int t, float scale,
+                                                        float2 *__restrict__ out) {
+  __shared__ float2 As[kStep][kTile], Bs[kStep][kTile];
+  const uint64_t xa0 = (uint64_t)blockIdx.x * kTile, xb0 = (uint64_t)blockIdx.y * kTile;
+  const uint64_t na = 1ull << nA, nb = 1ull << nB, branches = 1ull << t;
+  const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
+  float2 acc[4][4];
+#pragma unroll
+  for (int i = 0; i < 4; ++i)
+#pragma unroll
+    for (int j = 0; j < 4; ++j) acc[i][j] = make_float2(0.f, 0.f);
+  for (uint64_t l0 = 0; l0 < branches; l0 += kStep) {
+    for (int e = threadIdx.x; e < kStep * kTile; e += blockDim.x) {
+      const int k = e / kTile, i = e % kTile;
+      const bool lin = l0 + k < branches;
+      As[k][i] = (lin && xa0 + i < na) ? A[xa0 + i + ((l0 + k) << nA)] : make_float2(0.f, 0.f);
+      Bs[k][i] = (lin && xb0 + i < nb) ? B[xb0 + i + ((l0 + k) << nB)] : make_float2(0.f, 0.f);
+    }
+    __syncthreads();
+#pragma unroll
+    for (int k = 0; k < kStep; ++k) {
+      float2 a[4], b[4];
+#pragma unroll
+      for (int i = 0; i < 4; ++i) a[i] = As[k][tx * 4 + i];
+#pragma unroll
+      for (int j = 0; j < 4; ++j) b[j] = Bs[k][ty * 4 + j];
+#pragma unroll
+      for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+          acc[i][j].x = fmaf(a[i].x, b[j].x, fmaf(-a[i].y, b[j].y, acc[i][j].x));
+          acc[i][j].y = fmaf(a[i].x, b[j].y, fmaf(a[i].y, b[j].x, acc[i][j].y));
+        }
+    }
+    __syncthreads();
+  }
+#pragma unroll
+  for (int j = 0; j < 4; ++j) {
+    const uint64_t xb = xb0 + ty * 4 + j;
+    if (xb >= nb) continue;
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+      const uint64_t xa = xa0 + tx * 4 + i;
+      if (xa < na) out[xa + (xb << nA)] = make_float2(acc[i][j].x * scale, acc[i][j].y * scale);
+    }
+  }
+}
+
 }  // namespace
+
+cudaError_t launch_outer_sum(const float2 *A, int nA, const float2 *B, int nB, int t, float scale, float2 *out,
+                             cudaStream_t st) {
+  const uint64_t gx = ((1ull << nA) + kTile - 1) / kTile, gy = ((1ull << nB) + kTile - 1) / kTile;
+  if (gx > 0x7fffffffull || gy > 65535ull) return cudaErrorInvalidValue;
+  outer_sum_kernel<<<dim3((unsigned)gx, (unsigned)gy), 256, 0, st>>>(A, nA, B, nB, t, scale, out);
+  return cudaGetLastError();
+}
 
 cudaError_t launch_branch_sum(const float2 *A, int nA, const float2 *B, int nB, int t, const uint64_t *xa,
                               const uint64_t *xb, int m, double scale, double *out, cudaStream_t st) {

@@ -56,6 +56,11 @@ cudaError_t launch_branch_sum(const float2 *A, int nA, const float2 *B, int nB, 
 
 int device_sm_count();
 
+// Full state from two batched half-states (Eqs. 6-7): out[x_A + (x_B << nA)] = scale *
+// sum_l A[x_A + (l << nA)] B[x_B + (l << nB)] over 2^t branches (fp32).
+cudaError_t launch_outer_sum(const float2 *A, int nA, const float2 *B, int nB, int t, float scale, float2 *out,
+                             cudaStream_t st);
+
 // <a|b> = sum conj(a_i) b_i of two 2^n states: out2 = (re, im), fp64 (partials: 2 *
 // reduce_partials_needed() doubles of scratch).
 cudaError_t launch_inner(const float2 *a, const float2 *b, int n, double *partials, double *out2, cudaStream_t st);

@@ -86,6 +86,7 @@ def lib():
         'sv_norm': ([vp, P(c_double), P(c_double)], c_int),
         'sv_branch_amplitudes': ([P(sv_lattice), P(sv_cut), vp, c_size_t, P(sv_options), vp], c_int),
         'sv_branch_counts': ([P(sv_lattice), P(sv_cut), vp], c_int),
+        'sv_branch_full_state': ([P(sv_lattice), P(sv_cut), P(sv_options), vp], c_int),
         'sv_apply_batch': ([vp, c_size_t, P(sv_options), vp], c_int),
         'sv_batch_amplitudes': ([c_size_t, vp, c_size_t, vp], c_int),
         'sv_batch_free': ([], c_int),
@@ -235,6 +236,14 @@ def sv_branch_amplitudes(lat, half_a_mask, bits, opts=None, full_decomposition=F
     _check(lib().sv_branch_amplitudes(ctypes.byref(L), ctypes.byref(cut), b.ctypes.data, b.size,
                                       ctypes.byref(opts) if opts is not None else None, out.ctypes.data))
     return out.view(np.complex128)
+
+
+def sv_branch_full_state(lat, half_a_mask, h, opts=None, full_decomposition=False):
+    """Write sum_l A_l (x) B_l (the full state) into handle h."""
+    L = lat if isinstance(lat, sv_lattice) else lattice(lat)
+    cut = sv_cut(half_a_mask, int(bool(full_decomposition)))
+    _check(lib().sv_branch_full_state(ctypes.byref(L), ctypes.byref(cut),
+                                      ctypes.byref(opts) if opts is not None else None, h))
 
 
 def sv_branch_counts(lat, half_a_mask, full_decomposition=False):

@@ -384,3 +384,45 @@ def test_inner_product_and_basis_state():
     finally:
         sv.sv_destroy(h3)
         sv.sv_destroy(h4)
+
+
+@pytest.mark.parametrize('full', [False, True])
+def test_branch_full_state_matches_oracle(full):
+    """Eqs. 6-7: the full state as the sum over branches of A_l (x) B_l."""
+    lat = inputs.lattice_for(4, 4, 9, seed=31)
+    half_a = (1 << 8) - 1
+    n, gates = oracle_gates(lat)
+    want = csim.run(n, gates)
+    h = sv.sv_create(n)
+    try:
+        sv.sv_branch_full_state(lat, half_a, h, full_decomposition=full)
+        got = sv.sv_copy_state(h, n)
+        n2, _ = sv.sv_norm(h)
+    finally:
+        sv.sv_destroy(h)
+    assert rel_l2(got, want) <= REL_L2
+    assert abs(n2 - 1) <= NORM_TOL
+
+
+def test_branch_full_state_28q_equals_direct_run():
+    lat = inputs.C28
+    n = lat.n_qubits
+    a, b = sv.sv_create(n), sv.sv_create(n)
+    try:
+        sv.sv_branch_full_state(lat, inputs.C28_HALF_A, a)
+        sv.sv_apply_circuit(b, sv.sv_generate_circuit(lat))
+        ip = sv.sv_inner_product(b, a)
+        n2a, _ = sv.sv_norm(a)
+        bits = inputs.bitstrings(n, 64, seed=2)
+        assert rel_l2(sv.sv_get_amplitudes(a, bits), sv.sv_get_amplitudes(b, bits)) <= REL_L2
+    finally:
+        sv.sv_destroy(a)
+        sv.sv_destroy(b)
+    assert abs(n2a - 1) <= NORM_TOL
+    assert 1 - abs(ip) ** 2 / n2a <= 1e-9        # 1 - fidelity against the direct state
+    h = sv.sv_create(n)
+    try:
+        with pytest.raises(sv.SvError):          # half A must be the low qubits
+            sv.sv_branch_full_state(lat, ((1 << n) - 1) ^ inputs.C28_HALF_A, h)
+    finally:
+        sv.sv_destroy(h)

@@ -401,3 +401,19 @@ def test_implicit_branch_slices_vanish():
             lj = (l >> j) & 1
             idx = np.arange(A.size)
             assert np.all(A[((idx >> q) & 1) != lj] == 0)
+
+
+def test_full_state_is_the_sum_of_branch_outer_products():
+    """§2 Eqs. 6-7 (the tensor form): psi = sum_l A_l (x) B_l over all 2^t branches,
+    with half A the low qubits."""
+    lat = inputs.lattice_for(4, 4, 9, seed=31)
+    n, gates = oc.generate(lat.rows, lat.cols, lat.removed_mask, lat.depth, lat.seed)
+    half_a = (1 << 8) - 1
+    qa, qb, ga, gb, t = ov.split_halves(n, gates, half_a)
+    assert qa == list(range(8))
+    psi = np.zeros(1 << n, dtype=np.complex128)
+    for l in range(1 << t):
+        A = ov.run(len(qa), ov._branch_gates(ga, l, 'A'))
+        B = ov.run(len(qb), ov._branch_gates(gb, l, 'B'))
+        psi += np.outer(B, A).reshape(-1)      # index x_A + (x_B << n_A)
+    np.testing.assert_allclose(psi, ov.run(n, gates), rtol=0, atol=1e-12)
