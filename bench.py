@@ -41,7 +41,7 @@ def _peaks():
 # amplitudes; profiles/sv_pass_plain_28q_d30.md, profiles/fused_pass_kernel_f16_28q_d30.md);
 # a pass moves each amplitude once in and once out, so traffic scales with the amplitudes.
 TRAFFIC_PER_ALGORITHMIC_BYTE = {
-    'sv_pass': (2.147615e9 + 2.086388e9) / (16.0 * 2 ** 28),
+    'sv_pass': (2.148672e9 + 2.093911e9) / (16.0 * 2 ** 28),
     'fused_pass_kernel<f16>': (2.147713e9 + 2.096311e9) / (16.0 * 2 ** 28),
 }
 SMS, FP32_LANES_PER_SM = 152, 128

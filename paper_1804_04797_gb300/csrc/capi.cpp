@@ -58,6 +58,27 @@ svp::Options plan_options(const sv_options &o) {
   return p;
 }
 
+svp::Options apply_plan_options(const sv_options &o, int n, bool *want_jit) {
+  svp::Options po = plan_options(o);
+  // the tensor-core kernel takes 12- or 13-qubit tiles; smaller states use the plain one
+  if (po.fused && std::min(po.m, n) < 12) {
+    po.fused = false;
+    po.pack = true;
+    po.rk = svk::tile_pass_register_slots();
+    po.r = std::min(po.r, po.rk);
+  }
+  // plain path: kernels compiled for the plan where they pay (or where asked for), on
+  // 12-qubit tiles unless tile_bits says otherwise (they also take 14)
+  *want_jit = !po.fused && o.jit >= 0 &&
+              (o.jit == 1 || n >= kJitMinQubits || std::min(po.m, n) > svk::tile_pass_max_bits());
+  if (*want_jit) {
+    po.rk = svj::register_slots();
+    po.r = std::min(po.r, po.rk);
+    if (o.tile_bits == 0) po.m = svj::kTileBits;
+  }
+  return po;
+}
+
 sv_status check_options(const sv_options &o) {
   if (o.precision != SV_PREC_PLAIN && o.precision != SV_PREC_TF32X3 && o.precision != SV_PREC_F16X3 &&
       o.precision != SV_PREC_PERGATE)
@@ -265,23 +286,8 @@ sv_status apply_gates(sv_state *s, const std::vector<svp::Gate> &g) {
   if (g.empty() && !s->fresh) return SV_OK;
   svp::Plan P;
   const char *err = nullptr;
-  svp::Options po = plan_options(s->opts);
-  // the tensor-core kernel takes 12- or 13-qubit tiles; smaller states use the plain one
-  if (po.fused && std::min(po.m, s->n) < 12) {
-    po.fused = false;
-    po.pack = true;
-    po.rk = svk::tile_pass_register_slots();
-    po.r = std::min(po.r, po.rk);
-  }
-  // plain path: kernels compiled for this plan where they pay (or where asked for); they
-  // also take 14-qubit tiles (tile_bits = 14: one pass fewer on 34 qubits, but one CTA
-  // per SM, measured 7 % slower than 13-qubit tiles)
-  const bool want_jit = !po.fused && s->opts.jit >= 0 &&
-                        (s->opts.jit == 1 || s->n >= kJitMinQubits || std::min(po.m, s->n) > svk::tile_pass_max_bits());
-  if (want_jit) {
-    po.rk = svj::register_slots();
-    po.r = std::min(po.r, po.rk);
-  }
+  bool want_jit = false;
+  svp::Options po = apply_plan_options(s->opts, s->n, &want_jit);
   if (!svp::build_plan(s->n, g, po, s->fresh, &P, &err)) return fail(SV_ERR_ARG, err ? err : "planning failed");
   const svj::Module *jit = nullptr;
   if (want_jit) {
@@ -541,7 +547,8 @@ sv_status sv_plan(int n_qubits, const sv_gate *gates, size_t n_gates, const sv_o
   if ((st = convert_gates(n_qubits, gates, n_gates, false, &g)) != SV_OK) return st;
   svp::Plan P;
   const char *err = nullptr;
-  if (!svp::build_plan(n_qubits, g, plan_options(o), fresh_state != 0, &P, &err))
+  bool want_jit = false;
+  if (!svp::build_plan(n_qubits, g, apply_plan_options(o, n_qubits, &want_jit), fresh_state != 0, &P, &err))
     return fail(SV_ERR_ARG, err ? err : "planning failed");
   if (summary) {
     summary->passes = (int)P.passes.size();

@@ -24,6 +24,9 @@ namespace svj {
 // (0.87 s, 0.96 s): it halves the resident CTAs, and the stages need every warp.
 constexpr int kRegisterSlots = 4;
 int register_slots();
+// Default tile size of plans for these kernels: 12 qubits (8 passes on 34 qubits, five
+// CTAs per SM) measured faster than 13 (7 passes, two CTAs) and 14 (6 passes, one).
+constexpr int kTileBits = 12;
 
 // CUDA source of the kernel ("sv_pass") of one pass of a packed plan.  kpr: register
 // slots besides the pack bit (the plan's rk).

@@ -48,6 +48,9 @@ constexpr int kJitMinQubits = 24;
 sv_status cuda_fail(cudaError_t e, const char *what);
 sv_status ensure_device_buffer(void **buf, size_t *cap, size_t need);
 svp::Options plan_options(const sv_options &o);
+// The plan options sv_apply_circuit uses for an n-qubit state; *want_jit: the plain path
+// is to run on plan-specialised kernels.
+svp::Options apply_plan_options(const sv_options &o, int n, bool *want_jit);
 sv_status check_options(const sv_options &o);
 sv_status convert_gates(int n, const sv_gate *g, size_t count, bool inverse, std::vector<svp::Gate> *out);
 sv_status upload_plan(sv_state *s, const svp::Plan &P, svk::DevPlanView *view);
