@@ -455,9 +455,9 @@ __device__ __forceinline__ void build_chunk_table(const DevPass &P, uint64_t *ch
 // in memory, (re, im, re', im'), one commit group.  L2 is coherent, so the copies also see
 // data that other CTAs of the same launch wrote.  finish_tile_load() waits for the
 // thread's own copies and regroups them (each thread touches only its own slots).
+// (tid, T): this thread's index among the T threads that share the tile.
 __device__ __forceinline__ void load_tile_async(const float2 *__restrict__ psi, float4 *tile, const DevPass &P,
-                                                const uint64_t *chunk_off, uint64_t base) {
-  const uint32_t tid = threadIdx.x, T = blockDim.x;
+                                                const uint64_t *chunk_off, uint64_t base, uint32_t tid, uint32_t T) {
   const int cp = P.c - 1;  // pair bits inside a chunk of 2^c amplitudes
   const uint32_t in_mask = (1u << cp) - 1;
   const uint32_t sbase = (uint32_t)__cvta_generic_to_shared(tile);
@@ -470,9 +470,8 @@ __device__ __forceinline__ void load_tile_async(const float2 *__restrict__ psi, 
   }
   asm volatile("cp.async.commit_group;" ::: "memory");
 }
-__device__ __forceinline__ void finish_tile_load(float4 *tile) {
+__device__ __forceinline__ void finish_tile_load(float4 *tile, uint32_t tid, uint32_t T) {
   asm volatile("cp.async.wait_group 0;" ::: "memory");
-  const uint32_t tid = threadIdx.x, T = blockDim.x;
 #pragma unroll 4
   for (int it = 0; it < kP; ++it) {
     float4 &x = tile[pack_phys(tid + (uint32_t)it * T)];
@@ -482,8 +481,7 @@ __device__ __forceinline__ void finish_tile_load(float4 *tile) {
 }
 
 __device__ __forceinline__ void store_tile(float2 *__restrict__ psi, const float4 *tile, const DevPass &P,
-                                           const uint64_t *chunk_off, uint64_t base) {
-  const uint32_t tid = threadIdx.x, T = blockDim.x;
+                                           const uint64_t *chunk_off, uint64_t base, uint32_t tid, uint32_t T) {
   const int cp = P.c - 1;
   const uint32_t in_mask = (1u << cp) - 1;
 #pragma unroll 4
@@ -503,11 +501,24 @@ __device__ __forceinline__ void init_regs(Regs &R, Regs &I, const DevPass &P, ui
   if (!(P.flags & svp::PF_INIT_UNIFORM) && W == 0) R[0].x = 1.f;
 }
 
-__device__ __forceinline__ void init_tile(float4 *tile, const DevPass &P, uint64_t base) {
+__device__ __forceinline__ void init_tile(float4 *tile, const DevPass &P, uint64_t base, uint32_t tid, uint32_t T) {
   const float a = (P.flags & svp::PF_INIT_UNIFORM) ? P.init_amp : 0.f;
-  for (uint32_t k = threadIdx.x; k < (1u << (P.m - 1)); k += blockDim.x)
-    tile[k] = make_float4(a, a, 0.f, 0.f);
-  if (!(P.flags & svp::PF_INIT_UNIFORM) && base == 0 && threadIdx.x == 0) tile[0] = make_float4(1.f, 0.f, 0.f, 0.f);
+  for (uint32_t k = tid; k < (1u << (P.m - 1)); k += T) tile[k] = make_float4(a, a, 0.f, 0.f);
+  if (!(P.flags & svp::PF_INIT_UNIFORM) && base == 0 && tid == 0) tile[0] = make_float4(1.f, 0.f, 0.f, 0.f);
+}
+
+// The same for a CTA whose threads all share one tile.
+__device__ __forceinline__ void load_tile_async(const float2 *__restrict__ psi, float4 *tile, const DevPass &P,
+                                                const uint64_t *chunk_off, uint64_t base) {
+  load_tile_async(psi, tile, P, chunk_off, base, threadIdx.x, blockDim.x);
+}
+__device__ __forceinline__ void finish_tile_load(float4 *tile) { finish_tile_load(tile, threadIdx.x, blockDim.x); }
+__device__ __forceinline__ void store_tile(float2 *__restrict__ psi, const float4 *tile, const DevPass &P,
+                                           const uint64_t *chunk_off, uint64_t base) {
+  store_tile(psi, tile, P, chunk_off, base, threadIdx.x, blockDim.x);
+}
+__device__ __forceinline__ void init_tile(float4 *tile, const DevPass &P, uint64_t base) {
+  init_tile(tile, P, base, threadIdx.x, blockDim.x);
 }
 
 #ifndef SV_PLAN_KERNELS  // the interpreter
