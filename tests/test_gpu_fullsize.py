@@ -77,6 +77,30 @@ def test_34q_depth30_invariants():
         sv.sv_destroy(h)
 
 
+def test_34q_plan_kernels_and_interpreter_agree():
+    """The 34-qubit circuit on the interpreting kernel (13-qubit tiles), on the default
+    plan kernels (12-qubit tiles) and on 14-qubit-tile plan kernels: the same amplitudes
+    within fp32 rounding, norm 1."""
+    lat = inputs.C34
+    n = lat.n_qubits
+    g = sv.sv_generate_circuit(lat)
+    bits = np.array(inputs.sample_indices(n, 1024, seed=1), dtype=np.uint64)
+    out = {}
+    h = sv.sv_create(n)
+    try:
+        for name, kw in (('plan12', dict()), ('interp', dict(jit=-1)), ('plan14', dict(tile_bits=14))):
+            sv.sv_set_options(h, sv.options(**kw))
+            sv.sv_reset(h)
+            sv.sv_apply_circuit(h, g)
+            out[name] = sv.sv_get_amplitudes(h, bits)
+            n2, _ = sv.sv_norm(h)
+            assert abs(n2 - 1) <= NORM_TOL, name
+    finally:
+        sv.sv_destroy(h)
+    assert rel_l2(out['interp'], out['plan12']) <= REL_L2
+    assert rel_l2(out['plan14'], out['plan12']) <= REL_L2
+
+
 def test_34q_amplitudes_by_inner_product_match_full_state():
     """Task 2 by the inner product on the headline circuit (two 128 GiB states), cut after
     layer 15, against the forward full state's amplitudes."""
