@@ -278,6 +278,24 @@ sv_status build_stage_mats(svp::Plan *P, const std::vector<svp::Gate> &g, int r)
 
 namespace svc {
 
+// A fused pass whose bounded wait gave up leaves a non-zero error word in the plan.
+sv_status check_fused_error(sv_state *s, const svk::DevPlanView &view) {
+  int h_err = 0;
+  cudaError_t e = cudaMemcpyAsync(&h_err, view.err, sizeof(int), cudaMemcpyDeviceToHost, s->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s->stream);
+  if (e != cudaSuccess) {
+    s->broken = true;
+    s->plan_valid = false;
+    return cuda_fail(e, "fused pass");
+  }
+  if (h_err != 0) {
+    s->broken = true;
+    s->plan_valid = false;
+    return fail(SV_ERR_TIMEOUT, "fused pass: a tensor-core wait gave up (state undefined)");
+  }
+  return SV_OK;
+}
+
 sv_status apply_gates(sv_state *s, const std::vector<svp::Gate> &g) {
   sv_status st;
   if ((st = set_device(s)) != SV_OK) return st;
@@ -285,6 +303,26 @@ sv_status apply_gates(sv_state *s, const std::vector<svp::Gate> &g) {
   if ((s->opts.precision == SV_PREC_TF32X3 || s->opts.precision == SV_PREC_F16X3) && !svk::fused_supported())
     return fail(SV_ERR_CUDA, "fused tensor-core path needs an sm_103a device");
   if (g.empty() && !s->fresh) return SV_OK;
+  // the same gate list, options and starting condition as the last call: reuse its plan
+  uint64_t key = 1469598103934665603ull;
+  auto mix = [&key](const void *p, size_t len) {
+    const unsigned char *b = static_cast<const unsigned char *>(p);
+    for (size_t i = 0; i < len; ++i) key = (key ^ b[i]) * 1099511628211ull;
+  };
+  const int head[7] = {s->n, s->fresh ? 1 : 0, s->opts.precision, s->opts.fuse_k, s->opts.tile_bits,
+                       s->opts.low_bits, s->opts.jit};
+  mix(head, sizeof(head));
+  if (!g.empty()) mix(g.data(), g.size() * sizeof(svp::Gate));
+  if (s->plan_valid && s->plan_key == key) {
+    const bool f16 = s->opts.precision == SV_PREC_F16X3;
+    if ((st = run_plan(s, s->plan, s->plan_view, s->plan_po.fused, f16, s->plan_jit)) != SV_OK) {
+      s->plan_valid = false;
+      return st;
+    }
+    s->fresh = false;
+    return s->plan_po.fused ? check_fused_error(s, s->plan_view) : SV_OK;
+  }
+  s->plan_valid = false;
   svp::Plan P;
   const char *err = nullptr;
   bool want_jit = false;
@@ -314,17 +352,13 @@ sv_status apply_gates(sv_state *s, const std::vector<svp::Gate> &g) {
   if ((st = upload_plan(s, P, &view)) != SV_OK) return st;
   if ((st = run_plan(s, P, view, po.fused, f16, jit)) != SV_OK) return st;
   s->fresh = false;
-  if (po.fused) {
-    // a fused pass whose bounded wait gave up leaves a non-zero error word
-    int h_err = 0;
-    cudaError_t e = cudaMemcpyAsync(&h_err, view.err, sizeof(int), cudaMemcpyDeviceToHost, s->stream);
-    if (e == cudaSuccess) e = cudaStreamSynchronize(s->stream);
-    if (e != cudaSuccess) { s->broken = true; return cuda_fail(e, "fused pass"); }
-    if (h_err != 0) {
-      s->broken = true;
-      return fail(SV_ERR_TIMEOUT, "fused pass: a tensor-core wait gave up (state undefined)");
-    }
-  }
+  if (po.fused && (st = check_fused_error(s, view)) != SV_OK) return st;
+  s->plan = std::move(P);
+  s->plan_po = po;
+  s->plan_jit = jit;
+  s->plan_view = view;
+  s->plan_key = key;
+  s->plan_valid = true;
   return SV_OK;
 }
 

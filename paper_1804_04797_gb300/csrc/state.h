@@ -9,6 +9,10 @@
 #include "kernels.h"
 #include "plan.h"
 
+namespace svj {
+struct Module;
+}
+
 struct sv_state {
   int n = 0;
   float2 *psi = nullptr;  // 2^n complex64 amplitudes on the device
@@ -32,6 +36,14 @@ struct sv_state {
   double h2d = 0, d2h = 0;
   int other_launches = 0;
   int jit_launches = 0;
+  // the last plan run on this handle (a circuit applied again reuses it and its device
+  // copy: no planning, kernel-source hashing or upload)
+  bool plan_valid = false;
+  uint64_t plan_key = 0;
+  svp::Plan plan;
+  svp::Options plan_po;
+  const svj::Module *plan_jit = nullptr;
+  svk::DevPlanView plan_view{};
 };
 
 namespace svj {

@@ -426,3 +426,26 @@ def test_branch_full_state_28q_equals_direct_run():
             sv.sv_branch_full_state(lat, ((1 << n) - 1) ^ inputs.C28_HALF_A, h)
     finally:
         sv.sv_destroy(h)
+
+
+@pytest.mark.parametrize('kw', [dict(), dict(jit=-1), dict(precision=H16)])
+def test_repeated_circuit_reuses_its_plan(kw):
+    """A handle replays the last plan when the same circuit comes again (same options and
+    starting condition); a changed condition plans anew."""
+    lat = inputs.lattice_for(4, 6, 16, seed=9)
+    n = lat.n_qubits
+    g = sv.sv_generate_circuit(lat)
+    h = sv.sv_create(n, sv.options(**kw))
+    try:
+        sv.sv_apply_circuit(h, g)
+        a1 = sv.sv_copy_state(h, n)
+        sv.sv_reset(h)
+        sv.sv_apply_circuit(h, g)                 # same key: replayed
+        a2 = sv.sv_copy_state(h, n)
+        sv.sv_apply_circuit_inverse(h, g)         # another plan
+        sv.sv_apply_circuit(h, g)                 # not fresh now: planned again
+        a3 = sv.sv_copy_state(h, n)
+    finally:
+        sv.sv_destroy(h)
+    assert np.array_equal(a1.view(np.uint32), a2.view(np.uint32))
+    assert rel_l2(a3, a1) <= 2e-5
