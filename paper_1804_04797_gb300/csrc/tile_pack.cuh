@@ -64,49 +64,78 @@ struct Ops<float> {
   __device__ __forceinline__ static float rs(float a) { return rs2(a); }
 };
 
-struct GH {  // (x + y)/sqrt2, (x - y)/sqrt2
+// Each gate is written on s = x + y and d = x - y (its out()): f() forms them with adds,
+// fs() with y carrying a sign (+1 or -1: y's sign from ops before the gate folded into
+// one fused operation each, exact, the same result as negating y first).
+template <class T>
+struct Sgn;
+template <>
+struct Sgn<float2> {
+  __device__ __forceinline__ static float2 add(float2 x, float2 y, float s) { return fma2(y, f2(s, s), x); }
+  __device__ __forceinline__ static float2 sub(float2 x, float2 y, float s) { return fma2(y, f2(-s, -s), x); }
+};
+template <>
+struct Sgn<float> {
+  __device__ __forceinline__ static float add(float x, float y, float s) { return fmaf(y, s, x); }
+  __device__ __forceinline__ static float sub(float x, float y, float s) { return fmaf(y, -s, x); }
+};
+
+template <class G>
+struct Gate {
   template <class T>
   __device__ __forceinline__ static void f(T &xr, T &xi, T &yr, T &yi) {
     using O = Ops<T>;
     const T sr = O::add(xr, yr), si = O::add(xi, yi), dr = O::sub(xr, yr), di = O::sub(xi, yi);
+    G::out(sr, si, dr, di, xr, xi, yr, yi);
+  }
+  template <class T>
+  __device__ __forceinline__ static void fs(T &xr, T &xi, T &yr, T &yi, float s) {
+    using S = Sgn<T>;
+    const T sr = S::add(xr, yr, s), si = S::add(xi, yi, s), dr = S::sub(xr, yr, s), di = S::sub(xi, yi, s);
+    G::out(sr, si, dr, di, xr, xi, yr, yi);
+  }
+};
+
+struct GH : Gate<GH> {  // (x + y)/sqrt2, (x - y)/sqrt2
+  template <class T>
+  __device__ __forceinline__ static void out(T sr, T si, T dr, T di, T &xr, T &xi, T &yr, T &yi) {
+    using O = Ops<T>;
     xr = O::rs(sr); xi = O::rs(si); yr = O::rs(dr); yi = O::rs(di);
   }
 };
 // The square roots without their factor 1/2 (counted and applied once per stage):
-// X^{1/2}: x' = s + i d, y' = s - i d, with s = x + y, d = x - y
-struct GSX {
+// X^{1/2}: x' = s + i d, y' = s - i d
+struct GSX : Gate<GSX> {
   template <class T>
-  __device__ __forceinline__ static void f(T &xr, T &xi, T &yr, T &yi) {
+  __device__ __forceinline__ static void out(T sr, T si, T dr, T di, T &xr, T &xi, T &yr, T &yi) {
     using O = Ops<T>;
-    const T sr = O::add(xr, yr), si = O::add(xi, yi), dr = O::sub(xr, yr), di = O::sub(xi, yi);
     xr = O::sub(sr, di); xi = O::add(si, dr); yr = O::add(sr, di); yi = O::sub(si, dr);
   }
 };
-struct GSXDG {  // x' = s - i d, y' = s + i d
+struct GSXDG : Gate<GSXDG> {  // x' = s - i d, y' = s + i d
   template <class T>
-  __device__ __forceinline__ static void f(T &xr, T &xi, T &yr, T &yi) {
+  __device__ __forceinline__ static void out(T sr, T si, T dr, T di, T &xr, T &xi, T &yr, T &yi) {
     using O = Ops<T>;
-    const T sr = O::add(xr, yr), si = O::add(xi, yi), dr = O::sub(xr, yr), di = O::sub(xi, yi);
     xr = O::add(sr, di); xi = O::sub(si, dr); yr = O::sub(sr, di); yi = O::add(si, dr);
   }
 };
 // Y^{1/2}: x' = (1+i) d, y' = (1+i) s
-struct GSY {
+struct GSY : Gate<GSY> {
   template <class T>
-  __device__ __forceinline__ static void f(T &xr, T &xi, T &yr, T &yi) {
+  __device__ __forceinline__ static void out(T sr, T si, T dr, T di, T &xr, T &xi, T &yr, T &yi) {
     using O = Ops<T>;
-    const T sr = O::add(xr, yr), si = O::add(xi, yi), dr = O::sub(xr, yr), di = O::sub(xi, yi);
     xr = O::sub(dr, di); xi = O::add(dr, di); yr = O::sub(sr, si); yi = O::add(sr, si);
   }
 };
-// (Y^{1/2})^dagger: x' = (1-i) s, y' = -(1-i) d = (1-i) e with e = y - x
-struct GSYDG {
+// (Y^{1/2})^dagger: x' = (1-i) s, y' = -(1-i) d
+struct GSYDG : Gate<GSYDG> {
   template <class T>
-  __device__ __forceinline__ static void f(T &xr, T &xi, T &yr, T &yi) {
+  __device__ __forceinline__ static void out(T sr, T si, T dr, T di, T &xr, T &xi, T &yr, T &yi) {
     using O = Ops<T>;
-    const T sr = O::add(xr, yr), si = O::add(xi, yi), er = O::sub(yr, xr), ei = O::sub(yi, xi);
-    xr = O::add(sr, si); xi = O::sub(si, sr); yr = O::add(er, ei); yi = O::sub(ei, er);
+    xr = O::add(sr, si); xi = O::sub(si, sr); yr = O::sub(neg(dr), di); yi = O::sub(dr, di);
   }
+  __device__ __forceinline__ static float2 neg(float2 a) { return f2(-a.x, -a.y); }
+  __device__ __forceinline__ static float neg(float a) { return -a; }
 };
 
 // ---- diagonal phases on one element (r, i) ----------------------------------------------
@@ -144,6 +173,20 @@ template <class G>
 __device__ __forceinline__ void pairs_pack(Regs &R, Regs &I) {
 #pragma unroll
   for (int p = 0; p < kP; ++p) G::f(R[p].x, I[p].x, R[p].y, I[p].y);
+}
+// the same with y (the slot-1 element) carrying a sign s = +-1
+template <class G, int J>
+__device__ __forceinline__ void pairs_signed(Regs &R, Regs &I, float s) {
+  if constexpr (J < kPR) {
+#pragma unroll
+    for (int p = 0; p < kP; ++p)
+      if (!(p & (1 << J))) G::fs(R[p], I[p], R[p | (1 << J)], I[p | (1 << J)], s);
+  }
+}
+template <class G>
+__device__ __forceinline__ void pairs_pack_signed(Regs &R, Regs &I, float s) {
+#pragma unroll
+  for (int p = 0; p < kP; ++p) G::fs(R[p].x, I[p].x, R[p].y, I[p].y, s);
 }
 // phase D where register slot J is 1
 template <class D, int J>
