@@ -75,6 +75,7 @@ typedef struct {
   int jit;        /* plain path: run each plan on kernels compiled for it at run time */
                   /* (NVRTC; cached in memory and in the library's directory):       */
                   /* 1 = always (error if NVRTC fails), -1 = never, 0 = for n >= 24 [0] */
+                  /* (sv_apply_batch: per circuit, see there)                         */
 } sv_options;
 
 /* An R x C lattice circuit: bit r*cols+c of removed_mask drops site (r,c); kept sites
@@ -225,7 +226,10 @@ sv_status sv_branch_counts(const sv_lattice *lat, const sv_cut *cut, int counts[
  * sv_batch_free.  opts (may be NULL): tile_bits 0 or 10..13 (default 13); autotune = 1
  * with tile_bits 0 times tile sizes 11..13 on this batch and keeps the fastest in a JSON
  * cache (SV_AUTOTUNE_CACHE, default autotune.json beside the library); stream orders the
- * call after the caller's stream.  stats_out (may be NULL): 3 doubles per circuit,
+ * call after the caller's stream; jit 0 runs the circuits of 24 or more qubits (jit 1:
+ * of 12 or more; -1: none) on kernels compiled for their plans, each pass its own launch
+ * recorded in the same graph after the persistent one (with jit 0 and no NVRTC they join
+ * the persistent launch).  stats_out (may be NULL): 3 doubles per circuit,
  * [sum |alpha|^2, sum |alpha|^4, n_qubits].  Synchronises. */
 sv_status sv_apply_batch(const sv_lattice *circs, size_t count, const sv_options *opts,
                          double *stats_out);

@@ -1,5 +1,8 @@
 // C ABI of the uneven batch (K7): many independent lattice circuits in one persistent,
 // graph-captured launch, with the tile size picked by timing (autotune) and cached.
+// Circuits large enough to fill the device by themselves (the size from which single
+// circuits run on plan-specialised kernels) run as their own pass launches on such
+// kernels, recorded in the same graph after the persistent launch.
 #include <cuda_runtime.h>
 #include <dlfcn.h>
 
@@ -9,6 +12,7 @@
 #include <cstdlib>
 #include <cstring>
 #include <map>
+#include <memory>
 #include <mutex>
 #include <string>
 #include <vector>
@@ -16,6 +20,7 @@
 #include "../../include/sv.h"
 #include "batch.h"
 #include "capi_util.h"
+#include "jit.h"
 #include "kernels.h"
 #include "plan.h"
 #include "state.h"
@@ -44,30 +49,51 @@ struct DeviceBuf {
   }
 };
 
+// Plan-kernel circuits are dealt to this many parallel chains of launches (graph
+// branches), so that one circuit's last wave of tiles overlaps another's.  Measured on
+// the 512-circuit batch with every circuit on plan kernels: 1 branch 0.0469 s, 4 0.0414,
+// 8 0.0422, 16 0.0425, 64 0.0429.
+constexpr size_t kBranches = 4;
+
+// A circuit of the batch that runs on its plan's own kernels.
+struct JitCircuit {
+  size_t circuit = 0;
+  uint64_t state_off = 0;
+  svp::Plan P;
+  DeviceBuf plan;
+  svk::DevPlanView view{};
+  const svj::Module *M = nullptr;
+};
+
 // Everything one batch needs on the device, plus its instantiated graph.
 struct Batch {
   std::string key;
   int m = 13;
   int count = 0;
   std::vector<int> nq;
+  std::vector<std::unique_ptr<JitCircuit>> jit;
   DeviceBuf states, plan, cps, items, words, chunks, partials, chunk_begin, stats;
   svk::DevPlanView view{};
   uint64_t n_items = 0;
   int n_chunks = 0;
   size_t words_bytes = 0;
   cudaStream_t stream = nullptr;
+  std::vector<cudaStream_t> branch;  // parallel chains of the plan-kernel circuits
+  std::vector<cudaEvent_t> ev;       // fork, then one join per branch
   cudaGraphExec_t exec = nullptr;
   ~Batch() {
     if (exec) cudaGraphExecDestroy(exec);
     if (stream) cudaStreamDestroy(stream);
+    for (cudaStream_t b : branch) cudaStreamDestroy(b);
+    for (cudaEvent_t e : ev) cudaEventDestroy(e);
   }
 };
 
 std::mutex g_mu;
 Batch *g_batch = nullptr;  // the last batch (reused while the lattice list repeats)
 
-std::string batch_key(const sv_lattice *c, size_t count, int m) {
-  std::string k = "m" + std::to_string(m) + ":";
+std::string batch_key(const sv_lattice *c, size_t count, int m, int jit) {
+  std::string k = "m" + std::to_string(m) + "j" + std::to_string(jit) + ":";
   k.reserve(count * 48);
   char buf[96];
   for (size_t i = 0; i < count; ++i) {
@@ -78,11 +104,102 @@ std::string batch_key(const sv_lattice *c, size_t count, int m) {
   return k;
 }
 
+// A plan's arrays in one device buffer, as the pass kernels read them.
+sv_status upload_jit_plan(JitCircuit *J) {
+  const svp::Plan &P = J->P;
+  auto align = [](size_t x) { return (x + 255) & ~(size_t)255; };
+  const size_t o_stage = align(P.passes.size() * sizeof(svp::DevPass));
+  const size_t o_op = o_stage + align(P.stages.size() * sizeof(svp::DevStage));
+  const size_t o_gt = o_op + align(P.ops.size() * sizeof(svp::DevOp));
+  const size_t o_err = o_gt + align(P.gtab.size() * sizeof(svp::DevGroupEntry));
+  const size_t bytes = o_err + 256;
+  sv_status st = J->plan.alloc(bytes);
+  if (st != SV_OK) return st;
+  std::vector<char> hp(bytes, 0);
+  std::memcpy(hp.data(), P.passes.data(), P.passes.size() * sizeof(svp::DevPass));
+  std::memcpy(hp.data() + o_stage, P.stages.data(), P.stages.size() * sizeof(svp::DevStage));
+  std::memcpy(hp.data() + o_op, P.ops.data(), P.ops.size() * sizeof(svp::DevOp));
+  std::memcpy(hp.data() + o_gt, P.gtab.data(), P.gtab.size() * sizeof(svp::DevGroupEntry));
+  const cudaError_t e = cudaMemcpy(J->plan.p, hp.data(), bytes, cudaMemcpyHostToDevice);
+  if (e != cudaSuccess) return cuda_fail(e, "sv_apply_batch: plan upload");
+  char *d = static_cast<char *>(J->plan.p);
+  J->view.passes = reinterpret_cast<const svp::DevPass *>(d);
+  J->view.stages = reinterpret_cast<const svp::DevStage *>(d + o_stage);
+  J->view.ops = reinterpret_cast<const svp::DevOp *>(d + o_op);
+  J->view.mats = reinterpret_cast<const float *>(d + o_err);
+  J->view.err = reinterpret_cast<int *>(d + o_err);
+  J->view.gtab = reinterpret_cast<const svp::DevGroupEntry *>(d + o_gt);
+  return SV_OK;
+}
+
+// Plans and compiled kernels of the circuits that run on their own kernels (jit: the
+// options' field: 1 every circuit of at least one tile, 0 those of at least
+// kJitMinQubits, -1 none).  With
+// jit 0 and no compiler the set is left empty and those circuits join the persistent
+// launch.
+sv_status build_jit_circuits(const std::vector<std::vector<svp::Gate>> &gates, const std::vector<int> &nq,
+                             const std::vector<uint64_t> &state_off, int jit, Batch *B) {
+  B->jit.clear();
+  if (jit < 0) return SV_OK;
+  svp::Options po;
+  po.m = svj::kTileBits;
+  po.c = 4;
+  po.pack = true;
+  po.rk = svj::register_slots();
+  po.r = po.rk;
+  for (size_t i = 0; i < gates.size(); ++i) {
+    if (nq[i] < svj::kTileBits || (jit == 0 && nq[i] < kJitMinQubits)) continue;
+    std::unique_ptr<JitCircuit> J(new JitCircuit);
+    J->circuit = i;
+    J->state_off = state_off[i];
+    svp::Options pi = po;
+    pi.m = std::min(po.m, nq[i]);
+    const char *err = nullptr;
+    if (!svp::build_plan(nq[i], gates[i], pi, true, &J->P, &err)) return fail(SV_ERR_ARG, err ? err : "planning failed");
+    B->jit.push_back(std::move(J));
+  }
+  if (B->jit.empty()) return SV_OK;
+  // largest first, dealt round-robin to the branches
+  std::stable_sort(B->jit.begin(), B->jit.end(), [&](const std::unique_ptr<JitCircuit> &a,
+                                                     const std::unique_ptr<JitCircuit> &b) {
+    return nq[a->circuit] > nq[b->circuit];
+  });
+  std::vector<const svp::Plan *> plans;
+  for (auto &J : B->jit) plans.push_back(&J->P);
+  std::vector<const svj::Module *> mods;
+  std::string jerr;
+  if (!svj::get_modules(plans, po.rk, &mods, &jerr)) {
+    B->jit.clear();
+    return jit == 1 ? fail(SV_ERR_CUDA, jerr.c_str()) : SV_OK;
+  }
+  for (size_t j = 0; j < B->jit.size(); ++j) {
+    JitCircuit *J = B->jit[j].get();
+    J->M = mods[j];
+    sv_status st = upload_jit_plan(J);
+    if (st != SV_OK) return st;
+    const cudaError_t e = svj::prepare_passes(J->M, J->P);
+    if (e != cudaSuccess) return cuda_fail(e, "sv_apply_batch: plan kernels");
+  }
+  const size_t nb = std::min(B->jit.size(), kBranches);
+  for (size_t b = 0; b <= nb; ++b) {
+    cudaEvent_t e = nullptr;
+    if (cudaEventCreateWithFlags(&e, cudaEventDisableTiming) != cudaSuccess)
+      return cuda_fail(cudaGetLastError(), "sv_apply_batch: events");
+    B->ev.push_back(e);
+    if (b == nb) break;
+    cudaStream_t t = nullptr;
+    if (cudaStreamCreateWithFlags(&t, cudaStreamNonBlocking) != cudaSuccess)
+      return cuda_fail(cudaGetLastError(), "sv_apply_batch: streams");
+    B->branch.push_back(t);
+  }
+  return SV_OK;
+}
+
 // Build plans, the work queue and the device buffers of a batch with tile size m.
-sv_status build_batch(const sv_lattice *circs, size_t count, int m_req, Batch *B) {
+sv_status build_batch(const sv_lattice *circs, size_t count, int m_req, int jit, Batch *B) {
   B->count = (int)count;
   B->nq.resize(count);
-  int n_min = 64;
+  int n_min = 64;  // smallest circuit (of the persistent launch, below)
   std::vector<std::vector<svp::Gate>> gates(count);
   for (size_t i = 0; i < count; ++i) {
     const int n = lattice_qubits(circs[i]);
@@ -96,6 +213,19 @@ sv_status build_batch(const sv_lattice *circs, size_t count, int m_req, Batch *B
     if ((st = sv_generate_circuit(&circs[i], g.data(), ng, &ng)) != SV_OK) return st;
     if ((st = convert_gates(n, g.data(), ng, false, &gates[i])) != SV_OK) return st;
   }
+  std::vector<uint64_t> state_off(count);
+  uint64_t total_amps = 0;
+  for (size_t i = 0; i < count; ++i) {
+    state_off[i] = total_amps;
+    total_amps += 1ull << B->nq[i];
+  }
+  sv_status st;
+  if ((st = build_jit_circuits(gates, B->nq, state_off, jit, B)) != SV_OK) return st;
+  std::vector<char> on_jit(count, 0);
+  for (auto &J : B->jit) on_jit[J->circuit] = 1;
+  n_min = 64;
+  for (size_t i = 0; i < count; ++i)
+    if (!on_jit[i]) n_min = std::min(n_min, B->nq[i]);
   const int m = std::min(std::min(m_req, svk::tile_pass_max_bits()), n_min);
   B->m = m;
   svp::Options po;
@@ -110,9 +240,8 @@ sv_status build_batch(const sv_lattice *circs, size_t count, int m_req, Batch *B
   std::vector<svp::DevOp> ops;
   std::vector<svp::DevGroupEntry> gtab;
   std::vector<std::vector<uint32_t>> circ_passes(count);
-  std::vector<uint64_t> state_off(count);
-  uint64_t total_amps = 0;
   for (size_t i = 0; i < count; ++i) {
+    if (on_jit[i]) continue;
     svp::Plan P;
     const char *err = nullptr;
     if (!svp::build_plan(B->nq[i], gates[i], po, true, &P, &err)) return fail(SV_ERR_ARG, err ? err : "planning failed");
@@ -128,8 +257,6 @@ sv_status build_batch(const sv_lattice *circs, size_t count, int m_req, Batch *B
       circ_passes[i].push_back((uint32_t)passes.size());
       passes.push_back(dp);
     }
-    state_off[i] = total_amps;
-    total_amps += 1ull << B->nq[i];
   }
   // work queue: round r = r-th pass of every circuit that has one, larger circuits first
   std::vector<size_t> order(count);
@@ -174,7 +301,6 @@ sv_status build_batch(const sv_lattice *circs, size_t count, int m_req, Batch *B
   const size_t o_gt = o_op + align(ops.size() * sizeof(svp::DevOp));
   const size_t o_err = o_gt + align(gtab.size() * sizeof(svp::DevGroupEntry));
   const size_t plan_bytes = o_err + 256;
-  sv_status st;
   if ((st = B->states.alloc(total_amps * sizeof(float2))) != SV_OK) return st;
   if ((st = B->plan.alloc(plan_bytes)) != SV_OK) return st;
   if ((st = B->cps.alloc(std::max<size_t>(1, cps.size()) * sizeof(svk::BatchCP))) != SV_OK) return st;
@@ -208,14 +334,29 @@ sv_status build_batch(const sv_lattice *circs, size_t count, int m_req, Batch *B
   return SV_OK;
 }
 
-// Enqueue one run of the batch on stream st: reset the queue, the persistent launch,
-// the per-circuit statistics.
+// Enqueue one run of the batch on stream st: reset the queue, the persistent launch
+// (and, forked beside it, the plan-kernel circuits' pass launches on the branch
+// streams), then the per-circuit statistics.
 cudaError_t enqueue_batch(Batch *B, cudaStream_t st) {
   cudaError_t e = cudaMemsetAsync(B->words.p, 0, B->words_bytes, st);
-  if (e == cudaSuccess)
+  const size_t nb = B->branch.size();
+  if (e == cudaSuccess && nb) e = cudaEventRecord(B->ev[0], st);
+  for (size_t b = 0; e == cudaSuccess && b < nb; ++b) e = cudaStreamWaitEvent(B->branch[b], B->ev[0], 0);
+  if (e == cudaSuccess && B->n_items)
     e = svk::launch_batch(static_cast<float2 *>(B->states.p), B->view, static_cast<const svk::BatchCP *>(B->cps.p),
                           static_cast<const svk::BatchItem *>(B->items.p), B->n_items,
                           static_cast<unsigned int *>(B->words.p), B->m, st);
+  float2 *states = static_cast<float2 *>(B->states.p);
+  for (size_t j = 0; e == cudaSuccess && j < B->jit.size(); ++j) {
+    const JitCircuit &J = *B->jit[j];
+    const int n = B->nq[J.circuit];
+    for (size_t p = 0; e == cudaSuccess && p < J.P.passes.size(); ++p)
+      e = svj::launch_pass(J.M, states + J.state_off, n, J.view, (int)p, J.P.passes[p], B->branch[j % nb]);
+  }
+  for (size_t b = 0; e == cudaSuccess && b < nb; ++b) {
+    e = cudaEventRecord(B->ev[b + 1], B->branch[b]);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(st, B->ev[b + 1], 0);
+  }
   if (e == cudaSuccess)
     e = svk::launch_batch_stats(static_cast<const float2 *>(B->states.p), static_cast<const svk::BatchChunk *>(B->chunks.p),
                                 B->n_chunks, static_cast<double *>(B->partials.p),
@@ -276,23 +417,23 @@ void write_cache(const std::map<std::string, int> &c) {
   std::rename(tmp.c_str(), path.c_str());
 }
 
-std::string tune_key(const sv_lattice *circs, size_t count) {
+std::string tune_key(const sv_lattice *circs, size_t count, int jit) {
   cudaDeviceProp prop;
   int dev = 0;
   cudaGetDevice(&dev);
   cudaGetDeviceProperties(&prop, dev);
   uint64_t h = 1469598103934665603ull;  // FNV-1a over the lattice list
-  const std::string k = batch_key(circs, count, 0);
+  const std::string k = batch_key(circs, count, 0, 0);
   for (char ch : k) { h ^= (unsigned char)ch; h *= 1099511628211ull; }
   char buf[256];
-  std::snprintf(buf, sizeof(buf), "%s|batch|%zu|%016llx", prop.name, count, (unsigned long long)h);
+  std::snprintf(buf, sizeof(buf), "%s|batch|j%d|%zu|%016llx", prop.name, jit, count, (unsigned long long)h);
   for (char *p = buf; *p; ++p)
     if (*p == '"' || *p == '\\') *p = '_';
   return buf;
 }
 
-sv_status autotune_tile_bits(const sv_lattice *circs, size_t count, int *m_out) {
-  const std::string key = tune_key(circs, count);
+sv_status autotune_tile_bits(const sv_lattice *circs, size_t count, int jit, int *m_out) {
+  const std::string key = tune_key(circs, count, jit);
   std::map<std::string, int> cache = read_cache();
   auto it = cache.find(key);
   if (it != cache.end() && it->second >= 10 && it->second <= 13) { *m_out = it->second; return SV_OK; }
@@ -304,7 +445,7 @@ sv_status autotune_tile_bits(const sv_lattice *circs, size_t count, int *m_out) 
   cudaEventCreate(&b);
   for (int m : cand) {
     Batch B;
-    sv_status st = build_batch(circs, count, m, &B);
+    sv_status st = build_batch(circs, count, m, jit, &B);
     if (st != SV_OK) { cudaEventDestroy(a); cudaEventDestroy(b); return st; }
     float ms = 0;
     for (int rep = 0; rep < 2; ++rep) {  // second run is timed
@@ -339,13 +480,14 @@ extern "C" sv_status sv_apply_batch(const sv_lattice *circs, size_t count, const
   std::lock_guard<std::mutex> lock(g_mu);
   int m = o.tile_bits > 0 ? o.tile_bits : 13;
   sv_status st;
-  if (o.autotune && o.tile_bits == 0 && (st = autotune_tile_bits(circs, count, &m)) != SV_OK) return st;
-  const std::string key = batch_key(circs, count, m);
+  if (o.jit < -1 || o.jit > 1) return fail(SV_ERR_ARG, "sv_apply_batch: jit must be -1, 0 or 1");
+  if (o.autotune && o.tile_bits == 0 && (st = autotune_tile_bits(circs, count, o.jit, &m)) != SV_OK) return st;
+  const std::string key = batch_key(circs, count, m, o.jit);
   if (!g_batch || g_batch->key != key) {
     delete g_batch;
     g_batch = nullptr;
     Batch *B = new Batch();
-    if ((st = build_batch(circs, count, m, B)) != SV_OK) { delete B; return st; }
+    if ((st = build_batch(circs, count, m, o.jit, B)) != SV_OK) { delete B; return st; }
     B->key = key;
     // capture {reset, persistent launch, statistics} once; later calls replay it
     cudaError_t e = cudaStreamCreateWithFlags(&B->stream, cudaStreamNonBlocking);

@@ -48,6 +48,15 @@ struct Module;
 // nullptr with *err set if NVRTC or the module load fails.
 const Module *get_module(const svp::Plan &P, int kpr, std::string *err);
 
+// The modules of several plans at once: every pass kernel not yet cached is compiled in
+// one pool of worker threads.  false with *err set if any compile or load fails.
+bool get_modules(const std::vector<const svp::Plan *> &plans, int kpr, std::vector<const Module *> *out,
+                 std::string *err);
+
+// Set each pass kernel's shared-memory limit and occupancy now rather than at its first
+// launch (before a stream capture records the launches).
+cudaError_t prepare_passes(const Module *M, const svp::Plan &P);
+
 // Launch pass `pass` of a module on the plan's device copy.
 cudaError_t launch_pass(const Module *M, float2 *psi, int n, const svk::DevPlanView &view, int pass,
                         const svp::DevPass &hp, cudaStream_t st);

@@ -320,6 +320,32 @@ def test_batch_amplitudes_and_replay_match_oracle(tmp_path, monkeypatch):
         sv.sv_batch_amplitudes(0, [0])
 
 
+@pytest.mark.parametrize('jit', [0, 1])
+def test_batch_with_plan_kernel_circuits_matches_oracle(jit):
+    """Circuits of 24 qubits (jit 0), or all of them (jit 1), run on kernels compiled for
+    their plans inside the batch graph; the rest share the persistent launch."""
+    every = inputs.batch(512)
+    lats = every[:6] + [every[15]] + every[6:8]
+    assert lats[6].n_qubits == 24
+    try:
+        stats = sv.sv_apply_batch(lats, sv.options(jit=jit))
+    except sv.SvError as e:
+        if 'libnvrtc' in str(e):
+            pytest.skip('NVRTC not installed')
+        raise
+    for i in (0, 5, 6, 8):
+        n, gates = oracle_gates(lats[i])
+        want = csim.run(n, gates)
+        bits = inputs.bitstrings(n, 32, seed=11)
+        got = sv.sv_batch_amplitudes(i, bits)
+        assert rel_l2(got, want[np.array(bits, dtype=np.int64)]) <= REL_L2
+        s2, s4 = csim.reductions(want)
+        assert stats[i][2] == n
+        assert abs(stats[i][0] - 1) <= NORM_TOL and abs(stats[i][1] - s4) <= 1e-5 * s4
+    assert np.array_equal(stats, sv.sv_apply_batch(lats, sv.options(jit=jit)))
+    sv.sv_batch_free()
+
+
 def test_many_square_roots_in_one_stage():
     """200 X^{1/2} / Y^{1/2} gates on five qubits fall into one stage: their factors 1/2
     (deferred and applied in bulk by the tile kernels) must neither overflow nor lose
