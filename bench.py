@@ -41,7 +41,7 @@ def _peaks():
 # amplitudes; profiles/sv_pass_plain_28q_d30.md, profiles/fused_pass_kernel_f16_28q_d30.md);
 # a pass moves each amplitude once in and once out, so traffic scales with the amplitudes.
 TRAFFIC_PER_ALGORITHMIC_BYTE = {
-    'sv_pass': (2.148672e9 + 2.093911e9) / (16.0 * 2 ** 28),
+    'sv_pass': (2.147834e9 + 2.092286e9) / (16.0 * 2 ** 28),
     'fused_pass_kernel<f16>': (2.147713e9 + 2.096311e9) / (16.0 * 2 ** 28),
 }
 SMS, FP32_LANES_PER_SM = 152, 128
@@ -167,27 +167,29 @@ def run_batch(args, rank, world):
     graph-captured batch against one-at-a-time launches of the same kernels, with every
     circuit on kernels compiled for its plan (jit 1, the headline), with the default
     options (24-qubit circuits on plan kernels, the rest in the persistent launch), and
-    with the interpreting kernel only (jit -1)."""
+    with the interpreting kernel only (jit -1); timed without the per-circuit statistics
+    on both sides (one extra call checks the norms).  Also 512 small circuits (12..16
+    qubits), where one-at-a-time launches are bound by launch latency."""
     import numpy as np
     import torch
     from paper_1804_04797_gb300 import inputs, sv
     torch.cuda.set_device(int(os.environ.get('LOCAL_RANK', '0')))
-    lats = inputs.batch(512)
 
-    def graph(jit):
+    def graph(lats, jit):
         opts = sv.options(autotune=1, jit=jit)
         for _ in range(max(1, args.warmup)):
-            sv.sv_apply_batch(lats, opts)
+            sv.sv_apply_batch(lats, opts, stats=False)
         torch.cuda.synchronize()
         t0 = time.perf_counter()
         for _ in range(args.steps):
-            stats = sv.sv_apply_batch(lats, opts)
+            sv.sv_apply_batch(lats, opts, stats=False)
         torch.cuda.synchronize()
         dt = (time.perf_counter() - t0) / args.steps
+        stats = sv.sv_apply_batch(lats, opts)
         sv.sv_batch_free()
-        return dt, stats
+        return dt, float(np.max(np.abs(stats[:, 0] - 1.0)))
 
-    def sequential(jit):
+    def sequential(lats, jit):
         # one circuit at a time through sv_apply_circuit, states preallocated
         hs = [sv.sv_create(l.n_qubits, sv.options(jit=jit)) for l in lats]
         gl = [sv.sv_generate_circuit(l) for l in lats]
@@ -205,28 +207,30 @@ def run_batch(args, rank, world):
             sv.sv_destroy(h)
         return dt
 
+    def compare(lats, jit):
+        g, err = graph(lats, jit)
+        q = sequential(lats, jit)
+        return {'graph_s_per_batch': g, 'sequential_s_per_batch': q, 'speedup_vs_sequential': q / g,
+                'max_norm_err': err}
+
+    lats = inputs.batch(512)
     # every circuit on kernels compiled for its plan (the first call compiles ~3000 pass
     # kernels with NVRTC, or reads them from the on-disk cache): the headline
-    graph_s, stats = graph(1)
-    seq_s = sequential(1)
-    graph_default_s, _ = graph(0)
-    seq_default_s = sequential(0)
-    graph_interp_s, _ = graph(-1)
-    seq_interp_s = sequential(-1)
+    head = compare(lats, 1)
+    default = compare(lats, 0)
+    interp = compare(lats, -1)
+    small = compare(inputs.batch(512, n_min=12, n_max=16), 0)
     amps = sum(2 ** l.n_qubits for l in lats)
     line = {'metric': 'uneven batch circuits/s (graph-captured batch vs one-at-a-time)', 'workload': 'batch',
-            'value': len(lats) / graph_s, 'unit': 'circuits/s', 'higher_is_better': True,
+            'value': len(lats) / head['graph_s_per_batch'], 'unit': 'circuits/s', 'higher_is_better': True,
             'n_gpus': world, 'steps': args.steps, 'warmup': args.warmup,
             'config': {'workload': '512 circuits, 16..24 qubits, depth 10..24, seed 180404797',
                        'state_bytes': 8 * amps, 'options': 'jit=1 (plan kernels for every circuit), autotune=1'},
-            'graph_s_per_batch': graph_s, 'sequential_s_per_batch': seq_s,
-            'speedup_vs_sequential': seq_s / graph_s,
-            'default_options': {'graph_s_per_batch': graph_default_s, 'sequential_s_per_batch': seq_default_s,
-                                'speedup_vs_sequential': seq_default_s / graph_default_s},
-            'interpreting_kernel_only': {'graph_s_per_batch': graph_interp_s,
-                                         'sequential_s_per_batch': seq_interp_s,
-                                         'speedup_vs_sequential': seq_interp_s / graph_interp_s},
-            'max_norm_err': float(np.max(np.abs(stats[:, 0] - 1.0)))}
+            **head,
+            'default_options': default,
+            'interpreting_kernel_only': interp,
+            'small_circuits': {'workload': '512 circuits, 12..16 qubits, depth 10..24, default options '
+                                           '(all in the persistent launch)', **small}}
     if rank == 0:
         print(json.dumps(line), flush=True)
     return 0

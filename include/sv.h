@@ -229,8 +229,9 @@ sv_status sv_branch_counts(const sv_lattice *lat, const sv_cut *cut, int counts[
  * call after the caller's stream; jit 0 runs the circuits of 24 or more qubits (jit 1:
  * of 12 or more; -1: none) on kernels compiled for their plans, each pass its own launch
  * recorded in the same graph after the persistent one (with jit 0 and no NVRTC they join
- * the persistent launch).  stats_out (may be NULL): 3 doubles per circuit,
- * [sum |alpha|^2, sum |alpha|^4, n_qubits].  Synchronises. */
+ * the persistent launch).  stats_out: 3 doubles per circuit, [sum |alpha|^2,
+ * sum |alpha|^4, n_qubits]; NULL skips the statistics (a second graph, without the
+ * reduction over all states, is captured for such calls).  Synchronises. */
 sv_status sv_apply_batch(const sv_lattice *circs, size_t count, const sv_options *opts,
                          double *stats_out);
 

@@ -80,9 +80,10 @@ struct Batch {
   cudaStream_t stream = nullptr;
   std::vector<cudaStream_t> branch;  // parallel chains of the plan-kernel circuits
   std::vector<cudaEvent_t> ev;       // fork, then one join per branch
-  cudaGraphExec_t exec = nullptr;
+  cudaGraphExec_t exec[2] = {nullptr, nullptr};  // without, with the statistics
   ~Batch() {
-    if (exec) cudaGraphExecDestroy(exec);
+    for (cudaGraphExec_t x : exec)
+      if (x) cudaGraphExecDestroy(x);
     if (stream) cudaStreamDestroy(stream);
     for (cudaStream_t b : branch) cudaStreamDestroy(b);
     for (cudaEvent_t e : ev) cudaEventDestroy(e);
@@ -336,8 +337,8 @@ sv_status build_batch(const sv_lattice *circs, size_t count, int m_req, int jit,
 
 // Enqueue one run of the batch on stream st: reset the queue, the persistent launch
 // (and, forked beside it, the plan-kernel circuits' pass launches on the branch
-// streams), then the per-circuit statistics.
-cudaError_t enqueue_batch(Batch *B, cudaStream_t st) {
+// streams), then (with_stats) the per-circuit statistics.
+cudaError_t enqueue_batch(Batch *B, cudaStream_t st, bool with_stats) {
   cudaError_t e = cudaMemsetAsync(B->words.p, 0, B->words_bytes, st);
   const size_t nb = B->branch.size();
   if (e == cudaSuccess && nb) e = cudaEventRecord(B->ev[0], st);
@@ -357,7 +358,7 @@ cudaError_t enqueue_batch(Batch *B, cudaStream_t st) {
     e = cudaEventRecord(B->ev[b + 1], B->branch[b]);
     if (e == cudaSuccess) e = cudaStreamWaitEvent(st, B->ev[b + 1], 0);
   }
-  if (e == cudaSuccess)
+  if (e == cudaSuccess && with_stats)
     e = svk::launch_batch_stats(static_cast<const float2 *>(B->states.p), static_cast<const svk::BatchChunk *>(B->chunks.p),
                                 B->n_chunks, static_cast<double *>(B->partials.p),
                                 static_cast<const int *>(B->chunk_begin.p), B->count, static_cast<double *>(B->stats.p), st);
@@ -450,7 +451,7 @@ sv_status autotune_tile_bits(const sv_lattice *circs, size_t count, int jit, int
     float ms = 0;
     for (int rep = 0; rep < 2; ++rep) {  // second run is timed
       cudaEventRecord(a, 0);
-      cudaError_t e = enqueue_batch(&B, 0);
+      cudaError_t e = enqueue_batch(&B, 0, false);
       cudaEventRecord(b, 0);
       if (e == cudaSuccess) e = cudaEventSynchronize(b);
       if (e != cudaSuccess) { cudaEventDestroy(a); cudaEventDestroy(b); return cuda_fail(e, "sv_apply_batch: autotune"); }
@@ -489,31 +490,40 @@ extern "C" sv_status sv_apply_batch(const sv_lattice *circs, size_t count, const
     Batch *B = new Batch();
     if ((st = build_batch(circs, count, m, o.jit, B)) != SV_OK) { delete B; return st; }
     B->key = key;
-    // capture {reset, persistent launch, statistics} once; later calls replay it
-    cudaError_t e = cudaStreamCreateWithFlags(&B->stream, cudaStreamNonBlocking);
-    cudaGraph_t graph = nullptr;
-    if (e == cudaSuccess) e = cudaStreamBeginCapture(B->stream, cudaStreamCaptureModeThreadLocal);
-    if (e == cudaSuccess) {
-      cudaError_t e2 = enqueue_batch(B, B->stream);
-      e = cudaStreamEndCapture(B->stream, &graph);
-      if (e2 != cudaSuccess) e = e2;
-    }
-    if (e == cudaSuccess) e = cudaGraphInstantiate(&B->exec, graph, 0);
-    if (graph) cudaGraphDestroy(graph);
-    if (e != cudaSuccess) { delete B; return cuda_fail(e, "sv_apply_batch: graph capture"); }
+    const cudaError_t e = cudaStreamCreateWithFlags(&B->stream, cudaStreamNonBlocking);
+    if (e != cudaSuccess) { delete B; return cuda_fail(e, "sv_apply_batch: stream"); }
     g_batch = B;
   }
   Batch *B = g_batch;
+  const int with_stats = stats_out ? 1 : 0;
+  if (!B->exec[with_stats]) {
+    // capture {reset, launches, statistics if asked for} once; later calls replay it
+    cudaGraph_t graph = nullptr;
+    cudaError_t e = cudaStreamBeginCapture(B->stream, cudaStreamCaptureModeThreadLocal);
+    if (e == cudaSuccess) {
+      cudaError_t e2 = enqueue_batch(B, B->stream, with_stats != 0);
+      e = cudaStreamEndCapture(B->stream, &graph);
+      if (e2 != cudaSuccess) e = e2;
+    }
+    if (e == cudaSuccess) e = cudaGraphInstantiate(&B->exec[with_stats], graph, 0);
+    if (graph) cudaGraphDestroy(graph);
+    if (e != cudaSuccess) {
+      delete B;
+      g_batch = nullptr;
+      return cuda_fail(e, "sv_apply_batch: graph capture");
+    }
+  }
   cudaStream_t user = static_cast<cudaStream_t>(o.stream);
   cudaEvent_t ev;
   cudaError_t e = cudaEventCreateWithFlags(&ev, cudaEventDisableTiming);
   // order the graph after the caller's stream, run it, then order the caller after it
   if (e == cudaSuccess) e = cudaEventRecord(ev, user);
   if (e == cudaSuccess) e = cudaStreamWaitEvent(B->stream, ev, 0);
-  if (e == cudaSuccess) e = cudaGraphLaunch(B->exec, B->stream);
+  if (e == cudaSuccess) e = cudaGraphLaunch(B->exec[with_stats], B->stream);
   std::vector<double> st2(2 * count);
   unsigned int hw[2] = {0, 0};
-  if (e == cudaSuccess) e = cudaMemcpyAsync(st2.data(), B->stats.p, 2 * count * sizeof(double), cudaMemcpyDeviceToHost, B->stream);
+  if (e == cudaSuccess && with_stats)
+    e = cudaMemcpyAsync(st2.data(), B->stats.p, 2 * count * sizeof(double), cudaMemcpyDeviceToHost, B->stream);
   if (e == cudaSuccess) e = cudaMemcpyAsync(hw, B->words.p, sizeof(hw), cudaMemcpyDeviceToHost, B->stream);
   if (e == cudaSuccess) e = cudaStreamSynchronize(B->stream);
   cudaEventDestroy(ev);

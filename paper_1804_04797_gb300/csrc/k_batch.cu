@@ -99,13 +99,34 @@ __device__ __forceinline__ double warp_sum(double x) {
 __global__ void batch_stats_partial(const float2 *__restrict__ states, const BatchChunk *__restrict__ chunks,
                                     double *partials) {
   const BatchChunk ch = chunks[blockIdx.x];
-  const float2 *p = states + ch.start;
+  // two amplitudes per 16-byte load: chunk starts and lengths are even (every circuit
+  // has at least 2^6 amplitudes, chunks are 2^16); eight probabilities are added in
+  // fp32, then into the fp64 sums (fp64 per element is the slow part on this GPU)
+  const float4 *p = reinterpret_cast<const float4 *>(states + ch.start);
+  const uint32_t n4 = ch.len >> 1, stride = blockDim.x;
   double s2 = 0, s4 = 0;
-  for (uint32_t i = threadIdx.x; i < ch.len; i += blockDim.x) {
-    const float2 z = p[i];
-    const float q = fmaf(z.x, z.x, z.y * z.y);
-    s2 += q;
-    s4 += (double)q * q;
+  uint32_t i = threadIdx.x;
+  for (; i + 3 * stride < n4; i += 4 * stride) {
+    float4 z[4];
+#pragma unroll
+    for (int k = 0; k < 4; ++k) z[k] = p[i + k * stride];
+    float a2 = 0.f, a4 = 0.f;
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+      const float p0 = fmaf(z[k].x, z[k].x, z[k].y * z[k].y);
+      const float p1 = fmaf(z[k].z, z[k].z, z[k].w * z[k].w);
+      a2 += p0 + p1;
+      a4 = fmaf(p0, p0, fmaf(p1, p1, a4));
+    }
+    s2 += a2;
+    s4 += a4;
+  }
+  for (; i < n4; i += stride) {
+    const float4 z = p[i];
+    const float p0 = fmaf(z.x, z.x, z.y * z.y);
+    const float p1 = fmaf(z.z, z.z, z.w * z.w);
+    s2 += (double)(p0 + p1);
+    s4 += (double)fmaf(p0, p0, p1 * p1);
   }
   __shared__ double r2[8], r4[8];
   s2 = warp_sum(s2);

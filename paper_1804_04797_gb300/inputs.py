@@ -64,7 +64,7 @@ def lattice_for(n_rows, n_cols, depth, seed=0, removed=()):
 
 
 def batch_lattice(n, depth, seed):
-    """Uneven-batch lattice for n qubits (16..24): 4 rows x ceil(n/4) columns, all sites
+    """Uneven-batch lattice for n qubits (8..28): 4 rows x ceil(n/4) columns, all sites
     of the first floor(n/4) columns plus the first (n mod 4) rows of the last column."""
     cols = (n + 3) // 4
     full, extra = n // 4, n % 4
@@ -76,13 +76,14 @@ def batch_lattice(n, depth, seed):
     return Lattice(4, cols, mask, depth, seed)
 
 
-def batch(count=512, seed=BATCH_SEED):
-    """The uneven batch: n uniform in 16..24, depth uniform in 10..24 (n drawn first,
-    then depth, from one SplitMix64(seed)); circuit i uses generator seed seed + i."""
+def batch(count=512, seed=BATCH_SEED, n_min=16, n_max=24):
+    """The uneven batch: n uniform in n_min..n_max (16..24), depth uniform in 10..24 (n
+    drawn first, then depth, from one SplitMix64(seed)); circuit i uses generator seed
+    seed + i."""
     g = _splitmix(seed)
     out = []
     for i in range(count):
-        n = 16 + next(g) % 9
+        n = n_min + next(g) % (n_max - n_min + 1)
         d = 10 + next(g) % 15
         out.append(batch_lattice(n, d, seed + i))
     return out

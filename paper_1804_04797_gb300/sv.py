@@ -255,12 +255,15 @@ def sv_branch_counts(lat, half_a_mask, full_decomposition=False):
     return tuple(int(v) for v in out)
 
 
-def sv_apply_batch(lats, opts=None):
+def sv_apply_batch(lats, opts=None, stats=True):
+    """Run the batch; per-circuit [sum p, sum p^2, n] rows, or None with stats=False (the
+    reduction is then skipped)."""
     arr = (sv_lattice * len(lats))(*[x if isinstance(x, sv_lattice) else lattice(x) for x in lats])
-    stats = np.zeros(3 * len(lats), dtype=np.float64)
+    out = np.zeros(3 * len(lats), dtype=np.float64) if stats else None
     _check(lib().sv_apply_batch(ctypes.cast(arr, c_void_p), len(lats),
-                                ctypes.byref(opts) if opts is not None else None, stats.ctypes.data))
-    return stats.reshape(len(lats), 3)
+                                ctypes.byref(opts) if opts is not None else None,
+                                out.ctypes.data if stats else None))
+    return out.reshape(len(lats), 3) if stats else None
 
 
 def sv_batch_amplitudes(circuit, bits):

@@ -343,6 +343,12 @@ def test_batch_with_plan_kernel_circuits_matches_oracle(jit):
         assert stats[i][2] == n
         assert abs(stats[i][0] - 1) <= NORM_TOL and abs(stats[i][1] - s4) <= 1e-5 * s4
     assert np.array_equal(stats, sv.sv_apply_batch(lats, sv.options(jit=jit)))
+    # without statistics: another graph, the same states
+    before = [sv.sv_batch_amplitudes(i, inputs.bitstrings(lats[i].n_qubits, 16, seed=3)) for i in (1, 6)]
+    assert sv.sv_apply_batch(lats, sv.options(jit=jit), stats=False) is None
+    after = [sv.sv_batch_amplitudes(i, inputs.bitstrings(lats[i].n_qubits, 16, seed=3)) for i in (1, 6)]
+    for x, y in zip(before, after):
+        assert np.array_equal(x, y)
     sv.sv_batch_free()
 
 

@@ -61,6 +61,11 @@ def test_generator_batch_lattices():
         n_o, g_o = oc.generate(lat.rows, lat.cols, lat.removed_mask, lat.depth, lat.seed)
         assert 16 <= n_o <= 24 and 10 <= lat.depth <= 24
         assert _lib_gates(lat) == g_o
+    small = inputs.batch(64, n_min=12, n_max=16)
+    assert {lat.n_qubits for lat in small} == set(range(12, 17))
+    for lat in small[:16]:
+        n_o, g_o = oc.generate(lat.rows, lat.cols, lat.removed_mask, lat.depth, lat.seed)
+        assert n_o == lat.n_qubits and _lib_gates(lat) == g_o
 
 
 def test_generator_rejects_bad_lattices():
