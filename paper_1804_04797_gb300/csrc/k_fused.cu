@@ -139,8 +139,9 @@ __device__ __forceinline__ float tf32_rn(float x) {
   return __uint_as_float((__float_as_uint(x) + 0x1000u) & 0xFFFFE000u);
 }
 
-__device__ __forceinline__ uint32_t pack_h2(float a, float b) {
-  return (uint32_t)__half_as_ushort(__float2half_rn(a)) | ((uint32_t)__half_as_ushort(__float2half_rn(b)) << 16);
+// The 32 bits of a half2 (x in the low half).
+__device__ __forceinline__ uint32_t half2_bits(__half2 h) {
+  return (uint32_t)__half_as_ushort(__low2half(h)) | ((uint32_t)__half_as_ushort(__high2half(h)) << 16);
 }
 
 // TMEM columns: A_hi at [kAcols mb, +kAcols), A_lo at [kAcols (MB + mb), +kAcols),
@@ -169,21 +170,17 @@ __device__ __forceinline__ void issue_b_load(const float *mats, const DevStage &
                :: "r"(dst + kB), "l"(src + kB), "r"(kB), "r"(bar) : "memory");
 }
 
-// Sum over the CTA of one double per thread, fixed order; red holds one slot per warp
-// plus the result.  Every thread returns the total.
-__device__ __forceinline__ double cta_sum(double d, double *red) {
-  const int tid = threadIdx.x, nthreads = blockDim.x;
+// Sum over the warp of one double per thread; lane 0 writes it to slot[warp] (the CTA
+// total is then read by every thread, in a fixed order, after a barrier).
+__device__ __forceinline__ void warp_sum_to(double d, double *slot) {
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) d += __shfl_xor_sync(0xffffffffu, d, o);
-  if ((tid & 31) == 0) red[1 + (tid >> 5)] = d;
-  __syncthreads();
-  if (tid == 0) {
-    double t = 0.0;
-    for (int w = 0; w < nthreads / 32; ++w) t += red[1 + w];
-    red[0] = t;
-  }
-  __syncthreads();
-  return red[0];
+  if ((threadIdx.x & 31) == 0) slot[threadIdx.x >> 5] = d;
+}
+__device__ __forceinline__ double slots_sum(const double *slot) {
+  double t = 0.0;
+  for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += slot[w];
+  return t;
 }
 
 __device__ __forceinline__ float row_norm2(const float2 (&v)[kE]) {
@@ -251,10 +248,12 @@ __device__ __forceinline__ int store_a(const float2 (&v)[kE], uint32_t taddr_hi,
 #pragma unroll
       for (int e = 0; e < 16; ++e) {  // amplitude 16h+e -> column 16h+e (re low half, im high)
         const float2 z = v[16 * h + e];
-        const float xr = z.x * sc, xi = z.y * sc;
-        const float hr = __half2float(__float2half_rn(xr)), hi = __half2float(__float2half_rn(xi));
-        rh[e] = pack_h2(hr, hi);
-        rl[e] = pack_h2(xr - hr, xi - hi);
+        const float2 x = make_float2(z.x * sc, z.y * sc);
+        const __half2 h2 = __float22half2_rn(x);  // both parts in one conversion
+        const float2 hf = __half22float2(h2);
+        const __half2 l2 = __float22half2_rn(make_float2(x.x - hf.x, x.y - hf.y));
+        rh[e] = half2_bits(h2);
+        rl[e] = half2_bits(l2);
       }
       SV_TMEM_ST16(taddr_hi + 16 * h, rh);
       SV_TMEM_ST16(taddr_lo + 16 * h, rl);
@@ -280,7 +279,7 @@ fused_pass_kernel(float2 *__restrict__ psi, DevPlanView plan, int pass_index, ui
   __shared__ int abort_flag;
   __shared__ int16_t mma_list[256];
   __shared__ int n_mma;
-  __shared__ double red[1 + 8];
+  __shared__ double norm_in[8], norm_out[8];  // per-warp sums of the tile norm
 
   const int tid = threadIdx.x, warp = tid >> 5;
   if (tid == 0) {
@@ -332,7 +331,6 @@ fused_pass_kernel(float2 *__restrict__ psi, DevPlanView plan, int pass_index, ui
     // the tile's norm is measured in the first stage and restored in the last one with
     // unbiased stochastic rounding.
     const bool keep_norm = (P.flags & svp::PF_UNITARY) && n_mma > 0;
-    double norm_in = 0.0;
     int q = 0;  // MMA stage index within this tile
     for (int s = 0; s < P.stage_count; ++s) {
       const uint32_t si = P.stage_begin + s;
@@ -342,7 +340,8 @@ fused_pass_kernel(float2 *__restrict__ psi, DevPlanView plan, int pass_index, ui
       group_base(plan, si, tid, base, &L0, &G0);
       float2 v[kE];
       load_group(tile, st, L0, v);
-      if (keep_norm && s == 0) norm_in = cta_sum((double)row_norm2(v), red);
+      // (read after the last stage's barrier; the stage barriers between keep it stable)
+      if (keep_norm && s == 0) warp_sum_to((double)row_norm2(v), norm_in);
       if (!st.diag_only) {
         const int buf = qglob & 1;
         // prefetch the next MMA stage's B into the other buffer (its last reader, the
@@ -389,18 +388,18 @@ fused_pass_kernel(float2 *__restrict__ psi, DevPlanView plan, int pass_index, ui
             mma_out = true;
           }
         }
-        __syncthreads();
-        if (abort_flag) break;
-        if (!mbar_wait(bar_mma, mma_phase)) {
+        // every thread waits for the MMAs (bounded; if the B wait above gave up nothing
+        // was committed and the others give up too); a warp reads tensor memory only if
+        // all its lanes saw the MMAs complete (the loads are warp-wide)
+        const bool done = __all_sync(0xffffffffu, !(tid == 0 && abort_flag) && mbar_wait(bar_mma, mma_phase));
+        mma_phase ^= 1;
+        if (tid == 0 && done) mma_out = false;
+        if (!done) {
           atomicExch(err, 2);
           abort_flag = 1;
         }
-        mma_phase ^= 1;
-        if (tid == 0) mma_out = false;
-        __syncthreads();  // every thread sees the same abort_flag before the warp-wide loads
-        if (abort_flag) break;
         asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-        {
+        if (done) {
           // F16: undo the row scale and the 2^8 of B (exact powers of two)
           const float un = F16 ? __uint_as_float((uint32_t)(127 + 127 - kF16BExp - sexp) << 23) : 1.0f;
 #pragma unroll
@@ -425,9 +424,11 @@ fused_pass_kernel(float2 *__restrict__ psi, DevPlanView plan, int pass_index, ui
       }
       apply_ops(v, plan.ops, st.op_begin, st.op_count, G0, plan.mats);
       if (keep_norm && s == P.stage_count - 1) {
-        const double norm_out = cta_sum((double)row_norm2(v), red);
-        if (norm_out > 0.0) {
-          const float delta = (float)(sqrt(norm_in / norm_out) - 1.0);
+        warp_sum_to((double)row_norm2(v), norm_out);
+        __syncthreads();
+        const double n_in = slots_sum(norm_in), n_out = slots_sum(norm_out);
+        if (n_out > 0.0) {
+          const float delta = (float)(sqrt(n_in / n_out) - 1.0);
           const uint32_t seed = (uint32_t)base * 0x85EBCA6Bu + (uint32_t)(base >> 32) * 0xC2B2AE35u +
                                 (uint32_t)pass_index * 0x27D4EB2Fu + (uint32_t)tid * 0x165667B1u;
           scale_row(v, delta, seed);
