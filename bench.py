@@ -8,7 +8,8 @@ no flush is needed between steps.
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
 
 For N > 1 (torchrun, one rank per GPU) every rank simulates its own replica of the
-circuit (the simulation does not shard) and value = N circuits / max time.
+circuit (the state-vector simulation does not shard: one 34-qubit state fills one GPU)
+and value = N circuits / the slowest rank's time.
 --impl reference times the CPU oracle (the only reference this method has) on a bounded
 sample of the same workload on the host cores.
 """
@@ -25,6 +26,23 @@ sys.path.insert(0, ROOT)
 
 METRIC = '34q depth-30 s/circuit & %HBM roofline; fused-TC vs plain at rel-L2≤1e-5'
 UNIT = 's/circuit'
+
+
+def max_over_ranks(values, dist, device):
+    """Each value's maximum over the ranks (every rank gets the same list): timings are
+    the slowest rank's.  dist None: a single process."""
+    if dist is None:
+        return [float(v) for v in values]
+    import torch
+    t = torch.tensor([float(v) for v in values], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return [float(v) for v in t]
+
+
+def whole_job_s_per_circuit(slowest_s_per_circuit, world):
+    """N replicas each simulate one circuit per step and the step ends with the slowest:
+    N circuits per slowest time, i.e. the slowest time / N seconds per circuit."""
+    return slowest_s_per_circuit / world
 
 
 def _peaks():
@@ -401,10 +419,7 @@ def main():
         ms = ev0.elapsed_time(ev1)
         prof = sv.sv_get_profile(h)
         sv.sv_set_profiling(h, False)
-        if dist is not None:
-            t = torch.tensor([ms, wall], device='cuda')
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            ms, wall = float(t[0]), float(t[1])
+        ms, wall = max_over_ranks([ms, wall], dist, 'cuda')
         return ms, wall, prof, ck.summary()
 
     def step_device(h):
@@ -469,7 +484,7 @@ def main():
     ok = [k for k, r in results.items() if 's_per_circuit' in r and r.get('rel_l2_vs_plain_64amps', 1.0) <= 1e-5]
     best_name = min(ok, key=lambda k: results[k]['s_per_circuit'])
     best = results[best_name]
-    value = best['s_per_circuit'] / world
+    value = whole_job_s_per_circuit(best['s_per_circuit'], world)
     cpu = None
     if not args.no_cpu:
         v, dt, cores, desc = _oracle_sample()

@@ -1,0 +1,49 @@
+"""The multi-rank arithmetic of bench.py on CPU (gloo, world size 2): timings are the
+slowest rank's, and N replicas of one circuit each make N circuits per that time.  The
+GPU path differs only in the tensors' device (NCCL)."""
+import os
+import socket
+
+import pytest
+
+import bench
+
+
+def _free_port():
+    with socket.socket() as s:
+        s.bind(('127.0.0.1', 0))
+        return s.getsockname()[1]
+
+
+def _worker(rank, world, port, q):
+    import torch.distributed as dist
+    os.environ['MASTER_ADDR'] = '127.0.0.1'
+    os.environ['MASTER_PORT'] = str(port)
+    dist.init_process_group('gloo', rank=rank, world_size=world)
+    try:
+        # rank r took (1 + r) ms on the device and (5 - r) s of wall time
+        got = bench.max_over_ranks([1.0 + rank, 5.0 - rank], dist, 'cpu')
+        q.put((rank, got))
+    finally:
+        dist.destroy_process_group()
+
+
+def test_max_over_ranks_two_gloo_ranks():
+    import torch.multiprocessing as mp
+    ctx = mp.get_context('spawn')
+    q = ctx.Queue()
+    port = _free_port()
+    procs = [ctx.Process(target=_worker, args=(r, 2, port, q)) for r in range(2)]
+    for p in procs:
+        p.start()
+    out = dict(q.get(timeout=120) for _ in procs)
+    for p in procs:
+        p.join(timeout=60)
+        assert p.exitcode == 0
+    assert out == {0: [2.0, 5.0], 1: [2.0, 5.0]}
+
+
+def test_single_process_and_replica_value():
+    assert bench.max_over_ranks([0.5, 7], None, 'cpu') == [0.5, 7.0]
+    assert bench.whole_job_s_per_circuit(0.66, 1) == 0.66
+    assert bench.whole_job_s_per_circuit(0.66, 4) == pytest.approx(0.165)
