@@ -436,6 +436,9 @@ __device__ __forceinline__ void store_group(float4 *tile, const DevPlanView &pla
 
 // The same with the register-slot masks given (the kernels compiled for one plan pass
 // them as constants).
+// kCopied: the tile is still as the asynchronous copies left it, pairs as
+// (re, im, re', im') (the first stage of a pass that read its tile; see finish_tile_load).
+template <bool kCopied = false>
 __device__ __forceinline__ void load_group_rx(const float4 *tile, uint32_t a0, const uint32_t (&rx)[kPR], Regs &R,
                                               Regs &I) {
   const char *tb = reinterpret_cast<const char *>(tile);
@@ -446,8 +449,8 @@ __device__ __forceinline__ void load_group_rx(const float4 *tile, uint32_t a0, c
     for (int j = 0; j < kPR; ++j)
       if ((p >> j) & 1) a ^= rx[j];
     const float4 x = *reinterpret_cast<const float4 *>(tb + a);
-    R[p] = f2(x.x, x.y);
-    I[p] = f2(x.z, x.w);
+    R[p] = kCopied ? f2(x.x, x.z) : f2(x.x, x.y);
+    I[p] = kCopied ? f2(x.y, x.w) : f2(x.z, x.w);
   }
 }
 __device__ __forceinline__ void store_group_rx(float4 *tile, uint32_t a0, const uint32_t (&rx)[kPR], const Regs &R,
@@ -498,6 +501,11 @@ __device__ __forceinline__ void build_chunk_table(const DevPass &P, uint64_t *ch
 // in memory, (re, im, re', im'), one commit group.  L2 is coherent, so the copies also see
 // data that other CTAs of the same launch wrote.  finish_tile_load() waits for the
 // thread's own copies and regroups them (each thread touches only its own slots).
+// The plan-specialised kernels call finish_tile_copy() instead: it only waits, and their
+// first stage reads the pairs in the copied order (load_group_rx<true>) and stores them
+// regrouped, so the tile needs no regroup sweep (34 qubits: 0.667 -> 0.638 s).  In the
+// interpreting kernel the same change measured slower (its stage loop then holds two
+// copies of the group load).
 // (tid, T): this thread's index among the T threads that share the tile.
 __device__ __forceinline__ void load_tile_async(const float2 *__restrict__ psi, float4 *tile, const DevPass &P,
                                                 const uint64_t *chunk_off, uint64_t base, uint32_t tid, uint32_t T) {
@@ -556,6 +564,11 @@ __device__ __forceinline__ void load_tile_async(const float2 *__restrict__ psi, 
   load_tile_async(psi, tile, P, chunk_off, base, threadIdx.x, blockDim.x);
 }
 __device__ __forceinline__ void finish_tile_load(float4 *tile) { finish_tile_load(tile, threadIdx.x, blockDim.x); }
+// Wait only (a pass without stages still regroups, for store_tile).
+__device__ __forceinline__ void finish_tile_copy(float4 *tile, const DevPass &P) {
+  if (P.stage_count == 0) finish_tile_load(tile);
+  else asm volatile("cp.async.wait_group 0;" ::: "memory");
+}
 __device__ __forceinline__ void store_tile(float2 *__restrict__ psi, const float4 *tile, const DevPass &P,
                                            const uint64_t *chunk_off, uint64_t base) {
   store_tile(psi, tile, P, chunk_off, base, threadIdx.x, blockDim.x);
