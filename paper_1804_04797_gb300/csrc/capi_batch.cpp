@@ -426,7 +426,7 @@ std::string tune_key(const sv_lattice *circs, size_t count, int jit) {
   uint64_t h = 1469598103934665603ull;  // FNV-1a over the lattice list
   const std::string k = batch_key(circs, count, 0, 0);
   for (char ch : k) { h ^= (unsigned char)ch; h *= 1099511628211ull; }
-  char buf[256];
+  char buf[sizeof(prop.name) + 64];
   std::snprintf(buf, sizeof(buf), "%s|batch|j%d|%zu|%016llx", prop.name, jit, count, (unsigned long long)h);
   for (char *p = buf; *p; ++p)
     if (*p == '"' || *p == '\\') *p = '_';

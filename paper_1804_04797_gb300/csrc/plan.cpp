@@ -487,8 +487,6 @@ bool build_plan(int n, const std::vector<Gate> &gates, const Options &opt, bool 
     first_pass = false;
     if (P.passes.size() > 100000) { *err = "planner did not converge"; return false; }
   }
-  for (const DevStage &ds : P.stages)
-    if (ds.op_count > 65535) { *err = "plan too large"; return false; }
   // a no-op past the last op: kernels may load the op after a stage's last one
   DevOp end;
   std::memset(&end, 0, sizeof(end));
@@ -503,7 +501,7 @@ void stage_unitary(const Plan &P, const std::vector<Gate> &gates, int stage, int
   const DevStage &ds = P.stages[stage];
   const DevPass *pass = nullptr;
   for (const DevPass &p : P.passes)
-    if (stage >= p.stage_begin && stage < p.stage_begin + p.stage_count) pass = &p;
+    if (stage >= (int)p.stage_begin && stage < (int)(p.stage_begin + p.stage_count)) pass = &p;
   const int d = 1 << r;
   u->assign((size_t)2 * d * d, 0.0);
   for (int i = 0; i < d; ++i) (*u)[2 * ((size_t)i * d + i)] = 1.0;
