@@ -456,7 +456,7 @@ def main():
                 'kernel_ms': prof.ms, 'kernel_bytes': prof.hbm_bytes, 'per_launch_ms': per_launch_ms,
                 'bytes_per_launch': bytes_per_launch, 'achieved_gbs': bytes_per_launch / (per_launch_ms * 1e-3) / 1e9,
                 'norm_err': abs(norm2 - 1.0), 'n_sum_p2': (2.0 ** n) * sp2, 'rel_l2_vs_plain_64amps': agree,
-                'clocks': clocks, 'launches_per_step': prof.launches / args.steps,
+                'clocks': clocks, 'launches_per_step': (prof.launches + prof.other_launches) / args.steps,
                 'plan_kernel_launches': prof.jit_launches,
             }
 

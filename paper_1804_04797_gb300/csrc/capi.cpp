@@ -258,16 +258,35 @@ sv_status upload_plan(sv_state *s, const svp::Plan &P, svk::DevPlanView *view) {
 sv_status run_plan(sv_state *s, const svp::Plan &P, const svk::DevPlanView &view, bool fused, bool f16,
                    const svj::Module *jit) {
   const double amps = std::ldexp(1.0, s->n);
+  s->sums_valid = false;
+  // plan kernels: the last pass also sums p and p^2 of the state it writes (no separate
+  // read of the state for sv_norm)
+  const bool sums = jit && s->owns && !s->user_writes && !P.passes.empty();
+  if (sums && !s->d_sums) {
+    if (cudaMalloc(&s->d_sums, (2 + 2 * (size_t)svj::max_pass_grid()) * sizeof(double)) != cudaSuccess) {
+      cudaGetLastError();
+      s->d_sums = nullptr;
+      return fail(SV_ERR_OOM, "norm sums buffer allocation failed");
+    }
+  }
+  unsigned grid = 0;
   for (size_t p = 0; p < P.passes.size(); ++p) {
     const svp::DevPass &hp = P.passes[p];
     const double bytes = (hp.flags & (svp::PF_INIT_UNIFORM | svp::PF_INIT_ZERO)) ? 8.0 * amps : 16.0 * amps;
+    double *partials = sums && p + 1 == P.passes.size() ? s->d_sums + 2 : nullptr;
     prof_begin(s);
     cudaError_t e = fused ? svk::launch_fused_pass(s->psi, s->n, view, (int)p, hp, s->stream, f16)
-                    : jit ? svj::launch_pass(jit, s->psi, s->n, view, (int)p, hp, s->stream)
+                    : jit ? svj::launch_pass(jit, s->psi, s->n, view, (int)p, hp, s->stream, partials, &grid)
                           : svk::launch_tile_pass(s->psi, s->n, view, (int)p, hp, s->stream);
     prof_end(s, bytes);
     if (jit && s->prof) s->jit_launches += 1;
     if (e != cudaSuccess) { s->broken = true; return cuda_fail(e, "tile pass kernel"); }
+  }
+  if (sums) {
+    const cudaError_t e = svk::launch_norm_final(s->d_sums + 2, (int)grid, s->d_sums, s->stream);
+    if (e != cudaSuccess) { s->broken = true; return cuda_fail(e, "norm sums"); }
+    if (s->prof) s->other_launches += 1;
+    s->sums_valid = true;
   }
   return SV_OK;
 }
@@ -299,6 +318,7 @@ sv_status check_fused_error(sv_state *s, const svk::DevPlanView &view) {
 sv_status apply_gates(sv_state *s, const std::vector<svp::Gate> &g) {
   sv_status st;
   if ((st = set_device(s)) != SV_OK) return st;
+  s->sums_valid = false;
   if (s->opts.precision == SV_PREC_PERGATE || s->n < 6) return apply_pergate(s, g);
   if ((s->opts.precision == SV_PREC_TF32X3 || s->opts.precision == SV_PREC_F16X3) && !svk::fused_supported())
     return fail(SV_ERR_CUDA, "fused tensor-core path needs an sm_103a device");
@@ -438,6 +458,7 @@ sv_status sv_destroy(sv_state *s) {
   if (s->owns && s->psi) cudaFree(s->psi);
   if (s->d_plan) cudaFree(s->d_plan);
   if (s->d_scratch) cudaFree(s->d_scratch);
+  if (s->d_sums) cudaFree(s->d_sums);
   for (cudaEvent_t ev : s->events) cudaEventDestroy(ev);
   delete s;
   return SV_OK;
@@ -457,6 +478,7 @@ sv_status sv_reset(sv_state *s) {
   clear_error();
   if (!s) return fail(SV_ERR_ARG, "sv_reset: NULL state");
   s->fresh = true;
+  s->sums_valid = false;
   s->broken = false;
   return SV_OK;
 }
@@ -468,6 +490,8 @@ sv_status sv_device_ptr(sv_state *s, void **ptr) {
   if (st != SV_OK) return st;
   if ((st = materialize(s)) != SV_OK) return st;
   *ptr = s->psi;
+  s->user_writes = true;  // the caller may write the state from now on
+  s->sums_valid = false;
   return SV_OK;
 }
 
@@ -489,6 +513,7 @@ sv_status sv_load_state(sv_state *s, const void *src) {
   if (!s || !src) return fail(SV_ERR_ARG, "sv_load_state: NULL argument");
   sv_status st = set_device(s);
   if (st != SV_OK) return st;
+  s->sums_valid = false;
   cudaError_t e = cudaMemcpyAsync(s->psi, src, sizeof(float2) << s->n, cudaMemcpyDefault, s->stream);
   if (e == cudaSuccess) e = cudaStreamSynchronize(s->stream);
   if (e != cudaSuccess) return cuda_fail(e, "sv_load_state");
@@ -550,6 +575,17 @@ sv_status sv_norm(sv_state *s, double *norm2, double *sum_p2) {
   sv_status st = set_device(s);
   if (st != SV_OK) return st;
   if ((st = materialize(s)) != SV_OK) return st;
+  if (s->sums_valid) {
+    // summed by the last pass that wrote the state
+    double h[2] = {0, 0};
+    cudaError_t e = cudaMemcpyAsync(h, s->d_sums, sizeof(h), cudaMemcpyDeviceToHost, s->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s->stream);
+    if (e != cudaSuccess) return cuda_fail(e, "sv_norm");
+    if (s->prof) s->d2h += sizeof(h);
+    if (norm2) *norm2 = h[0];
+    if (sum_p2) *sum_p2 = h[1];
+    return SV_OK;
+  }
   const size_t need = (size_t)(svk::reduce_partials_needed() + 2) * 2 * sizeof(double);
   if ((st = ensure_device_buffer(&s->d_scratch, &s->d_scratch_cap, need)) != SV_OK) return st;
   double *partials = static_cast<double *>(s->d_scratch);

@@ -223,6 +223,7 @@ extern "C" sv_status sv_set_basis_state(sv_state *s, uint64_t x) {
   if (s->n < 64 && (x >> s->n)) return fail(SV_ERR_ARG, "sv_set_basis_state: x has bits >= n");
   sv_status st = set_device(s);
   if (st != SV_OK) return st;
+  s->sums_valid = false;
   const cudaError_t e = svk::launch_basis_state(s->psi, s->n, x, s->stream);
   if (e != cudaSuccess) { s->broken = true; return cuda_fail(e, "sv_set_basis_state"); }
   s->fresh = false;
@@ -318,6 +319,7 @@ extern "C" sv_status sv_branch_full_state(const sv_lattice *lat, const sv_cut *c
   const float scale = std::ldexp(1.0f, C.tf);
   if (e == cudaSuccess)
     e = svk::launch_outer_sum(A.s->psi, C.na, B.s->psi, C.nb, C.tf, scale, out->psi, out->stream);
+  out->sums_valid = false;
   if (e != cudaSuccess) { out->broken = true; return cuda_fail(e, "sv_branch_full_state"); }
   out->fresh = false;
   if (out->prof) out->other_launches += 1;

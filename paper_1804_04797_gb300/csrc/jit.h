@@ -57,8 +57,14 @@ bool get_modules(const std::vector<const svp::Plan *> &plans, int kpr, std::vect
 // launch (before a stream capture records the launches).
 cudaError_t prepare_passes(const Module *M, const svp::Plan &P);
 
-// Launch pass `pass` of a module on the plan's device copy.
+// Launch pass `pass` of a module on the plan's device copy.  sums (the plan's last pass
+// only; null elsewhere): per CTA, the sums of p and p^2 of the amplitudes it stored, at
+// sums[2 b], sums[2 b + 1] for CTA b; *grid_out (may be null): the CTAs launched.
 cudaError_t launch_pass(const Module *M, float2 *psi, int n, const svk::DevPlanView &view, int pass,
-                        const svp::DevPass &hp, cudaStream_t st);
+                        const svp::DevPass &hp, cudaStream_t st, double *sums = nullptr,
+                        unsigned *grid_out = nullptr);
+
+// Upper bound of the CTAs one pass launch uses (sizes the sums buffer).
+unsigned max_pass_grid();
 
 }  // namespace svj

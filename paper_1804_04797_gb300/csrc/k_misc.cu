@@ -297,6 +297,11 @@ cudaError_t launch_norm(const float2 *psi, int n, double *partials, double *out2
   return cudaGetLastError();
 }
 
+cudaError_t launch_norm_final(const double *partials, int count, double *out2, cudaStream_t st) {
+  norm_final_kernel<<<1, kBlock, 0, st>>>(partials, count, out2);
+  return cudaGetLastError();
+}
+
 cudaError_t launch_inner(const float2 *a, const float2 *b, int n, double *partials, double *out2, cudaStream_t st) {
   if (n < 2) {
     inner_small_kernel<<<1, 1, 0, st>>>(a, b, 1ull << n, out2);

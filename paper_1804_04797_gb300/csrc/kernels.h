@@ -43,6 +43,9 @@ cudaError_t launch_gate_diag(float2 *psi, int n, uint64_t mask, uint64_t val, fl
 int reduce_partials_needed();
 cudaError_t launch_norm(const float2 *psi, int n, double *partials, double *out2,
                         cudaStream_t st);
+// The second level of launch_norm alone: out2 = the sums of count partial pairs (fixed
+// order), e.g. the per-CTA sums a plan kernel's last pass wrote.
+cudaError_t launch_norm_final(const double *partials, int count, double *out2, cudaStream_t st);
 // out[2j], out[2j+1] = re, im of psi[bits[j]]
 cudaError_t launch_gather(const float2 *psi, const uint64_t *bits, int64_t m, double *out,
                           cudaStream_t st);

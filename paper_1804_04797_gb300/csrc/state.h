@@ -44,6 +44,13 @@ struct sv_state {
   svp::Options plan_po;
   const svj::Module *plan_jit = nullptr;
   svk::DevPlanView plan_view{};
+  // the norm sums (sum p, sum p^2) of the current state, computed by the last pass of a
+  // plan-kernel run as it wrote the state: d_sums[0..1]; d_sums[2..] per-CTA partials.
+  // Any other write of the state clears sums_valid; a state the caller can write
+  // directly (created from its pointer, or exposed by sv_device_ptr) never sets it.
+  double *d_sums = nullptr;
+  bool sums_valid = false;
+  bool user_writes = false;
 };
 
 namespace svj {

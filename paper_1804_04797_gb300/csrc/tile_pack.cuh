@@ -543,6 +543,46 @@ __device__ __forceinline__ void store_tile(float2 *__restrict__ psi, const float
   }
 }
 
+// store_tile that also adds the stored amplitudes' probabilities p and p^2 to a2 and
+// a4: per tile in fp32 (32 values per thread), across tiles in fp64 (the reductions of
+// the state's norm, fused into the pass that writes it).
+__device__ __forceinline__ void store_tile_sums(float2 *__restrict__ psi, const float4 *tile, const DevPass &P,
+                                                const uint64_t *chunk_off, uint64_t base, double &a2, double &a4) {
+  const int cp = P.c - 1;
+  const uint32_t in_mask = (1u << cp) - 1;
+  const uint32_t tid = threadIdx.x, T = blockDim.x;
+  float s2 = 0.f, s4 = 0.f;
+#pragma unroll 4
+  for (int it = 0; it < kP; ++it) {
+    const uint32_t k = tid + (uint32_t)it * T;
+    const float4 x = tile[pack_phys(k)];  // (re, re', im, im')
+    const float p0 = fmaf(x.x, x.x, x.z * x.z), p1 = fmaf(x.y, x.y, x.w * x.w);
+    s2 += p0 + p1;
+    s4 = fmaf(p0, p0, fmaf(p1, p1, s4));
+    *reinterpret_cast<float4 *>(psi + base + chunk_off[k >> cp] + 2 * (k & in_mask)) = make_float4(x.x, x.z, x.y, x.w);
+  }
+  a2 += (double)s2;
+  a4 += (double)s4;
+}
+
+// The CTA's sums (fixed order) to partials[2 blockIdx.x], [2 blockIdx.x + 1].
+__device__ __forceinline__ void block_sums_out(double a2, double a4, double *partials) {
+  __shared__ double r2[32], r4[32];
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    a2 += __shfl_xor_sync(0xffffffffu, a2, o);
+    a4 += __shfl_xor_sync(0xffffffffu, a4, o);
+  }
+  if ((threadIdx.x & 31) == 0) { r2[threadIdx.x >> 5] = a2; r4[threadIdx.x >> 5] = a4; }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double t2 = 0.0, t4 = 0.0;
+    for (int w = 0; w < (int)((blockDim.x + 31) >> 5); ++w) { t2 += r2[w]; t4 += r4[w]; }
+    partials[2 * blockIdx.x] = t2;
+    partials[2 * blockIdx.x + 1] = t4;
+  }
+}
+
 // The generated first tile of a fresh state: 2^{-n/2} everywhere, or |0..0> (element 0
 // of group 0 of tile 0, the thread with condition word 0).
 __device__ __forceinline__ void init_regs(Regs &R, Regs &I, const DevPass &P, uint32_t W) {

@@ -171,8 +171,10 @@ def sv_copy_state(h, n_qubits, dst=None):
 
 
 def sv_load_state(h, src):
-    ptr = src if isinstance(src, int) else np.ascontiguousarray(src, dtype=np.complex64).ctypes.data
-    keep = src
+    """src: a device or host address (int), or an array converted to complex64 (kept
+    alive until the copy is done)."""
+    keep = src if isinstance(src, int) else np.ascontiguousarray(src, dtype=np.complex64)
+    ptr = keep if isinstance(keep, int) else keep.ctypes.data
     _check(lib().sv_load_state(h, c_void_p(ptr)))
     del keep
 

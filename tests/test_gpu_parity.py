@@ -352,6 +352,39 @@ def test_batch_with_plan_kernel_circuits_matches_oracle(jit):
     sv.sv_batch_free()
 
 
+def test_norm_summed_by_the_last_pass():
+    """Plan kernels sum p and p^2 in the pass that writes the state and sv_norm returns
+    those sums: they match the oracle and a separate reduction of the same state, and any
+    other write of the state (load, basis state, a caller-writable pointer) drops them."""
+    lat = inputs.lattice_for(4, 5, 14, seed=21)
+    n, gates = oracle_gates(lat)
+    assert n == 20
+    want = csim.run(n, gates)
+    _s2w, s4w = csim.reductions(want)
+    g = sv.sv_generate_circuit(lat)
+    h = sv.sv_create(n, sv.options(jit=1))
+    try:
+        sv.sv_apply_circuit(h, g)
+        s2, s4 = sv.sv_norm(h)
+        assert abs(s2 - 1) <= NORM_TOL and abs(s4 - s4w) <= 1e-5 * s4w
+        state = sv.sv_copy_state(h, n)
+        sv.sv_load_state(h, state)  # the same amplitudes, reduced by the separate kernel
+        r2, r4 = sv.sv_norm(h)
+        assert abs(r2 - s2) <= 1e-6 and abs(r4 - s4) <= 1e-6 * s4
+        sv.sv_set_basis_state(h, 5)
+        assert sv.sv_norm(h) == (1.0, 1.0)
+        sv.sv_reset(h)
+        sv.sv_apply_circuit(h, g)
+        assert sv.sv_norm(h) == (s2, s4)  # the same run, the same sums
+        sv.sv_device_ptr(h)  # from now on the caller may write the state
+        sv.sv_reset(h)
+        sv.sv_apply_circuit(h, g)
+        d2, d4 = sv.sv_norm(h)
+        assert abs(d2 - s2) <= 1e-6 and abs(d4 - s4) <= 1e-6 * s4
+    finally:
+        sv.sv_destroy(h)
+
+
 def test_many_square_roots_in_one_stage():
     """200 X^{1/2} / Y^{1/2} gates on five qubits fall into one stage: their factors 1/2
     (deferred and applied in bulk by the tile kernels) must neither overflow nor lose
