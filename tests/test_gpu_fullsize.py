@@ -8,7 +8,8 @@ size: norm, the Porter-Thomas statistic N * sum p^2 ~ 2, the inverse circuit ret
 (6x7, depth 10, cut between rows 2 and 3, t = 10): the cut-branch amplitudes against the
 oracle's own split-and-sum (complex128, all 1024 branches on the host cores).  The
 34-qubit amplitudes by the inner product of a forward and a backward state against the
-forward state's.
+forward state's.  The 34-qubit lattice at depth 16 (12 CZs across a row cut): sampled
+amplitudes of the full-size state against the oracle's split-and-sum.
 """
 import numpy as np
 import pytest
@@ -115,6 +116,31 @@ def test_34q_amplitudes_by_inner_product_match_full_state():
         sv.sv_destroy(h)
     got = sv.sv_amplitudes_by_inner_product(lat, 15, bits)
     assert rel_l2(got, full) <= REL_L2
+
+
+def test_34q_sampled_amplitudes_match_oracle_split_sum():
+    """The 34-qubit lattice at depth 16 on the full 128 GiB state (the tile shape and
+    launch configuration the bench times) against the oracle's split-and-sum at the cut
+    between rows 2 and 3: t = 12 crossing CZs, 4096 branches of two 17-qubit halves in
+    complex128 on the host cores.  Plan kernels, the interpreting kernel and F16x3."""
+    c = inputs.C34
+    lat = inputs.Lattice(c.rows, c.cols, c.removed_mask, 16, c.seed)
+    n, gates = oc.generate(lat.rows, lat.cols, lat.removed_mask, lat.depth, lat.seed)
+    half_a = (1 << 17) - 1  # rows 0..2 (row 0 lacks its first site)
+    assert n == 34 and len(oc.cut_crossings(gates, half_a)) == 12
+    bits = inputs.bitstrings(n, 64, seed=3)
+    want = csim.branch_amplitudes(n, gates, half_a, bits)
+    g = sv.sv_generate_circuit(lat)
+    for kw in (dict(), dict(jit=-1), dict(precision=sv.SV_PREC_F16X3)):
+        h = sv.sv_create(n, sv.options(**kw))
+        try:
+            sv.sv_apply_circuit(h, g)
+            got = sv.sv_get_amplitudes(h, bits)
+            norm2, _ = sv.sv_norm(h)
+        finally:
+            sv.sv_destroy(h)
+        assert rel_l2(got, want) <= REL_L2, kw
+        assert abs(norm2 - 1) <= NORM_TOL, kw
 
 
 def test_42q_cut_branch_amplitudes_match_oracle():
