@@ -161,7 +161,10 @@ sv_status sv_get_amplitudes(sv_state *s, const uint64_t *bits, size_t m, double 
 
 /* fp64 sums over the state: norm2 = sum |alpha|^2, sum_p2 = sum |alpha|^4 (the
  * Porter-Thomas statistic of §3: N * sum_p2 -> 2).  Either pointer may be NULL.
- * Deterministic (fixed two-level tree). */
+ * Deterministic (fixed two-level tree).  After sv_apply_circuit on plan-specialised
+ * kernels (sv_options.jit) the sums were formed by the pass that wrote the state and the
+ * call reads no state; any other write of the state (reset, load, basis state, a
+ * sv_device_ptr or sv_create_from_ptr state) makes it reduce the state again. */
 sv_status sv_norm(sv_state *s, double *norm2, double *sum_p2);
 
 /* Allocation-free variant of sv_norm, for callers that cannot allocate device memory:
