@@ -292,14 +292,18 @@ sv_status sv_inner_product(sv_state *a, sv_state *b, double *out_re_im);
  * the equation alpha_x = <phi|psi>): the lattice circuit U = U2 U1 is cut after layer
  * split_layer (U1 = layers 0..split_layer, the H layer included; U2 = the rest),
  * |psi> = U1 H^n |0> is computed once, and for every bitstring x, |phi_x> = U2^dagger |x>
- * and alpha_x = <phi_x|psi>.  Two n-qubit states are allocated (2 x 8 x 2^n bytes, at
- * most n = 34 on GB300) and freed on return; out_re_im receives 2m doubles.  A
- * split_layer at or beyond the depth gives the plain amplitudes of the full state. */
+ * and alpha_x = <phi_x|psi>; on plan-specialised kernels (sv_options.jit) the last pass
+ * of phi_x sums <phi_x|psi> instead of storing phi_x.  Two n-qubit states are allocated
+ * (2 x 8 x 2^n bytes, at most n = 34 on GB300) and freed on return; out_re_im receives
+ * 2m doubles.  A split_layer at or beyond the depth gives the plain amplitudes of the
+ * full state. */
 sv_status sv_amplitudes_by_inner_product(const sv_lattice *lat, int split_layer, const uint64_t *bits, size_t m,
                                          const sv_options *opts, double *out_re_im);
 
 /* Compile the plan-specialised kernels of a gate list for sm_103a without a device
- * (NVRTC only; no cache is read or written): a check of the code generator.  log (may
+ * (NVRTC only; no cache is read or written), and the last pass once more as the variant
+ * that sums an inner product instead of storing (sv_amplitudes_by_inner_product): a check
+ * of the code generator.  log (may
  * be NULL) receives up to log_cap bytes of the compiler's messages, NUL-terminated.
  * SV_ERR_CUDA when NVRTC is missing or the compile fails. */
 sv_status sv_jit_check(int n_qubits, const sv_gate *gates, size_t n_gates, const sv_options *opts,

@@ -382,6 +382,79 @@ sv_status apply_gates(sv_state *s, const std::vector<svp::Gate> &g) {
   return SV_OK;
 }
 
+sv_status apply_gates_inner(sv_state *s, const std::vector<svp::Gate> &g, const sv_state *with, double *out,
+                            bool *fused) {
+  *fused = false;
+  sv_status st;
+  if ((st = set_device(s)) != SV_OK) return st;
+  if (s->opts.precision != SV_PREC_PLAIN || s->n < 6 || g.empty() || s->fresh || s->broken || !s->owns)
+    return SV_OK;
+  bool want_jit = false;
+  svp::Options po = apply_plan_options(s->opts, s->n, &want_jit);
+  if (!want_jit || po.fused) return SV_OK;
+  s->sums_valid = false;
+  uint64_t key = 1469598103934665603ull ^ 0x696e6e6572ull;  // distinct from apply_gates' keys
+  auto mix = [&key](const void *p, size_t len) {
+    const unsigned char *b = static_cast<const unsigned char *>(p);
+    for (size_t i = 0; i < len; ++i) key = (key ^ b[i]) * 1099511628211ull;
+  };
+  const int head[6] = {s->n, s->opts.precision, s->opts.fuse_k, s->opts.tile_bits, s->opts.low_bits, s->opts.jit};
+  mix(head, sizeof(head));
+  mix(g.data(), g.size() * sizeof(svp::Gate));
+  if (!(s->plan_valid && s->plan_key == key)) {
+    s->plan_valid = false;
+    svp::Plan P;
+    const char *err = nullptr;
+    if (!svp::build_plan(s->n, g, po, false, &P, &err)) return fail(SV_ERR_ARG, err ? err : "planning failed");
+    std::string jerr;
+    const svj::Module *M = svj::get_module(P, po.rk, &jerr, true);
+    if (!M) return SV_OK;  // no compiler: the caller applies and reduces separately
+    svk::DevPlanView view;
+    if ((st = upload_plan(s, P, &view)) != SV_OK) return st;
+    s->plan = std::move(P);
+    s->plan_po = po;
+    s->plan_jit = M;
+    s->plan_view = view;
+    s->plan_key = key;
+    s->plan_valid = true;
+  }
+  if (!s->d_sums) {
+    if (cudaMalloc(&s->d_sums, (2 + 2 * (size_t)svj::max_pass_grid()) * sizeof(double)) != cudaSuccess) {
+      cudaGetLastError();
+      s->d_sums = nullptr;
+      return fail(SV_ERR_OOM, "sums buffer allocation failed");
+    }
+  }
+  // the other state's pending work first (the handles may use different streams)
+  cudaError_t e = with->stream == s->stream ? cudaSuccess : cudaStreamSynchronize(with->stream);
+  const svp::Plan &P = s->plan;
+  const double amps = std::ldexp(1.0, s->n);
+  unsigned grid = 0;
+  for (size_t p = 0; e == cudaSuccess && p < P.passes.size(); ++p) {
+    const bool last = p + 1 == P.passes.size();
+    prof_begin(s);
+    e = svj::launch_pass(s->plan_jit, s->psi, s->n, s->plan_view, (int)p, P.passes[p], s->stream,
+                         last ? s->d_sums + 2 : nullptr, last ? &grid : nullptr, last ? with->psi : nullptr);
+    prof_end(s, 16.0 * amps);  // last pass: reads this state and the other
+    if (s->prof) s->jit_launches += 1;
+  }
+  double h[2] = {0, 0};
+  if (e == cudaSuccess) e = svk::launch_norm_final(s->d_sums + 2, (int)grid, s->d_sums, s->stream);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(h, s->d_sums, sizeof(h), cudaMemcpyDeviceToHost, s->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s->stream);
+  // the last pass did not store: the state is not the circuit's result
+  s->broken = true;
+  if (e != cudaSuccess) return cuda_fail(e, "inner product pass");
+  if (s->prof) {
+    s->other_launches += 1;
+    s->d2h += sizeof(h);
+  }
+  out[0] = h[0];
+  out[1] = h[1];
+  *fused = true;
+  return SV_OK;
+}
+
 }  // namespace svc
 
 static sv_status apply_impl(sv_state *s, const sv_gate *gates, size_t n_gates, bool inverse) {
@@ -663,7 +736,14 @@ sv_status sv_jit_check(int n_qubits, const sv_gate *gates, size_t n_gates, const
     return fail(SV_ERR_ARG, err ? err : "planning failed");
   std::vector<std::string> cubins;
   std::string lg;
-  const bool ok = svj::compile_plan(P, po.rk, "sm_103a", &cubins, &lg, "");
+  bool ok = svj::compile_plan(P, po.rk, "sm_103a", &cubins, &lg, "");
+  if (ok && !P.passes.empty()) {
+    // and the last pass as the inner-product variant (the backward states of the
+    // inner-product amplitudes)
+    std::string cubin, lg2;
+    ok = svj::compile(svj::pass_source(P, po.rk, (int)P.passes.size() - 1, true), "sm_103a", &cubin, &lg2);
+    if (!lg2.empty()) lg += "inner last pass: " + lg2;
+  }
   if (log && log_cap) {
     const size_t k = std::min(lg.size(), log_cap - 1);
     std::memcpy(log, lg.data(), k);

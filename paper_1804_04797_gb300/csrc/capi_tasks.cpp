@@ -284,9 +284,15 @@ extern "C" sv_status sv_amplitudes_by_inner_product(const sv_lattice *lat, int s
   if ((st = sv_apply_circuit(A.s, g1.data(), g1.size())) != SV_OK) return st;  // |psi> = U1 H|0>
   if (m == 0) return SV_OK;
   if ((st = sv_create(n, &o, &B.s)) != SV_OK) return st;
+  std::vector<svp::Gate> g2_inv;
+  if ((st = convert_gates(n, g2.data(), g2.size(), true, &g2_inv)) != SV_OK) return st;
   for (size_t j = 0; j < m; ++j) {
-    // |phi_x> = U2^dagger |x>;  alpha_x = <phi_x|psi>
+    // |phi_x> = U2^dagger |x>;  alpha_x = <phi_x|psi>: on plan kernels the last pass of
+    // phi_x sums the inner product instead of storing phi_x
     if ((st = sv_set_basis_state(B.s, bits[j])) != SV_OK) return st;
+    bool fused = false;
+    if ((st = apply_gates_inner(B.s, g2_inv, A.s, out_re_im + 2 * j, &fused)) != SV_OK) return st;
+    if (fused) continue;
     if ((st = sv_apply_circuit_inverse(B.s, g2.data(), g2.size())) != SV_OK) return st;
     if ((st = sv_inner_product(B.s, A.s, out_re_im + 2 * j)) != SV_OK) return st;
   }

@@ -29,8 +29,9 @@ int register_slots();
 constexpr int kTileBits = 12;
 
 // CUDA source of the kernel ("sv_pass") of one pass of a packed plan.  kpr: register
-// slots besides the pack bit (the plan's rk).
-std::string pass_source(const svp::Plan &P, int kpr, int pass);
+// slots besides the pack bit (the plan's rk).  inner (the last pass only): instead of
+// storing the state, the kernel sums conj(state) * other over it into per-CTA partials.
+std::string pass_source(const svp::Plan &P, int kpr, int pass, bool inner = false);
 
 // Compile CUDA source for an architecture ("sm_103a") to a cubin with NVRTC; the
 // device headers are compiled into the library.  Returns false with *log set.
@@ -46,23 +47,24 @@ struct Module;
 // The compiled kernels of plan P on the current device, from the in-process cache, the
 // on-disk cache (the library's build directory, subdirectory jit) or a fresh compile.
 // nullptr with *err set if NVRTC or the module load fails.
-const Module *get_module(const svp::Plan &P, int kpr, std::string *err);
+const Module *get_module(const svp::Plan &P, int kpr, std::string *err, bool inner = false);
 
 // The modules of several plans at once: every pass kernel not yet cached is compiled in
 // one pool of worker threads.  false with *err set if any compile or load fails.
 bool get_modules(const std::vector<const svp::Plan *> &plans, int kpr, std::vector<const Module *> *out,
-                 std::string *err);
+                 std::string *err, bool inner = false);
 
 // Set each pass kernel's shared-memory limit and occupancy now rather than at its first
 // launch (before a stream capture records the launches).
 cudaError_t prepare_passes(const Module *M, const svp::Plan &P);
 
 // Launch pass `pass` of a module on the plan's device copy.  sums (the plan's last pass
-// only; null elsewhere): per CTA, the sums of p and p^2 of the amplitudes it stored, at
+// only; null elsewhere): per CTA, the sums of p and p^2 of the amplitudes it stored (an
+// inner module's last pass: of re and im of conj(state) * other, without storing), at
 // sums[2 b], sums[2 b + 1] for CTA b; *grid_out (may be null): the CTAs launched.
 cudaError_t launch_pass(const Module *M, float2 *psi, int n, const svk::DevPlanView &view, int pass,
                         const svp::DevPass &hp, cudaStream_t st, double *sums = nullptr,
-                        unsigned *grid_out = nullptr);
+                        unsigned *grid_out = nullptr, const float2 *other = nullptr);
 
 // Upper bound of the CTAs one pass launch uses (sizes the sums buffer).
 unsigned max_pass_grid();

@@ -75,6 +75,13 @@ sv_status convert_gates(int n, const sv_gate *g, size_t count, bool inverse, std
 sv_status upload_plan(sv_state *s, const svp::Plan &P, svk::DevPlanView *view);
 sv_status run_plan(sv_state *s, const svp::Plan &P, const svk::DevPlanView &view, bool fused, bool f16 = false,
                    const svj::Module *jit = nullptr);
+// Apply g to s on plan-specialised kernels whose last pass, instead of storing the state,
+// sums <state | with> (conj(state) * with over all amplitudes) into out[0] (re), out[1]
+// (im); s is left unusable (the last pass did not write it).  *fused = false (and s
+// untouched) where these kernels are not in use for s's options or NVRTC is missing: the
+// caller then applies and reduces separately.
+sv_status apply_gates_inner(sv_state *s, const std::vector<svp::Gate> &g, const sv_state *with, double *out,
+                            bool *fused);
 // Plan and run an internal gate list (kinds may include K_PEQ) on the state.
 sv_status apply_gates(sv_state *s, const std::vector<svp::Gate> &g);
 sv_status set_device(sv_state *s);

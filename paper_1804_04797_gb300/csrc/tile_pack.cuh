@@ -565,6 +565,30 @@ __device__ __forceinline__ void store_tile_sums(float2 *__restrict__ psi, const 
   a4 += (double)s4;
 }
 
+// <phi|psi> over the tile instead of storing it: phi = the tile as the stages left it,
+// psi read from `other` at the same positions; conj(phi) psi summed in fp32 over the
+// thread's 32 amplitudes, then into the fp64 sums re, im.
+__device__ __forceinline__ void inner_tile(const float2 *__restrict__ other, const float4 *tile, const DevPass &P,
+                                           const uint64_t *chunk_off, uint64_t base, double &re, double &im) {
+  const int cp = P.c - 1;
+  const uint32_t in_mask = (1u << cp) - 1;
+  const uint32_t tid = threadIdx.x, T = blockDim.x;
+  float sr = 0.f, si = 0.f;
+#pragma unroll 4
+  for (int it = 0; it < kP; ++it) {
+    const uint32_t k = tid + (uint32_t)it * T;
+    const float4 x = tile[pack_phys(k)];  // phi: (re, re', im, im')
+    const float4 y = *reinterpret_cast<const float4 *>(other + base + chunk_off[k >> cp] + 2 * (k & in_mask));
+    // psi: (re, im, re', im');  conj(a) b = (a.re b.re + a.im b.im) + i (a.re b.im - a.im b.re)
+    sr = fmaf(x.x, y.x, fmaf(x.z, y.y, sr));
+    sr = fmaf(x.y, y.z, fmaf(x.w, y.w, sr));
+    si = fmaf(x.x, y.y, fmaf(-x.z, y.x, si));
+    si = fmaf(x.y, y.w, fmaf(-x.w, y.z, si));
+  }
+  re += (double)sr;
+  im += (double)si;
+}
+
 // The CTA's sums (fixed order) to partials[2 blockIdx.x], [2 blockIdx.x + 1].
 __device__ __forceinline__ void block_sums_out(double a2, double a4, double *partials) {
   __shared__ double r2[32], r4[32];
