@@ -231,6 +231,32 @@ def test_amplitudes_and_probabilities_gather():
     np.testing.assert_allclose(probs, np.abs(amps) ** 2, rtol=1e-12, atol=0)
 
 
+def test_empty_inputs():
+    """An empty gate list leaves the state as it is (|0...0> when fresh), a gather of no
+    bitstrings returns nothing, an empty batch is a no-op."""
+    n = 12
+    lat = inputs.lattice_for(3, 4, 6, seed=1)
+    n_o, gates = oracle_gates(lat)
+    assert n_o == n
+    h = sv.sv_create(n)
+    try:
+        sv.sv_apply_circuit(h, sv.gates_from_tuples([]))
+        psi = sv.sv_copy_state(h, n)
+        assert psi[0] == 1 and np.count_nonzero(psi) == 1
+        # from the written |0...0> (no uniform shortcut): the H layer runs as gates
+        sv.sv_apply_circuit(h, sv.sv_generate_circuit(lat))
+        before = sv.sv_copy_state(h, n)
+        assert rel_l2(before, csim.run(n, gates)) <= REL_L2
+        sv.sv_apply_circuit(h, sv.gates_from_tuples([]))
+        sv.sv_apply_circuit_inverse(h, sv.gates_from_tuples([]))
+        assert np.array_equal(sv.sv_copy_state(h, n), before)
+        assert sv.sv_get_amplitudes(h, []).size == 0
+        assert sv.sv_get_probabilities(h, []).size == 0
+    finally:
+        sv.sv_destroy(h)
+    assert sv.sv_apply_batch([]).shape == (0, 3)
+
+
 def test_invalid_arguments_leave_state_usable():
     h = sv.sv_create(10)
     try:
