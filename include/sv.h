@@ -127,7 +127,10 @@ sv_status sv_load_state(sv_state *s, const void *src);
  * the initial state in its first pass instead of reading the buffer. */
 sv_status sv_reset(sv_state *s);
 
-/* Device pointer of the amplitudes (owned by the handle or the caller). */
+/* Device pointer of the amplitudes (owned by the handle or the caller).  The caller
+ * may read or write the amplitudes through it between calls on the handle's stream; from
+ * then on sv_norm always reduces the state itself (sums formed by earlier passes are not
+ * reused). */
 sv_status sv_device_ptr(sv_state *s, void **ptr);
 
 /* --- circuits ---------------------------------------------------------------------- */
@@ -149,6 +152,9 @@ sv_status sv_generate_circuit(const sv_lattice *lat, sv_gate *out, size_t cap, s
  * groups (the bunching of gates on "local qubits" of §2.3, generalised to any qubit
  * set).  If the state is still the initial |0..0> and the list starts with H on every
  * qubit, that layer becomes the uniform amplitude 2^{-n/2} written by the first pass.
+ * The same list, options and starting condition as the handle's previous call reuse that
+ * call's plan and kernels.  On plan-specialised kernels (sv_options.jit) the last pass
+ * also forms the fp64 norm sums that sv_norm then returns.
  * SV_ERR_ARG for a qubit >= n, CZ with q0 == q1, or an unknown kind (state untouched).
  * A CUDA failure marks the handle SV_ERR_STATE. */
 sv_status sv_apply_circuit(sv_state *s, const sv_gate *gates, size_t n_gates);
