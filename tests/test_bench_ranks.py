@@ -1,6 +1,7 @@
-"""The multi-rank arithmetic of bench.py on CPU (gloo, world size 2): timings are the
-slowest rank's, and N replicas of one circuit each make N circuits per that time.  The
-GPU path differs only in the tensors' device (NCCL)."""
+"""bench.py's host-side arithmetic on CPU.  Multi-rank (gloo, world size 2): timings are
+the slowest rank's, and N replicas of one circuit each make N circuits per that time (the
+GPU path differs only in the tensors' device, NCCL).  The algorithmic flop count behind
+the FP32 roofline, recounted from the oracle's own gate list."""
 import os
 import socket
 
@@ -47,3 +48,17 @@ def test_single_process_and_replica_value():
     assert bench.max_over_ranks([0.5, 7], None, 'cpu') == [0.5, 7.0]
     assert bench.whole_job_s_per_circuit(0.66, 1) == 0.66
     assert bench.whole_job_s_per_circuit(0.66, 4) == pytest.approx(0.165)
+
+
+def test_algorithmic_flops_of_the_34q_circuit():
+    """4 real operations per amplitude for each square root of X or Y, 2 for each T (half
+    the amplitudes times (1 + i)/sqrt2), none for CZ; the H layer is the generated uniform
+    state: 768 per amplitude for the 34-qubit depth-30 circuit."""
+    from oracle import circuit as oc
+    from paper_1804_04797_gb300 import inputs, sv
+    lat = inputs.C34
+    n, gates = oc.generate(lat.rows, lat.cols, lat.removed_mask, lat.depth, lat.seed)
+    kinds = [k for (k, _a, _b, layer) in gates if layer > 0]
+    want = 4 * sum(k in ('SX', 'SY') for k in kinds) + 2 * sum(k == 'T' for k in kinds)
+    assert 'H' not in kinds and want == 768
+    assert bench.algorithmic_flops_per_amplitude(sv.sv_generate_circuit(lat)) == want
