@@ -41,7 +41,6 @@ batch_kernel(float2 *__restrict__ states, DevPlanView plan, const BatchCP *__res
   __shared__ DevPass P;
   __shared__ uint64_t chunk_off[1 << 10];
   __shared__ unsigned int s_item;
-  __shared__ uint32_t s_cp;
   __shared__ int s_stop;
   const int tid = threadIdx.x;
   unsigned int *done = words + kBatchHeader;
