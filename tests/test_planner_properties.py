@@ -50,3 +50,57 @@ def test_execution_order_is_a_valid_reordering(case):
     want = ov.run(n, gates, start)
     got = ov.run(n, [gates[i] for i in order.tolist()], start)
     np.testing.assert_allclose(got, want, atol=1e-11 * max(1.0, float(np.abs(want).max())))
+
+
+def _recount(gates, in_a):
+    """Crossing CZs, those that only sign the output (neither qubit meets a later
+    non-diagonal gate), and the implicit ones (one side quiet), from the gate list."""
+    last_nd = {}
+    for i, (k, q0, _q1, _l) in enumerate(gates):
+        if k in ('H', 'SX', 'SY'):
+            last_nd[q0] = i
+    t = absorbed = full = impl_a = impl_b = 0
+    for i, (k, q0, q1, _l) in enumerate(gates):
+        if k != 'CZ' or in_a[q0] == in_a[q1]:
+            continue
+        t += 1
+        qa, qb = (q0, q1) if in_a[q0] else (q1, q0)
+        quiet_a, quiet_b = last_nd.get(qa, -1) < i, last_nd.get(qb, -1) < i
+        if quiet_a and quiet_b:
+            absorbed += 1
+        elif quiet_a:
+            impl_a += 1
+        elif quiet_b:
+            impl_b += 1
+        else:
+            full += 1
+    return t, absorbed, full + impl_b, full + impl_a, full
+
+
+@st.composite
+def cuts(draw):
+    rows = draw(st.integers(2, 5))
+    cols = draw(st.integers(2, 6))
+    depth = draw(st.integers(1, 16))
+    seed = draw(st.integers(0, 2 ** 32))
+    cut_row = draw(st.integers(1, rows - 1))
+    return rows, cols, depth, seed, cut_row
+
+
+@settings(max_examples=120, deadline=None)
+@given(cuts())
+def test_cut_plan_counts_match_a_recount(case):
+    rows, cols, depth, seed, cut_row = case
+    n, gates = oc.generate(rows, cols, 0, depth, seed)
+    half_a = (1 << (cut_row * cols)) - 1  # rows 0..cut_row-1
+    in_a = [bool((half_a >> q) & 1) for q in range(n)]
+    lat = sv.sv_lattice(rows, cols, 0, depth, seed)
+    n_a = cut_row * cols
+    n_b = n - n_a
+    t = _recount(gates, in_a)[0]
+    for full, want in ((False, _recount(gates, in_a)), (True, (t, 0, t, t, t))):
+        if n_a + want[2] > 34 or n_b + want[3] > 34:  # a half state beyond one GPU: refused
+            with pytest.raises(sv.SvError):
+                sv.sv_branch_counts(lat, half_a, full_decomposition=full)
+        else:
+            assert sv.sv_branch_counts(lat, half_a, full_decomposition=full) == want
