@@ -104,3 +104,19 @@ def test_cut_plan_counts_match_a_recount(case):
                 sv.sv_branch_counts(lat, half_a, full_decomposition=full)
         else:
             assert sv.sv_branch_counts(lat, half_a, full_decomposition=full) == want
+
+
+@settings(max_examples=8, deadline=None, suppress_health_check=[HealthCheck.too_slow])
+@given(plans())
+def test_generated_kernels_compile(case):
+    """Every plan-specialised pass kernel of a random plan (and its last pass as the
+    inner-product variant) compiles for sm_103a (NVRTC, no device)."""
+    n, gates, kw, fresh = case
+    kw = {k: v for k, v in kw.items() if k != 'precision'}  # the plain path's kernels
+    lib_gates = sv.gates_from_tuples([(oc.KIND_CODE[k], a, max(b, 0), l) for (k, a, b, l) in gates])
+    try:
+        sv.sv_jit_check(n, lib_gates, sv.options(**kw), fresh_state=fresh)
+    except sv.SvError as e:
+        if 'libnvrtc' in str(e):
+            pytest.skip('NVRTC not installed')
+        raise
