@@ -67,11 +67,13 @@ SMS, FP32_LANES_PER_SM = 152, 128
 
 def algorithmic_flops_per_amplitude(gates):
     """Real additions and multiplications the gate list needs per amplitude: a square root
-    of X or Y updates a pair with 8 real adds (4 per amplitude; its 1/2 is an exact
-    power-of-two scale), H with 8 adds + 4 multiplies (6), T and its adjoint multiply half
-    the amplitudes by (1 +- i)/sqrt2 (2 adds + 2 multiplies each: 2 per amplitude); Z, CZ
-    and the projectors change signs or zero and take none.  The leading layer of H on a
-    fresh state is the generated uniform state."""
+    of X or Y is a scalar e^{+-i pi/4} 2^{-1/2} (applied once per circuit) times an
+    unscaled rotation that updates a pair with 4 real additions (2 per amplitude), H a
+    pair with 4 additions and 4 multiplications by 1/sqrt2 (4 per amplitude), T and its
+    adjoint multiply half the amplitudes by (1 +- i)/sqrt2 (2 additions + 2
+    multiplications each: 2 per amplitude); Z, CZ and the projectors change signs or zero
+    and take none.  The leading layer of H on a fresh state is the generated uniform
+    state."""
     kinds = [int(k) for k in gates['kind']]
     i = 0
     seen = set()
@@ -79,7 +81,7 @@ def algorithmic_flops_per_amplitude(gates):
         seen.add(int(gates['q0'][i]))
         i += 1
     rest = kinds[i:]
-    return 4.0 * sum(k in (2, 3, 9, 10) for k in rest) + 6.0 * sum(k == 0 for k in rest) + \
+    return 2.0 * sum(k in (2, 3, 9, 10) for k in rest) + 4.0 * sum(k == 0 for k in rest) + \
         2.0 * sum(k in (1, 8) for k in rest)
 
 

@@ -172,6 +172,9 @@ bool build_plan(int n, const std::vector<Gate> &gates, const Options &opt, bool 
 
   const double amps = std::ldexp(1.0, n);
   bool first_pass = true;
+  // packed plans: the square roots' scalars not yet applied -- an odd factor 2^{-1/2}
+  // carried between stages, and the phase e^{i pi phase8/4} -- for the plan's end
+  int sqrt_carry = 0, phase8 = 0;
   while (!rem.empty() || (first_pass && fresh_state)) {
     const uint64_t S = choose_tile(n, m, c, gates, rem);
     std::vector<char> applied;
@@ -427,9 +430,11 @@ bool build_plan(int n, const std::vector<Gate> &gates, const Options &opt, bool 
         for (int gi : inner) lower(gi);
       for (int gi : post) lower(gi);
       if (pack) {
-        // the packed kernel applies the factors 1/2 of the square roots in bulk: a
-        // P_SCALE after every kMaxDeferred of them, the remainder at the stage's end;
-        // non-diagonal gates, T and two-qubit ops of a packed plan are unconditional
+        // the packed kernel applies the square roots as unscaled rotations; their
+        // factors 2^{-1/2} are applied in pairs as exact 1/2 in bulk (a P_SCALE after
+        // every kMaxDeferred halves, the remainder at the stage's end), an odd one is
+        // carried on, and their phases go to the plan's end (P_GLOBAL); non-diagonal
+        // gates, T and two-qubit ops of a packed plan are unconditional
         std::vector<DevOp> ops(P.ops.begin() + ds.op_begin, P.ops.end());
         P.ops.resize(ds.op_begin);
         // condition word: group index bit i <-> tile bit nonr[i], then one bit per
@@ -438,7 +443,7 @@ bool build_plan(int n, const std::vector<Gate> &gates, const Options &opt, bool 
         for (int q = 0; q < 64; ++q) wpos[q] = -1;
         for (int i = 0; i < group_bits; ++i) wpos[dp.tq[ds.nonr[i]]] = i;
         for (int i = 0; i < dp.nt; ++i) wpos[dp.ntq[i]] = group_bits + i;
-        int pending = 0;
+        int units = sqrt_carry;  // factors 2^{-1/2} pending
         for (DevOp o : ops) {
           const bool cond_ok = o.cmask == 0 || o.act == A_Z || o.act == A_P0 || o.act == A_P1 ||
                                o.act == A_PHASE || o.act == A_ZERO;
@@ -451,18 +456,20 @@ bool build_plan(int n, const std::vector<Gate> &gates, const Options &opt, bool 
           }
           P.ops.push_back(o);
           if (o.act == A_SX || o.act == A_SY || o.act == A_SXDG || o.act == A_SYDG) {
-            if (++pending == kMaxDeferred) {
+            phase8 = (phase8 + ((o.act == A_SX || o.act == A_SY) ? 1 : 7)) & 7;
+            if (++units == 2 * kMaxDeferred) {
               DevOp sc;
               std::memset(&sc, 0, sizeof(sc));
               sc.act = A_COUNT;
               sc.code = P_SCALE;
               sc.arg = (uint8_t)kMaxDeferred;
               P.ops.push_back(sc);
-              pending = 0;
+              units = 0;
             }
           }
         }
-        ds.halves = (uint8_t)pending;
+        ds.halves = (uint8_t)(units / 2);
+        sqrt_carry = units % 2;
       }
       if (P.ops.size() - ds.op_begin > 65535) { *err = "stage too large"; return false; }
       ds.op_count = (uint16_t)(P.ops.size() - ds.op_begin);
@@ -486,6 +493,22 @@ bool build_plan(int n, const std::vector<Gate> &gates, const Options &opt, bool 
     rem.swap(later);
     first_pass = false;
     if (P.passes.size() > 100000) { *err = "planner did not converge"; return false; }
+  }
+  // the square roots' remaining scalar, e^{i pi phase8/4} 2^{-sqrt_carry/2}, at the end of
+  // the last stage (whose ops are the last ones so far)
+  if (pack && (phase8 != 0 || sqrt_carry != 0)) {
+    if (P.stages.empty() || P.stages.back().op_begin + P.stages.back().op_count != P.ops.size()) {
+      *err = "packed plan: no last stage for the square roots' scalar";
+      return false;
+    }
+    DevOp g;
+    std::memset(&g, 0, sizeof(g));
+    g.act = A_COUNT;
+    g.code = P_GLOBAL;
+    g.arg = (uint8_t)(phase8 | (sqrt_carry << 3));
+    P.ops.push_back(g);
+    if (P.stages.back().op_count == 65535) { *err = "stage too large"; return false; }
+    P.stages.back().op_count += 1;
   }
   // a no-op past the last op: kernels may load the op after a stage's last one
   DevOp end;

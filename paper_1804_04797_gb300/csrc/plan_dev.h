@@ -70,11 +70,15 @@ enum PCode : uint8_t {
   P_PHASE = 132,  // scalar phase w^arg (accumulated, applied once)
   P_ZERO = 133,   // the whole group becomes zero
   P_U = 134,      // + j, general 2x2                                 (134..139)
-  P_SCALE = 140,  // every element times 2^-arg (deferred factors 1/2 of square roots)
-  P_COUNT = 141
+  P_SCALE = 140,   // every element times 2^-arg (deferred scalars of square roots)
+  P_GLOBAL = 141,  // every element times e^{i pi q/4} 2^{-u/2}, arg = q + 8 u (plan end)
+  P_COUNT = 142
 };
-// A packed stage defers the factors 1/2 of its square-root gates: at most kMaxDeferred
-// are pending at any point (a P_SCALE op applies them), the rest is DevStage::halves.
+// A packed plan applies the square roots as unscaled rotations (norm sqrt2 each) and
+// defers their scalars e^{+-i pi/4} 2^{-1/2}: two of the factors 2^{-1/2} make one factor
+// 1/2, of which a stage holds at most kMaxDeferred pending (a P_SCALE op applies them),
+// the rest is DevStage::halves; an odd factor 2^{-1/2} and the phases are carried to the
+// end of the plan (one P_GLOBAL op).
 constexpr int kMaxDeferred = 64;
 
 // Stage group addressing: group index g of a thread -> (tile-local index L0, global

@@ -73,11 +73,14 @@ template <>
 struct Sgn<float2> {
   __device__ __forceinline__ static float2 add(float2 x, float2 y, float s) { return fma2(y, f2(s, s), x); }
   __device__ __forceinline__ static float2 sub(float2 x, float2 y, float s) { return fma2(y, f2(-s, -s), x); }
+  // s y - x
+  __device__ __forceinline__ static float2 rsub(float2 x, float2 y, float s) { return fma2(y, f2(s, s), f2(-x.x, -x.y)); }
 };
 template <>
 struct Sgn<float> {
   __device__ __forceinline__ static float add(float x, float y, float s) { return fmaf(y, s, x); }
   __device__ __forceinline__ static float sub(float x, float y, float s) { return fmaf(y, -s, x); }
+  __device__ __forceinline__ static float rsub(float x, float y, float s) { return fmaf(y, s, -x); }
 };
 
 template <class G>
@@ -103,39 +106,67 @@ struct GH : Gate<GH> {  // (x + y)/sqrt2, (x - y)/sqrt2
     xr = O::rs(sr); xi = O::rs(si); yr = O::rs(dr); yi = O::rs(di);
   }
 };
-// The square roots without their factor 1/2 (counted and applied once per stage):
-// X^{1/2}: x' = s + i d, y' = s - i d
-struct GSX : Gate<GSX> {
+// The square roots as a scalar times an unscaled rotation (two additions per amplitude);
+// the planner counts the scalars, e^{+-i pi/4} 2^{-1/2} per gate, and applies their
+// product at the end of the plan (P_GLOBAL, with exact powers of two on the way):
+//   X^{1/2} = e^{i pi/4} 2^{-1/2} [[1, -i], [-i, 1]]   (X^{1/2})^+ = e^{-i pi/4} 2^{-1/2} [[1, i], [i, 1]]
+//   Y^{1/2} = e^{i pi/4} 2^{-1/2} [[1, -1], [1, 1]]    (Y^{1/2})^+ = e^{-i pi/4} 2^{-1/2} [[1, 1], [-1, 1]]
+// fs(): y carries a sign s (+1 or -1), folded into fused operations (exact products).
+struct GSX {  // x' = x - i y, y' = -i x + y
   template <class T>
-  __device__ __forceinline__ static void out(T sr, T si, T dr, T di, T &xr, T &xi, T &yr, T &yi) {
+  __device__ __forceinline__ static void f(T &xr, T &xi, T &yr, T &yi) {
     using O = Ops<T>;
-    xr = O::sub(sr, di); xi = O::add(si, dr); yr = O::add(sr, di); yi = O::sub(si, dr);
+    const T a = O::add(xr, yi), b = O::sub(xi, yr), c = O::add(xi, yr), d = O::sub(yi, xr);
+    xr = a; xi = b; yr = c; yi = d;
+  }
+  template <class T>
+  __device__ __forceinline__ static void fs(T &xr, T &xi, T &yr, T &yi, float s) {
+    using S = Sgn<T>;
+    const T a = S::add(xr, yi, s), b = S::sub(xi, yr, s), c = S::add(xi, yr, s), d = S::rsub(xr, yi, s);
+    xr = a; xi = b; yr = c; yi = d;
   }
 };
-struct GSXDG : Gate<GSXDG> {  // x' = s - i d, y' = s + i d
+struct GSXDG {  // x' = x + i y, y' = i x + y
   template <class T>
-  __device__ __forceinline__ static void out(T sr, T si, T dr, T di, T &xr, T &xi, T &yr, T &yi) {
+  __device__ __forceinline__ static void f(T &xr, T &xi, T &yr, T &yi) {
     using O = Ops<T>;
-    xr = O::add(sr, di); xi = O::sub(si, dr); yr = O::sub(sr, di); yi = O::add(si, dr);
+    const T a = O::sub(xr, yi), b = O::add(xi, yr), c = O::sub(yr, xi), d = O::add(xr, yi);
+    xr = a; xi = b; yr = c; yi = d;
+  }
+  template <class T>
+  __device__ __forceinline__ static void fs(T &xr, T &xi, T &yr, T &yi, float s) {
+    using S = Sgn<T>;
+    const T a = S::sub(xr, yi, s), b = S::add(xi, yr, s), c = S::rsub(xi, yr, s), d = S::add(xr, yi, s);
+    xr = a; xi = b; yr = c; yi = d;
   }
 };
-// Y^{1/2}: x' = (1+i) d, y' = (1+i) s
-struct GSY : Gate<GSY> {
+struct GSY {  // x' = x - y, y' = x + y
   template <class T>
-  __device__ __forceinline__ static void out(T sr, T si, T dr, T di, T &xr, T &xi, T &yr, T &yi) {
+  __device__ __forceinline__ static void f(T &xr, T &xi, T &yr, T &yi) {
     using O = Ops<T>;
-    xr = O::sub(dr, di); xi = O::add(dr, di); yr = O::sub(sr, si); yi = O::add(sr, si);
+    const T a = O::sub(xr, yr), b = O::sub(xi, yi), c = O::add(xr, yr), d = O::add(xi, yi);
+    xr = a; xi = b; yr = c; yi = d;
+  }
+  template <class T>
+  __device__ __forceinline__ static void fs(T &xr, T &xi, T &yr, T &yi, float s) {
+    using S = Sgn<T>;
+    const T a = S::sub(xr, yr, s), b = S::sub(xi, yi, s), c = S::add(xr, yr, s), d = S::add(xi, yi, s);
+    xr = a; xi = b; yr = c; yi = d;
   }
 };
-// (Y^{1/2})^dagger: x' = (1-i) s, y' = -(1-i) d
-struct GSYDG : Gate<GSYDG> {
+struct GSYDG {  // x' = x + y, y' = y - x
   template <class T>
-  __device__ __forceinline__ static void out(T sr, T si, T dr, T di, T &xr, T &xi, T &yr, T &yi) {
+  __device__ __forceinline__ static void f(T &xr, T &xi, T &yr, T &yi) {
     using O = Ops<T>;
-    xr = O::add(sr, si); xi = O::sub(si, sr); yr = O::sub(neg(dr), di); yi = O::sub(dr, di);
+    const T a = O::add(xr, yr), b = O::add(xi, yi), c = O::sub(yr, xr), d = O::sub(yi, xi);
+    xr = a; xi = b; yr = c; yi = d;
   }
-  __device__ __forceinline__ static float2 neg(float2 a) { return f2(-a.x, -a.y); }
-  __device__ __forceinline__ static float neg(float a) { return -a; }
+  template <class T>
+  __device__ __forceinline__ static void fs(T &xr, T &xi, T &yr, T &yi, float s) {
+    using S = Sgn<T>;
+    const T a = S::add(xr, yr, s), b = S::add(xi, yi, s), c = S::rsub(xr, yr, s), d = S::rsub(xi, yi, s);
+    xr = a; xi = b; yr = c; yi = d;
+  }
 };
 
 // ---- diagonal phases on one element (r, i) ----------------------------------------------
@@ -158,6 +189,41 @@ struct DTDG {  // times e^{-i pi/4}
 
 // ---- actions on a thread's 32 pairs -------------------------------------------------------
 using Regs = float2[kP];
+
+// The product of the square roots' scalars, applied once at the end of a plan (P_GLOBAL,
+// arg = q + 8 u): every element times e^{i pi q/4} 2^{-u/2}.  Odd q: e^{i pi q/4} =
+// (c + i d)/sqrt2 with c, d = +-1, so what remains after the additions is 1/2 (exact) for
+// u = 1 and 1/sqrt2 (hi + lo) for u = 0; even q: i^{q/2} (exact), then 1/sqrt2 if u = 1.
+template <int Q, int U>
+__device__ __forceinline__ void global_factor(Regs &R, Regs &I) {
+#pragma unroll
+  for (int p = 0; p < kP; ++p) {
+    const float2 r = R[p], i = I[p];
+    float2 nr = r, ni = i;
+    if constexpr (Q & 1) {
+      constexpr float c = (Q == 1 || Q == 7) ? 1.f : -1.f, d = (Q == 1 || Q == 3) ? 1.f : -1.f;
+      nr = fma2(i, f2(-d, -d), mul2(r, f2(c, c)));  // c r - d i
+      ni = fma2(i, f2(c, c), mul2(r, f2(d, d)));    // d r + c i
+      if constexpr (U == 1) {
+        nr = mul2(nr, f2(0.5f, 0.5f));
+        ni = mul2(ni, f2(0.5f, 0.5f));
+      } else {
+        nr = rs2x2(nr);
+        ni = rs2x2(ni);
+      }
+    } else {
+      if constexpr (Q == 2) { nr = f2(-i.x, -i.y); ni = r; }
+      if constexpr (Q == 4) { nr = f2(-r.x, -r.y); ni = f2(-i.x, -i.y); }
+      if constexpr (Q == 6) { nr = i; ni = f2(-r.x, -r.y); }
+      if constexpr (U == 1) {
+        nr = rs2x2(nr);
+        ni = rs2x2(ni);
+      }
+    }
+    R[p] = nr;
+    I[p] = ni;
+  }
+}
 
 // gate G on register slot J (pairs p and p | 2^J)
 template <class G, int J>
@@ -353,6 +419,26 @@ __device__ __forceinline__ void apply_op(Regs &R, Regs &I, uint32_t code, uint32
     case P_PHASE: ph += cond ? (int)arg : 0; break;
     case P_ZERO: zero = zero || cond; break;
     case P_SCALE: scale_all(R, I, __int_as_float((127 - (int)arg) << 23)); break;  // 2^-arg, exact
+    case P_GLOBAL:
+      switch (arg & 15u) {
+        case 1: global_factor<1, 0>(R, I); break;
+        case 2: global_factor<2, 0>(R, I); break;
+        case 3: global_factor<3, 0>(R, I); break;
+        case 4: global_factor<4, 0>(R, I); break;
+        case 5: global_factor<5, 0>(R, I); break;
+        case 6: global_factor<6, 0>(R, I); break;
+        case 7: global_factor<7, 0>(R, I); break;
+        case 8: global_factor<0, 1>(R, I); break;
+        case 9: global_factor<1, 1>(R, I); break;
+        case 10: global_factor<2, 1>(R, I); break;
+        case 11: global_factor<3, 1>(R, I); break;
+        case 12: global_factor<4, 1>(R, I); break;
+        case 13: global_factor<5, 1>(R, I); break;
+        case 14: global_factor<6, 1>(R, I); break;
+        case 15: global_factor<7, 1>(R, I); break;
+        default: break;
+      }
+      break;
     default: break;
   }
 }

@@ -51,14 +51,15 @@ def test_single_process_and_replica_value():
 
 
 def test_algorithmic_flops_of_the_34q_circuit():
-    """4 real operations per amplitude for each square root of X or Y, 2 for each T (half
-    the amplitudes times (1 + i)/sqrt2), none for CZ; the H layer is the generated uniform
-    state: 768 per amplitude for the 34-qubit depth-30 circuit."""
+    """2 real operations per amplitude for each square root of X or Y (an unscaled
+    rotation; its scalar is applied once per circuit), 2 for each T (half the amplitudes
+    times (1 + i)/sqrt2), none for CZ; the H layer is the generated uniform state: 464 per
+    amplitude for the 34-qubit depth-30 circuit."""
     from oracle import circuit as oc
     from paper_1804_04797_gb300 import inputs, sv
     lat = inputs.C34
     n, gates = oc.generate(lat.rows, lat.cols, lat.removed_mask, lat.depth, lat.seed)
     kinds = [k for (k, _a, _b, layer) in gates if layer > 0]
-    want = 4 * sum(k in ('SX', 'SY') for k in kinds) + 2 * sum(k == 'T' for k in kinds)
-    assert 'H' not in kinds and want == 768
+    want = 2 * sum(k in ('SX', 'SY') for k in kinds) + 2 * sum(k == 'T' for k in kinds)
+    assert 'H' not in kinds and want == 464
     assert bench.algorithmic_flops_per_amplitude(sv.sv_generate_circuit(lat)) == want
