@@ -59,7 +59,7 @@ def _peaks():
 # amplitudes; profiles/sv_pass_plain_28q_d30.md, profiles/fused_pass_kernel_f16_28q_d30.md);
 # a pass moves each amplitude once in and once out, so traffic scales with the amplitudes.
 TRAFFIC_PER_ALGORITHMIC_BYTE = {
-    'sv_pass': (2.148424e9 + 2.091639e9) / (16.0 * 2 ** 28),
+    'sv_pass': (2.147776e9 + 2.128476e9) / (16.0 * 2 ** 28),
     'fused_pass_kernel<f16>': (2.147810e9 + 2.087095e9) / (16.0 * 2 ** 28),
 }
 SMS, FP32_LANES_PER_SM = 152, 128
