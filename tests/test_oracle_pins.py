@@ -417,3 +417,28 @@ def test_full_state_is_the_sum_of_branch_outer_products():
         B = ov.run(len(qb), ov._branch_gates(gb, l, 'B'))
         psi += np.outer(B, A).reshape(-1)      # index x_A + (x_B << n_A)
     np.testing.assert_allclose(psi, ov.run(n, gates), rtol=0, atol=1e-12)
+
+
+def test_square_roots_as_scaled_rotations():
+    """The factorisation the plain kernels use (a scalar e^{+-i pi/4} 2^{-1/2} times an
+    unscaled rotation), checked on the oracle's own matrices: X^{1/2} = e^{i pi/4}
+    2^{-1/2} [[1,-i],[-i,1]], Y^{1/2} = e^{i pi/4} 2^{-1/2} [[1,-1],[1,1]], and their
+    adjoints with e^{-i pi/4} and [[1,i],[i,1]], [[1,1],[-1,1]]."""
+    w = np.exp(1j * np.pi / 4) / np.sqrt(2.0)
+    sx, sy = ov.gate_matrix('SX'), ov.gate_matrix('SY')
+    np.testing.assert_allclose(sx, w * np.array([[1, -1j], [-1j, 1]]), atol=1e-15)
+    np.testing.assert_allclose(sy, w * np.array([[1, -1], [1, 1]]), atol=1e-15)
+    np.testing.assert_allclose(sx.conj().T, np.conj(w) * np.array([[1, 1j], [1j, 1]]), atol=1e-15)
+    np.testing.assert_allclose(sy.conj().T, np.conj(w) * np.array([[1, 1], [-1, 1]]), atol=1e-15)
+    # a circuit's square roots leave one scalar: its phase count mod 8 and its 2^{-1/2} count
+    rng = np.random.default_rng(3)
+    kinds = rng.choice(['SX', 'SY'], size=37)
+    total = np.eye(2, dtype=np.complex128)
+    bare = np.eye(2, dtype=np.complex128)
+    rot = {'SX': np.array([[1, -1j], [-1j, 1]]), 'SY': np.array([[1, -1], [1, 1]])}
+    for k in kinds:
+        total = ov.gate_matrix(k) @ total
+        bare = rot[k] @ bare
+    q, u = len(kinds) % 8, len(kinds) % 2
+    scalar = np.exp(1j * np.pi * q / 4) * 2.0 ** (-u / 2) * 2.0 ** (-(len(kinds) - u) / 2)
+    np.testing.assert_allclose(total, scalar * bare, atol=1e-12)
