@@ -56,7 +56,8 @@ typedef struct {
 
 /* Arithmetic of the in-tile update. */
 enum {
-  SV_PREC_PLAIN = 0,  /* fp32 CUDA-core arithmetic, one gate at a time               */
+  SV_PREC_PLAIN = 0,  /* fp32 CUDA-core arithmetic, one gate at a time (the square    */
+                      /* roots as rotations, their scalar applied once per plan)      */
   SV_PREC_TF32X3 = 1, /* fused k-qubit unitaries on tcgen05 tensor cores, 3-pass     */
                       /* split-TF32 products (hi*hi + hi*lo + lo*hi), fp32 accumulate */
   SV_PREC_F16X3 = 2,  /* the same with fp16 hi/lo parts (same 11-bit significand,     */
@@ -70,7 +71,9 @@ typedef struct {
   int precision;  /* SV_PREC_*                                            [PLAIN]       */
   int autotune;   /* reserved: 1 = pick tile_bits by timing (sv_apply_batch)  [0]      */
   void *stream;   /* cudaStream_t used by the handle                      [legacy 0]    */
-  int tile_bits;  /* qubits per gathered tile, fuse_k+5..13               [13]          */
+  int tile_bits;  /* qubits per gathered tile, 6..14 (14: plan-specialised kernels    */
+                  /* only) [12 on plan-specialised and tensor-core kernels, 13 on the  */
+                  /* interpreting kernel]                                              */
   int low_bits;   /* contiguous low qubits in every tile (coalescing)     [4]           */
   int jit;        /* plain path: run each plan on kernels compiled for it at run time */
                   /* (NVRTC; cached in memory and in the library's directory):       */
@@ -315,7 +318,10 @@ sv_status sv_amplitudes_by_inner_product(const sv_lattice *lat, int split_layer,
 sv_status sv_jit_check(int n_qubits, const sv_gate *gates, size_t n_gates, const sv_options *opts,
                        int fresh_state, char *log, size_t log_cap);
 
+/* Turn the per-kernel timing of the handle on (on != 0, counters cleared) or off; it
+ * records a CUDA event pair around every pass launch on the handle's stream. */
 sv_status sv_set_profiling(sv_state *s, int on);
+/* The counters since profiling was turned on (synchronises the handle's stream). */
 sv_status sv_get_profile(sv_state *s, sv_profile *out);
 
 #ifdef __cplusplus
