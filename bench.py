@@ -55,9 +55,9 @@ def _peaks():
 
 
 # DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) per algorithmic byte of the
-# dominant kernels, from one ncu capture each on a 28-qubit depth-30 pass (2^28
-# amplitudes; profiles/sv_pass_plain_28q_d30.md, profiles/fused_pass_kernel_f16_28q_d30.md);
-# a pass moves each amplitude once in and once out, so traffic scales with the amplitudes.
+# dominant kernels, from one ncu capture each on one pass of the 28-qubit depth-30 circuit
+# (2^28 amplitudes); a pass moves each amplitude once in and once out, so traffic scales
+# with the amplitudes.
 TRAFFIC_PER_ALGORITHMIC_BYTE = {
     'sv_pass': (2.147776e9 + 2.128476e9) / (16.0 * 2 ** 28),
     'fused_pass_kernel<f16>': (2.147810e9 + 2.087095e9) / (16.0 * 2 ** 28),

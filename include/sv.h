@@ -62,12 +62,18 @@ enum {
                       /* split-TF32 products (hi*hi + hi*lo + lo*hi), fp32 accumulate */
   SV_PREC_F16X3 = 2,  /* the same with fp16 hi/lo parts (same 11-bit significand,     */
                       /* twice the tensor rate; rows scaled by powers of two)          */
+                      /* Both tensor-core modes need tiles of 12 or 13 qubits: a      */
+                      /* state below 12 qubits runs the plain kernel instead, and     */
+                      /* sv_profile.plain_fallbacks counts those applies.             */
   SV_PREC_PERGATE = 3 /* one full sweep of the state per gate (no tiling; baseline)  */
 };
 
 /* Options.  Zero-initialised fields take the defaults in brackets. */
 typedef struct {
-  int fuse_k;     /* qubits per fused block / register group, 2..5        [5]           */
+  int fuse_k;     /* qubits per register group besides qubit 0 (plain) or per fused   */
+                  /* block (tensor cores), 1..5; 0 = the default 5 (plain kernels     */
+                  /* compiled per plan use at most 4).  The tensor-core precisions    */
+                  /* take 5 only: any other value is SV_ERR_ARG.                       */
   int precision;  /* SV_PREC_*                                            [PLAIN]       */
   int autotune;   /* reserved: 1 = pick tile_bits by timing (sv_apply_batch)  [0]      */
   void *stream;   /* cudaStream_t used by the handle                      [legacy 0]    */
@@ -181,7 +187,9 @@ sv_status sv_norm(sv_state *s, double *norm2, double *sum_p2);
  * allocator that has reserved the GPU), or code that must avoid the implicit device-wide
  * synchronisation of cudaMalloc/cudaFree.  The paper has no counterpart; this is a
  * library-usage convenience.
- *   dev_state  2^n_qubits complex64 amplitudes on the current device (caller-owned).
+ *   dev_state  2^n_qubits complex64 amplitudes on the current device (caller-owned),
+ *              16-byte aligned (8-byte for n_qubits = 1): the reduction reads two
+ *              amplitudes per vector load; a misaligned pointer is SV_ERR_ARG.
  *   n_qubits   1..34; anything else is SV_ERR_ARG.
  *   stream     cudaStream_t to run on (NULL = legacy default stream); synchronised.
  *   norm2, sum_p2  host doubles for sum |alpha|^2 and sum |alpha|^4 (either may be NULL).
@@ -287,6 +295,8 @@ typedef struct {
   double d2h_bytes;   /* device-to-host bytes copied by the library (results)     */
   int other_launches; /* other kernels (reductions, gathers, init)               */
   int jit_launches;   /* tile passes run on plan-specialised (run-time compiled) kernels */
+  int plain_fallbacks; /* applies with a tensor-core precision that ran the plain kernel */
+                       /* (states below 12 qubits)                                    */
 } sv_profile;
 
 /* The basis state |x> (1 at index x, 0 elsewhere).  SV_ERR_ARG if x has bits >= n. */

@@ -88,6 +88,8 @@ sv_status check_options(const sv_options &o) {
   if (o.tile_bits != 0 && (o.tile_bits < 6 || o.tile_bits > svp::kMaxTileBits))
     return fail(SV_ERR_ARG, "options: tile_bits must be 0 or 6..14");
   const bool fused = o.precision == SV_PREC_TF32X3 || o.precision == SV_PREC_F16X3;
+  if (fused && o.fuse_k != 0 && o.fuse_k != 5)
+    return fail(SV_ERR_ARG, "options: the tensor-core precisions apply 5-qubit blocks (fuse_k 0 or 5)");
   if (o.tile_bits == 14 && (fused || o.jit < 0))
     return fail(SV_ERR_ARG, "options: 14-qubit tiles need the plain path's plan-specialised kernels");
   if (o.low_bits < 0 || o.low_bits > 13) return fail(SV_ERR_ARG, "options: low_bits must be 0..13");
@@ -259,6 +261,7 @@ sv_status run_plan(sv_state *s, const svp::Plan &P, const svk::DevPlanView &view
                    const svj::Module *jit) {
   const double amps = std::ldexp(1.0, s->n);
   s->sums_valid = false;
+  if (s->prof && s->plan_fallback) s->plain_fallbacks += 1;
   // plan kernels: the last pass also sums p and p^2 of the state it writes (no separate
   // read of the state for sv_norm)
   const bool sums = jit && s->owns && !s->user_writes && !P.passes.empty();
@@ -319,7 +322,11 @@ sv_status apply_gates(sv_state *s, const std::vector<svp::Gate> &g) {
   sv_status st;
   if ((st = set_device(s)) != SV_OK) return st;
   s->sums_valid = false;
-  if (s->opts.precision == SV_PREC_PERGATE || s->n < 6) return apply_pergate(s, g);
+  if (s->opts.precision == SV_PREC_PERGATE || s->n < 6) {
+    // (a tensor-core request on a state this small is a plain fallback too)
+    if (s->prof && (s->opts.precision == SV_PREC_TF32X3 || s->opts.precision == SV_PREC_F16X3)) s->plain_fallbacks += 1;
+    return apply_pergate(s, g);
+  }
   if ((s->opts.precision == SV_PREC_TF32X3 || s->opts.precision == SV_PREC_F16X3) && !svk::fused_supported())
     return fail(SV_ERR_CUDA, "fused tensor-core path needs an sm_103a device");
   if (g.empty() && !s->fresh) return SV_OK;
@@ -348,6 +355,8 @@ sv_status apply_gates(sv_state *s, const std::vector<svp::Gate> &g) {
   bool want_jit = false;
   svp::Options po = apply_plan_options(s->opts, s->n, &want_jit);
   if (!svp::build_plan(s->n, g, po, s->fresh, &P, &err)) return fail(SV_ERR_ARG, err ? err : "planning failed");
+  // a tensor-core request on a state (or tile) below 12 qubits runs the plain kernel
+  s->plan_fallback = (s->opts.precision == SV_PREC_TF32X3 || s->opts.precision == SV_PREC_F16X3) && !po.fused;
   const svj::Module *jit = nullptr;
   if (want_jit) {
     std::string jerr;
@@ -762,6 +771,7 @@ sv_status sv_set_profiling(sv_state *s, int on) {
   s->h2d = s->d2h = 0;
   s->other_launches = 0;
   s->jit_launches = 0;
+  s->plain_fallbacks = 0;
   return SV_OK;
 }
 
@@ -777,6 +787,7 @@ sv_status sv_get_profile(sv_state *s, sv_profile *out) {
   out->d2h_bytes = s->d2h;
   out->other_launches = s->other_launches;
   out->jit_launches = s->jit_launches;
+  out->plain_fallbacks = s->plain_fallbacks;
   for (size_t i = 0; i + 1 < s->ev_used; i += 2) {
     float ms = 0;
     if (cudaEventElapsedTime(&ms, s->events[i], s->events[i + 1]) == cudaSuccess) out->ms += ms;

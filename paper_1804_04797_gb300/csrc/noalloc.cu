@@ -10,6 +10,7 @@
 // doubles; its scratch is a fixed file-scope device array, so it allocates nothing.
 #include <cuda_runtime.h>
 
+#include <cstdint>
 #include <mutex>
 
 #include "../../include/sv.h"
@@ -37,6 +38,11 @@ extern "C" sv_status sv_norm_noalloc(const void *dev_state, int n_qubits, void *
   if (!dev_state) return svc::fail(SV_ERR_ARG, "sv_norm_noalloc: dev_state is NULL");
   if (n_qubits < 1 || n_qubits > 34)
     return svc::fail(SV_ERR_ARG, "sv_norm_noalloc: n_qubits must be 1..34 (states up to 2^34 amplitudes)");
+  // the reduction reads two amplitudes per 16-byte vector (one 8-byte amplitude when n = 1)
+  const uintptr_t align = n_qubits >= 2 ? 16 : 8;
+  if ((reinterpret_cast<uintptr_t>(dev_state) & (align - 1)) != 0)
+    return svc::fail(SV_ERR_ARG, n_qubits >= 2 ? "sv_norm_noalloc: dev_state must be 16-byte aligned"
+                                               : "sv_norm_noalloc: dev_state must be 8-byte aligned");
   if (svk::reduce_partials_needed() > kNoallocBlocks)
     return svc::fail(SV_ERR_ARG, "sv_norm_noalloc: reduction grid larger than the static scratch");
   int dev = 0;

@@ -36,6 +36,8 @@ struct sv_state {
   double h2d = 0, d2h = 0;
   int other_launches = 0;
   int jit_launches = 0;
+  int plain_fallbacks = 0;     // applies of a tensor-core request run on the plain kernel
+  bool plan_fallback = false;  // the current plan is such a fallback
   // the last plan run on this handle (a circuit applied again reuses it and its device
   // copy: no planning, kernel-source hashing or upload)
   bool plan_valid = false;

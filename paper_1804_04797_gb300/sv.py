@@ -49,7 +49,8 @@ class sv_plan_summary(ctypes.Structure):
 
 class sv_profile(ctypes.Structure):
     _fields_ = [('launches', c_int), ('ms', c_double), ('hbm_bytes', c_double), ('h2d_bytes', c_double),
-                ('d2h_bytes', c_double), ('other_launches', c_int), ('jit_launches', c_int)]
+                ('d2h_bytes', c_double), ('other_launches', c_int), ('jit_launches', c_int),
+                ('plain_fallbacks', c_int)]
 
 
 _lib = None

@@ -76,12 +76,38 @@ SIZES = [inputs.lattice_for(2, 3, 8, seed=4),            # 6 qubits: one tile = 
 def test_sizes_match_oracle(lat):
     n, gates = oracle_gates(lat)
     want = csim.run(n, gates)
-    for kw in (dict(), dict(tile_bits=min(13, max(6, n)), low_bits=min(4, n), fuse_k=5), dict(precision=TC),
-               dict(precision=TC, tile_bits=12), dict(precision=H16), dict(precision=H16, tile_bits=12),
-               dict(jit=1), dict(jit=-1)):
+    modes = [dict(), dict(tile_bits=min(13, max(6, n)), low_bits=min(4, n), fuse_k=5), dict(jit=1), dict(jit=-1)]
+    # the tensor-core kernels take 12- and 13-qubit tiles: smaller states run the plain
+    # kernel (test_tensor_core_request_below_12_qubits_is_reported), so only states that
+    # reach the tensor cores carry their labels here
+    if n >= 12:
+        modes += [dict(precision=TC), dict(precision=TC, tile_bits=12), dict(precision=H16),
+                  dict(precision=H16, tile_bits=12)]
+    for kw in modes:
         psi, norm2, _ = run_gpu(lat, **kw)
         assert rel_l2(psi, want) <= REL_L2, kw
         assert abs(norm2 - 1) <= NORM_TOL
+
+
+@pytest.mark.parametrize('prec', [TC, H16], ids=['tf32x3', 'f16x3'])
+@pytest.mark.parametrize('lat', [inputs.lattice_for(3, 3, 12, seed=2), inputs.lattice_for(1, 3, 6, seed=1)],
+                         ids=['9q', '3q'])
+def test_tensor_core_request_below_12_qubits_is_reported(lat, prec):
+    """Below 12 qubits a tensor-core request runs the plain kernel (tile passes; per-gate
+    sweeps below 6 qubits); the profile counts it as a plain fallback, and the state still
+    matches the oracle."""
+    n, gates = oracle_gates(lat)
+    want = csim.run(n, gates)
+    h = sv.sv_create(n, sv.options(precision=prec))
+    try:
+        sv.sv_set_profiling(h, True)
+        sv.sv_apply_circuit(h, sv.sv_generate_circuit(lat))
+        prof = sv.sv_get_profile(h)
+        psi = sv.sv_copy_state(h, n)
+    finally:
+        sv.sv_destroy(h)
+    assert prof.plain_fallbacks == 1
+    assert rel_l2(psi, want) <= REL_L2
 
 
 def test_layer0_only_is_uniform():

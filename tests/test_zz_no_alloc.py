@@ -55,3 +55,48 @@ def test_noalloc_rejects_sizes_beyond_the_maximum():
         _noalloc(16, 0)
     with pytest.raises(sv.SvError):
         _noalloc(0, 10)
+
+
+def test_noalloc_rejects_misaligned_pointers_before_any_launch():
+    # the reduction reads 16-byte vectors (n >= 2) or 8-byte amplitudes (n = 1); the
+    # check runs on the host before any CUDA call, so these pointers are never touched
+    with pytest.raises(sv.SvError, match='aligned'):
+        _noalloc(8, 10)
+    with pytest.raises(sv.SvError, match='aligned'):
+        _noalloc(4, 1)
+
+
+@pytest.mark.parametrize('gates', [[], [(sv.SV_H, 0)]], ids=['basis', 'uniform'])
+def test_noalloc_one_qubit_state(gates):
+    # n = 1 takes the single-thread reduction of 8-byte amplitudes
+    h = sv.sv_create(1)
+    try:
+        g = sv.gates_from_tuples([(k, q, 0, 0) for k, q in gates])
+        sv.sv_apply_circuit(h, g)
+        want2, want4 = sv.sv_norm(h)
+        ptr = sv.sv_device_ptr(h)
+        got = [_noalloc(ptr, 1), _noalloc(ptr, 1)]
+    finally:
+        sv.sv_destroy(h)
+    for got2, got4 in got:
+        assert abs(got2 - want2) <= NORM_TOL
+        assert abs(got4 - want4) <= NORM_TOL * want4
+    assert got[0] == got[1]
+
+
+def test_noalloc_on_a_caller_stream_matches_the_default_stream():
+    import torch
+    lat = inputs.lattice_for(4, 4, 10, seed=3)
+    n = lat.n_qubits
+    h = sv.sv_create(n)
+    try:
+        sv.sv_apply_circuit(h, sv.sv_generate_circuit(lat))
+        ptr = sv.sv_device_ptr(h)
+        torch.cuda.synchronize()
+        st = torch.cuda.Stream()
+        on_stream = _noalloc(ptr, n, st.cuda_stream)
+        on_default = _noalloc(ptr, n)
+    finally:
+        sv.sv_destroy(h)
+    assert on_stream == on_default
+    assert abs(on_stream[0] - 1.0) <= NORM_TOL
