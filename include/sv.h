@@ -85,6 +85,17 @@ typedef struct {
                   /* (NVRTC; cached in memory and in the library's directory):       */
                   /* 1 = always (error if NVRTC fails), -1 = never, 0 = for n >= 24 [0] */
                   /* (sv_apply_batch: per circuit, see there)                         */
+  int pipeline;   /* plain path on plan-specialised kernels: 0 = the pipelined         */
+                  /* persistent kernel (one CTA per SM; a producer warp streams tiles  */
+                  /* into a ring of shared-memory slots with TMA tensor copies while   */
+                  /* compute groups run the stages) wherever the tile shape allows it  */
+                  /* (10..13 tile qubits, low_bits 4) [0]; -1 = one CTA per tile in    */
+                  /* flight, tile read with per-thread asynchronous copies             */
+  int norm_restore; /* tensor-core precisions: 0 = restore every tile's norm in the    */
+                  /* pass's last stage (unbiased stochastic rounding; the tensor      */
+                  /* cores' fp32 accumulation truncates toward zero, ~1e-7 per stage)  */
+                  /* [0]; -1 = leave the products as the tensor cores computed them    */
+                  /* (the raw error; the norm is then a check, not a correction)       */
 } sv_options;
 
 /* An R x C lattice circuit: bit r*cols+c of removed_mask drops site (r,c); kept sites
@@ -276,6 +287,8 @@ typedef struct {
   int init_uniform;   /* 1 if the layer-0 H gates became the uniform first pass           */
   double hbm_bytes;   /* algorithmic bytes of the passes: 16 * 2^n per read-write pass,   */
                       /* 8 * 2^n for the write-only first pass                             */
+  int matrix_stages;  /* stages with gates inside their register qubits (on the tensor-    */
+                      /* core path: one 32x32 complex product per tile each)               */
 } sv_plan_summary;
 
 /* Plan a gate list for an n-qubit state without touching the device.  order_out (may
@@ -333,6 +346,11 @@ sv_status sv_jit_check(int n_qubits, const sv_gate *gates, size_t n_gates, const
 sv_status sv_set_profiling(sv_state *s, int on);
 /* The counters since profiling was turned on (synchronises the handle's stream). */
 sv_status sv_get_profile(sv_state *s, sv_profile *out);
+/* Each timed launch since profiling was turned on, in launch order (synchronises the
+ * handle's stream): *n_out = the number of launches; the first min(n, cap) entries of
+ * ms_out (device time of the launch, CUDA events on the handle's stream) and bytes_out
+ * (its algorithmic bytes) are written; either array may be NULL. */
+sv_status sv_get_launch_times(sv_state *s, double *ms_out, double *bytes_out, size_t cap, size_t *n_out);
 
 #ifdef __cplusplus
 }

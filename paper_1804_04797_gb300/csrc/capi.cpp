@@ -76,6 +76,10 @@ svp::Options apply_plan_options(const sv_options &o, int n, bool *want_jit) {
     po.rk = svj::register_slots();
     po.r = std::min(po.r, po.rk);
     if (o.tile_bits == 0) po.m = svj::kTileBits;
+    // the pipelined kernel reads tiles as 8-row TMA boxes (4 low qubits) into groups of
+    // at least a warp: 10..13 tile qubits
+    const int m = std::min(po.m, n);
+    if (o.pipeline >= 0 && po.c == 4 && m >= 10 && m <= 13) po.layout = 1;
   }
   return po;
 }
@@ -94,6 +98,8 @@ sv_status check_options(const sv_options &o) {
     return fail(SV_ERR_ARG, "options: 14-qubit tiles need the plain path's plan-specialised kernels");
   if (o.low_bits < 0 || o.low_bits > 13) return fail(SV_ERR_ARG, "options: low_bits must be 0..13");
   if (o.jit < -1 || o.jit > 1) return fail(SV_ERR_ARG, "options: jit must be -1, 0 or 1");
+  if (o.pipeline < -1 || o.pipeline > 0) return fail(SV_ERR_ARG, "options: pipeline must be -1 or 0");
+  if (o.norm_restore < -1 || o.norm_restore > 0) return fail(SV_ERR_ARG, "options: norm_restore must be -1 or 0");
   const int m = o.tile_bits > 0 ? o.tile_bits : 13;
   const int c = o.low_bits > 0 ? o.low_bits : 4;
   if (c > m || m - c > 10) return fail(SV_ERR_ARG, "options: need low_bits <= tile_bits <= low_bits + 10");
@@ -131,6 +137,25 @@ using namespace svc;
 // ---------------------------------------------------------------------------------------
 
 namespace svc {
+
+sv_status take_pending_error(sv_state *s) {
+  if (!s->err_pending) return SV_OK;
+  int h_err = 0;
+  cudaError_t e = cudaMemcpyAsync(&h_err, s->err_pending, sizeof(int), cudaMemcpyDeviceToHost, s->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s->stream);
+  s->err_pending = nullptr;
+  if (e != cudaSuccess) {
+    s->broken = true;
+    s->plan_valid = false;
+    return cuda_fail(e, "tile pass");
+  }
+  if (h_err != 0) {
+    s->broken = true;
+    s->plan_valid = false;
+    return fail(SV_ERR_TIMEOUT, "tile pass: a bounded wait gave up (state undefined)");
+  }
+  return SV_OK;
+}
 
 sv_status set_device(sv_state *s) {
   cudaError_t e = cudaSetDevice(s->device);
@@ -285,6 +310,9 @@ sv_status run_plan(sv_state *s, const svp::Plan &P, const svk::DevPlanView &view
     if (jit && s->prof) s->jit_launches += 1;
     if (e != cudaSuccess) { s->broken = true; return cuda_fail(e, "tile pass kernel"); }
   }
+  if (jit)
+    for (size_t p = 0; p < P.passes.size(); ++p)
+      if (svj::pass_is_pipelined(P, (int)p)) s->err_pending = view.err;
   if (sums) {
     const cudaError_t e = svk::launch_norm_final(s->d_sums + 2, (int)grid, s->d_sums, s->stream);
     if (e != cudaSuccess) { s->broken = true; return cuda_fail(e, "norm sums"); }
@@ -336,8 +364,8 @@ sv_status apply_gates(sv_state *s, const std::vector<svp::Gate> &g) {
     const unsigned char *b = static_cast<const unsigned char *>(p);
     for (size_t i = 0; i < len; ++i) key = (key ^ b[i]) * 1099511628211ull;
   };
-  const int head[7] = {s->n, s->fresh ? 1 : 0, s->opts.precision, s->opts.fuse_k, s->opts.tile_bits,
-                       s->opts.low_bits, s->opts.jit};
+  const int head[9] = {s->n, s->fresh ? 1 : 0, s->opts.precision, s->opts.fuse_k, s->opts.tile_bits,
+                       s->opts.low_bits, s->opts.jit, s->opts.pipeline, s->opts.norm_restore};
   mix(head, sizeof(head));
   if (!g.empty()) mix(g.data(), g.size() * sizeof(svp::Gate));
   if (s->plan_valid && s->plan_key == key) {
@@ -365,6 +393,7 @@ sv_status apply_gates(sv_state *s, const std::vector<svp::Gate> &g) {
     if (!jit) {
       // no compiler: the interpreting kernel, with its register width, on tiles it takes
       po.m = std::min(po.m, svk::tile_pass_max_bits());
+      po.layout = 0;
       po.rk = svk::tile_pass_register_slots();
       po.r = std::min(plan_options(s->opts).r, po.rk);
       P = svp::Plan();
@@ -374,6 +403,8 @@ sv_status apply_gates(sv_state *s, const std::vector<svp::Gate> &g) {
   }
   const bool f16 = s->opts.precision == SV_PREC_F16X3;
   if (po.fused && (st = build_stage_mats(&P, g, std::min(po.r, std::min(po.m, s->n)), f16)) != SV_OK) return st;
+  if (po.fused && s->opts.norm_restore < 0)
+    for (svp::DevPass &dp : P.passes) dp.flags |= svp::PF_RAW;
   if (po.fused)
     for (const svp::DevPass &dp : P.passes)
       if (dp.stage_count > 256) return fail(SV_ERR_ARG, "fused path: more than 256 stages in one pass");
@@ -407,7 +438,8 @@ sv_status apply_gates_inner(sv_state *s, const std::vector<svp::Gate> &g, const 
     const unsigned char *b = static_cast<const unsigned char *>(p);
     for (size_t i = 0; i < len; ++i) key = (key ^ b[i]) * 1099511628211ull;
   };
-  const int head[6] = {s->n, s->opts.precision, s->opts.fuse_k, s->opts.tile_bits, s->opts.low_bits, s->opts.jit};
+  const int head[7] = {s->n, s->opts.precision, s->opts.fuse_k, s->opts.tile_bits, s->opts.low_bits, s->opts.jit,
+                       s->opts.pipeline};
   mix(head, sizeof(head));
   mix(g.data(), g.size() * sizeof(svp::Gate));
   if (!(s->plan_valid && s->plan_key == key)) {
@@ -451,9 +483,16 @@ sv_status apply_gates_inner(sv_state *s, const std::vector<svp::Gate> &g, const 
   if (e == cudaSuccess) e = svk::launch_norm_final(s->d_sums + 2, (int)grid, s->d_sums, s->stream);
   if (e == cudaSuccess) e = cudaMemcpyAsync(h, s->d_sums, sizeof(h), cudaMemcpyDeviceToHost, s->stream);
   if (e == cudaSuccess) e = cudaStreamSynchronize(s->stream);
+  if (e != cudaSuccess) {
+    s->broken = true;
+    return cuda_fail(e, "inner product pass");
+  }
+  for (size_t p = 0; p < P.passes.size(); ++p)
+    if (svj::pass_is_pipelined(P, (int)p)) s->err_pending = s->plan_view.err;
+  const sv_status werr = take_pending_error(s);
   // the last pass did not store: the state is not the circuit's result
   s->broken = true;
-  if (e != cudaSuccess) return cuda_fail(e, "inner product pass");
+  if (werr != SV_OK) return werr;
   if (s->prof) {
     s->other_launches += 1;
     s->d2h += sizeof(h);
@@ -583,6 +622,7 @@ sv_status sv_copy_state(sv_state *s, void *dst) {
   if (s->broken) return fail(SV_ERR_STATE, "state is unusable after an earlier failure");
   sv_status st = set_device(s);
   if (st != SV_OK) return st;
+  if ((st = take_pending_error(s)) != SV_OK) return st;
   if ((st = materialize(s)) != SV_OK) return st;
   cudaError_t e = cudaMemcpyAsync(dst, s->psi, sizeof(float2) << s->n, cudaMemcpyDefault, s->stream);
   if (e == cudaSuccess) e = cudaStreamSynchronize(s->stream);
@@ -621,6 +661,7 @@ static sv_status gather_common(sv_state *s, const uint64_t *bits, size_t m, doub
   if (m == 0) return SV_OK;
   sv_status st = set_device(s);
   if (st != SV_OK) return st;
+  if ((st = take_pending_error(s)) != SV_OK) return st;
   if ((st = materialize(s)) != SV_OK) return st;
   const size_t need = m * sizeof(uint64_t) + 2 * m * sizeof(double) + 512;
   if ((st = ensure_device_buffer(&s->d_scratch, &s->d_scratch_cap, need)) != SV_OK) return st;
@@ -656,6 +697,7 @@ sv_status sv_norm(sv_state *s, double *norm2, double *sum_p2) {
   if (s->broken) return fail(SV_ERR_STATE, "state is unusable after an earlier failure");
   sv_status st = set_device(s);
   if (st != SV_OK) return st;
+  if ((st = take_pending_error(s)) != SV_OK) return st;
   if ((st = materialize(s)) != SV_OK) return st;
   if (s->sums_valid) {
     // summed by the last pass that wrote the state
@@ -709,6 +751,8 @@ sv_status sv_plan(int n_qubits, const sv_gate *gates, size_t n_gates, const sv_o
     summary->ops = (int)P.ops.size() - 1;  // without the closing no-op
     summary->init_uniform = P.init_uniform ? 1 : 0;
     summary->hbm_bytes = P.hbm_bytes;
+    summary->matrix_stages = 0;
+    for (const std::vector<int> &sg : P.stage_gates) summary->matrix_stages += sg.empty() ? 0 : 1;
   }
   if (order_out) std::copy(P.order.begin(), P.order.end(), order_out);
   if (pass_out) std::copy(P.pass_of.begin(), P.pass_of.end(), pass_out);
@@ -739,6 +783,8 @@ sv_status sv_jit_check(int n_qubits, const sv_gate *gates, size_t n_gates, const
   po.pack = true;
   po.rk = svj::register_slots();
   po.r = std::min(po.r, po.rk);
+  if (o.tile_bits == 0) po.m = svj::kTileBits;
+  if (o.pipeline >= 0 && po.c == 4 && std::min(po.m, n_qubits) >= 10 && std::min(po.m, n_qubits) <= 13) po.layout = 1;
   svp::Plan P;
   const char *err = nullptr;
   if (!svp::build_plan(n_qubits, g, po, fresh_state != 0, &P, &err))
@@ -750,7 +796,10 @@ sv_status sv_jit_check(int n_qubits, const sv_gate *gates, size_t n_gates, const
     // and the last pass as the inner-product variant (the backward states of the
     // inner-product amplitudes)
     std::string cubin, lg2;
-    ok = svj::compile(svj::pass_source(P, po.rk, (int)P.passes.size() - 1, true), "sm_103a", &cubin, &lg2);
+    const int last = (int)P.passes.size() - 1;
+    ok = svj::compile(svj::pass_is_pipelined(P, last) ? svj::pipe_pass_source(P, po.rk, last, true)
+                                                      : svj::pass_source(P, po.rk, last, true),
+                      "sm_103a", &cubin, &lg2);
     if (!lg2.empty()) lg += "inner last pass: " + lg2;
   }
   if (log && log_cap) {
@@ -792,6 +841,25 @@ sv_status sv_get_profile(sv_state *s, sv_profile *out) {
     float ms = 0;
     if (cudaEventElapsedTime(&ms, s->events[i], s->events[i + 1]) == cudaSuccess) out->ms += ms;
     out->hbm_bytes += s->ev_bytes[i / 2];
+  }
+  return SV_OK;
+}
+
+sv_status sv_get_launch_times(sv_state *s, double *ms_out, double *bytes_out, size_t cap, size_t *n_out) {
+  clear_error();
+  if (!s || !n_out) return fail(SV_ERR_ARG, "NULL argument");
+  cudaError_t e = cudaStreamSynchronize(s->stream);
+  if (e != cudaSuccess) return cuda_fail(e, "sv_get_launch_times");
+  const size_t n = s->ev_used / 2;
+  *n_out = n;
+  for (size_t i = 0; i < n && i < cap; ++i) {
+    float ms = 0;
+    if (ms_out) {
+      e = cudaEventElapsedTime(&ms, s->events[2 * i], s->events[2 * i + 1]);
+      if (e != cudaSuccess) return cuda_fail(e, "sv_get_launch_times");
+      ms_out[i] = ms;
+    }
+    if (bytes_out) bytes_out[i] = s->ev_bytes[i];
   }
   return SV_OK;
 }

@@ -28,6 +28,18 @@ int register_slots();
 // CTAs per SM) measured faster than 13 (7 passes, two CTAs) and 14 (6 passes, one).
 constexpr int kTileBits = 12;
 
+// Pipelined kernels (plans with Options::layout = 1, tile_pipe.cuh): compute groups and
+// shared-memory tile slots per CTA for a tile size; false where the tile size has none.
+// 12-qubit tiles: three groups of 128 threads with two 32 KB slots each (one CTA per SM;
+// 13 warps, so up to 128 registers a thread).  Slots are a multiple of the groups.
+constexpr int kPipeGroups12 = 3;
+constexpr int kPipeSlots12 = 6;
+bool pipe_shape(int m, int *groups, int *slots);
+// Whether pass `pass` of P runs on the pipelined kernel (layout-1 plan, at least one stage).
+bool pass_is_pipelined(const svp::Plan &P, int pass);
+// CUDA source of the pipelined kernel ("sv_pass") of one pass of a layout-1 packed plan.
+std::string pipe_pass_source(const svp::Plan &P, int kpr, int pass, bool inner = false);
+
 // CUDA source of the kernel ("sv_pass") of one pass of a packed plan.  kpr: register
 // slots besides the pack bit (the plan's rk).  inner (the last pass only): instead of
 // storing the state, the kernel sums conj(state) * other over it into per-CTA partials.

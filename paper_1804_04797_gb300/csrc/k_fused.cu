@@ -330,7 +330,7 @@ fused_pass_kernel(float2 *__restrict__ psi, DevPlanView plan, int pass_index, ui
     // ~0.3 ulp of every output per stage (a systematic norm drift of ~1e-7 per stage);
     // the tile's norm is measured in the first stage and restored in the last one with
     // unbiased stochastic rounding.
-    const bool keep_norm = (P.flags & svp::PF_UNITARY) && n_mma > 0;
+    const bool keep_norm = (P.flags & svp::PF_UNITARY) && !(P.flags & svp::PF_RAW) && n_mma > 0;
     int q = 0;  // MMA stage index within this tile
     for (int s = 0; s < P.stage_count; ++s) {
       const uint32_t si = P.stage_begin + s;

@@ -117,20 +117,42 @@ void order_group_bits(int m, const std::vector<int> &nonr, uint8_t *out) {
   for (size_t i = 0; i < all.size(); ++i) out[i] = (uint8_t)all[i];
 }
 
-// Packed tiles: pair index k (tile bits 1..m-1) is stored at 16-byte slot
-// k ^ ((k>>3 ^ k>>6 ^ k>>9) & 7); pair bit i toggles slot bit (i mod 3).  A quarter warp
-// (8 lanes, one 128-byte wavefront of 16-byte accesses) is conflict-free when its three
-// lane bits have distinct residues.
-uint32_t pack_phys(uint32_t k) { return k ^ (((k >> 3) ^ (k >> 6) ^ (k >> 9)) & 7u); }
-uint32_t pack_offset(int tile_bit) { return 16u * pack_phys(1u << (tile_bit - 1)); }
+// Packed tiles: pair index k (tile bits 1..m-1) is stored at 16-byte slot pack_phys(k,
+// layout).  Layout 0: pair bit i toggles slot bit (i mod 3).  Layout 1 (the TMA 128-byte
+// swizzle): tile bits 1..3 toggle slot bits 0..2 directly, tile bits 4..6 (a box's row)
+// toggle them too, higher tile bits none.  A quarter warp (8 lanes, one 128-byte wavefront
+// of 16-byte accesses) is conflict-free when its three lane bits toggle three independent
+// bank-group bit patterns.
+uint32_t pack_offset(int tile_bit, int layout) { return 16u * pack_phys(1u << (tile_bit - 1), layout); }
 
-void order_group_bits_packed(const std::vector<int> &nonr, uint8_t *out) {
+// The bank-group bits (16-byte slot bits 0..2) a tile bit toggles.
+uint32_t bank_bits(int tile_bit, int layout) { return pack_phys(1u << (tile_bit - 1), layout) & 7u; }
+
+// Order the stage's group bits with three conflict-free lane bits first.  Layout 1, last
+// stage of a pass: tile bits 1..3 go first when all three are group bits, so that a
+// quarter warp's 16-byte stores of the last stage (straight from registers to HBM) fill
+// one 128-byte line.
+void order_group_bits_packed(const std::vector<int> &nonr, uint8_t *out, int layout, bool last_stage) {
   std::vector<int> lanes, rest;
-  bool used_res[3] = {false, false, false};
-  for (int b : nonr) {
-    const int res = (b - 1) % 3;
-    if ((int)lanes.size() < 3 && !used_res[res]) { used_res[res] = true; lanes.push_back(b); }
-    else rest.push_back(b);
+  std::vector<int> cand = nonr;
+  if (layout == 1) {
+    // low tile bits first (coalesced stores), then the box rows, then the rest
+    std::stable_sort(cand.begin(), cand.end(), [](int a, int b) { return a < b; });
+    const bool low3 = std::count(nonr.begin(), nonr.end(), 1) && std::count(nonr.begin(), nonr.end(), 2) &&
+                      std::count(nonr.begin(), nonr.end(), 3);
+    if (last_stage && low3) {
+      lanes = {1, 2, 3};
+      for (int b : cand)
+        if (b > 3) rest.push_back(b);
+    }
+  }
+  if (lanes.empty()) {
+    uint32_t span = 0;  // bank-group patterns covered so far (unit vectors in both layouts)
+    for (int b : cand) {
+      const uint32_t v = layout == 1 ? bank_bits(b, layout) : (1u << ((b - 1) % 3));
+      if ((int)lanes.size() < 3 && v && !(span & v)) { span |= v; lanes.push_back(b); }
+      else rest.push_back(b);
+    }
   }
   std::vector<int> all = lanes;
   for (int b : rest) all.push_back(b);
@@ -144,6 +166,7 @@ bool build_plan(int n, const std::vector<Gate> &gates, const Options &opt, bool 
   Plan &P = *plan;
   P = Plan();
   P.n = n;
+  P.layout = opt.layout;
   const int m = std::min(opt.m, n);
   const int c = std::min(opt.c, m);
   const bool pack = opt.pack;
@@ -152,6 +175,7 @@ bool build_plan(int n, const std::vector<Gate> &gates, const Options &opt, bool 
   const int r = std::min(std::min(opt.r, rk), m);
   if (m > kMaxTileBits || rk > kMaxReg || r < 1 || c < 0 || m - rk > 12) { *err = "bad tile shape"; return false; }
   if (pack && (rk < 1 || m < rk + 1 || c < 1)) { *err = "packed plan needs tiles of >= rk + 1 qubits"; return false; }
+  if (opt.layout == 1 && (!pack || c != 4 || m < 7 || m > 13)) { *err = "TMA tile layout needs packed tiles of 7..13 qubits with 4 low ones"; return false; }
 
   // leading layer of H on every qubit of a fresh state -> uniform first pass
   size_t start = 0;
@@ -296,6 +320,7 @@ bool build_plan(int n, const std::vector<Gate> &gates, const Options &opt, bool 
       std::vector<int> inner, post;
       const std::pair<int, int> placed = run_stage(Rm, done, &inner, &post);
       left -= (size_t)placed.second;
+      const bool last_stage = left == 0;
       std::vector<int> R;
       for (int bb = pack ? 1 : 0; bb < m; ++bb)
         if ((Rm >> bb) & 1u) R.push_back(bb);
@@ -313,7 +338,7 @@ bool build_plan(int n, const std::vector<Gate> &gates, const Options &opt, bool 
       std::vector<int> nonr;
       for (int b = pack ? 1 : 0; b < m; ++b)
         if (std::find(rb.begin(), rb.end(), b) == rb.end()) nonr.push_back(b);
-      if (pack) order_group_bits_packed(nonr, ds.nonr);
+      if (pack) order_group_bits_packed(nonr, ds.nonr, opt.layout, last_stage);
       else order_group_bits(m, nonr, ds.nonr);
       const int group_bits = (int)nonr.size();
       for (int half = 0; half < kRegEntry / 16; ++half) {
@@ -323,7 +348,7 @@ bool build_plan(int n, const std::vector<Gate> &gates, const Options &opt, bool 
           for (int i = 0; i < 4; ++i) {
             const int gi = 4 * half + i;
             if (!((v >> i) & 1) || gi >= group_bits) continue;
-            ge.L ^= pack ? pack_offset(ds.nonr[gi]) : (1u << ds.nonr[gi]);
+            ge.L ^= pack ? pack_offset(ds.nonr[gi], opt.layout) : (1u << ds.nonr[gi]);
             ge.G |= 1ull << dp.tq[ds.nonr[gi]];
           }
           P.gtab.push_back(ge);
@@ -334,7 +359,7 @@ bool build_plan(int n, const std::vector<Gate> &gates, const Options &opt, bool 
         std::memset(&ge, 0, sizeof(ge));
         const int j = e - kRegEntry;
         if (pack && j < rpad) {
-          ge.L = pack_offset(rb[j]);
+          ge.L = pack_offset(rb[j], opt.layout);
           ge.G = 1ull << dp.tq[rb[j]];
         }
         P.gtab.push_back(ge);
@@ -479,6 +504,58 @@ bool build_plan(int n, const std::vector<Gate> &gates, const Options &opt, bool 
       const int pass_index = (int)P.passes.size();
       for (int gi : inner) { P.order.push_back(gi); P.pass_of.push_back(pass_index); }
       for (int gi : post) { P.order.push_back(gi); P.pass_of.push_back(pass_index); }
+    }
+    // Layout 1 (the pipelined kernels store the last stage's registers straight to HBM):
+    // a last stage that holds any of tile bits 1..3 in registers would scatter 16-byte
+    // pieces over many 128-byte lines per store instruction, so the pass ends with a
+    // data-only stage instead (no ops; register slots on the four highest tile bits, lane
+    // bits 1..3), one more trip through shared memory, after which every quarter warp
+    // stores whole 128-byte lines.
+    if (opt.layout == 1 && P.stages.size() > dp.stage_begin) {
+      const DevStage &ls = P.stages.back();
+      bool low = false;
+      for (int j = 0; j < rk; ++j) low = low || (ls.rbit[j] >= 1 && ls.rbit[j] <= 3);
+      if (low) {
+        DevStage ds;
+        std::memset(&ds, 0, sizeof(ds));
+        ds.r = 0;
+        std::vector<int> rb, nonr;
+        for (int b = m - 1; (int)rb.size() < rk; --b) rb.push_back(b);
+        for (int j = 0; j < rk; ++j) ds.rbit[j] = (uint8_t)rb[j];
+        for (int b = 1; b < m; ++b)
+          if (std::find(rb.begin(), rb.end(), b) == rb.end()) nonr.push_back(b);
+        order_group_bits_packed(nonr, ds.nonr, opt.layout, true);
+        const int group_bits = (int)nonr.size();
+        for (int half = 0; half < kRegEntry / 16; ++half) {
+          for (int v = 0; v < 16; ++v) {
+            DevGroupEntry ge;
+            std::memset(&ge, 0, sizeof(ge));
+            for (int i = 0; i < 4; ++i) {
+              const int gi = 4 * half + i;
+              if (!((v >> i) & 1) || gi >= group_bits) continue;
+              ge.L ^= pack_offset(ds.nonr[gi], opt.layout);
+              ge.G |= 1ull << dp.tq[ds.nonr[gi]];
+            }
+            P.gtab.push_back(ge);
+          }
+        }
+        for (int e = kRegEntry; e < kGroupEntries; ++e) {
+          DevGroupEntry ge;
+          std::memset(&ge, 0, sizeof(ge));
+          const int j = e - kRegEntry;
+          if (j < rk) {
+            ge.L = pack_offset(rb[j], opt.layout);
+            ge.G = 1ull << dp.tq[rb[j]];
+          }
+          P.gtab.push_back(ge);
+        }
+        ds.op_begin = (uint32_t)P.ops.size();
+        ds.op_count = 0;
+        ds.diag_only = 1;
+        P.stages.push_back(ds);
+        P.stage_gates.emplace_back();
+        P.stage_post.emplace_back();
+      }
     }
     dp.stage_count = (uint16_t)(P.stages.size() - dp.stage_begin);
     {

@@ -43,7 +43,17 @@ struct Options {
   int rk = 5;        // register qubits per thread of the kernel that runs the plan
   bool fused = false;
   bool pack = false; // packed plain kernel: tile bit 0 joins every stage as the pack bit
+  // shared-memory layout of a packed tile (pair k = tile bits 1..m-1 at a 16-byte slot):
+  //   0  slot k ^ ((k>>3 ^ k>>6 ^ k>>9) & 7): every pair bit toggles a bank-group bit
+  //   1  slot k ^ ((k>>3) & 7): the 128-byte swizzle of the tensor-memory-access (TMA)
+  //      copies, the tile as 1 KB boxes of eight 128-byte rows (rows: tile bits 4..6)
+  int layout = 0;
 };
+
+// 16-byte slot of pair k of a packed tile in a layout (see Options::layout).
+inline uint32_t pack_phys(uint32_t k, int layout) {
+  return layout == 1 ? k ^ ((k >> 3) & 7u) : k ^ (((k >> 3) ^ (k >> 6) ^ (k >> 9)) & 7u);
+}
 
 struct Plan {
   int n = 0;
@@ -58,6 +68,7 @@ struct Plan {
   std::vector<std::vector<int>> stage_post;   // per stage: diagonal gates applied after
   bool init_uniform = false;
   double hbm_bytes = 0;
+  int layout = 0;  // shared-memory layout of the packed tiles (Options::layout)
 };
 
 // Build the plan.  fresh_state: the state is |0..0> and was never written, so a

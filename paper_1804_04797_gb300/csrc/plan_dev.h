@@ -117,6 +117,7 @@ enum PassFlags : uint8_t {
   PF_INIT_ZERO = 2,     // tile content is |0..0>; nothing is read
   PF_UNITARY = 4,       // no projector in the pass: every tile keeps its norm
   PF_PACKED = 8,        // packed plan: stages of tile bit 0 + up to rk bits, PCode ops
+  PF_RAW = 16,          // tensor-core pass: the tiles' norms are not restored
 };
 
 struct DevPass {

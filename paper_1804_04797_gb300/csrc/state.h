@@ -38,6 +38,9 @@ struct sv_state {
   int jit_launches = 0;
   int plain_fallbacks = 0;     // applies of a tensor-core request run on the plain kernel
   bool plan_fallback = false;  // the current plan is such a fallback
+  // error word of the last plan run on kernels with bounded waits (the pipelined plan
+  // kernels), read by the next call that synchronises the stream; null when none is due
+  int *err_pending = nullptr;
   // the last plan run on this handle (a circuit applied again reuses it and its device
   // copy: no planning, kernel-source hashing or upload)
   bool plan_valid = false;
@@ -89,6 +92,10 @@ sv_status apply_gates(sv_state *s, const std::vector<svp::Gate> &g);
 sv_status set_device(sv_state *s);
 // Write |0..0> if the state is still the never-written initial one.
 sv_status materialize(sv_state *s);
+// The error word of a plan run whose kernels wait with a limit, if one is due: reads it
+// (synchronising the stream) and returns SV_ERR_TIMEOUT (handle marked unusable) if a
+// wait gave up, else SV_OK.
+sv_status take_pending_error(sv_state *s);
 // Fused path: the stage unitaries as split-TF32 operands (see k_fused.cu).
 sv_status build_stage_mats(svp::Plan *P, const std::vector<svp::Gate> &g, int r, bool f16);
 

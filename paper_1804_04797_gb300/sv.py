@@ -30,7 +30,8 @@ class SvError(RuntimeError):
 
 class sv_options(ctypes.Structure):
     _fields_ = [('fuse_k', c_int), ('precision', c_int), ('autotune', c_int), ('stream', c_void_p),
-                ('tile_bits', c_int), ('low_bits', c_int), ('jit', c_int)]
+                ('tile_bits', c_int), ('low_bits', c_int), ('jit', c_int), ('pipeline', c_int),
+                ('norm_restore', c_int)]
 
 
 class sv_lattice(ctypes.Structure):
@@ -44,7 +45,7 @@ class sv_cut(ctypes.Structure):
 
 class sv_plan_summary(ctypes.Structure):
     _fields_ = [('passes', c_int), ('stages', c_int), ('ops', c_int), ('init_uniform', c_int),
-                ('hbm_bytes', c_double)]
+                ('hbm_bytes', c_double), ('matrix_stages', c_int)]
 
 
 class sv_profile(ctypes.Structure):
@@ -101,6 +102,7 @@ def lib():
         'sv_amplitudes_by_inner_product': ([P(sv_lattice), c_int, vp, c_size_t, P(sv_options), vp], c_int),
         'sv_set_profiling': ([vp, c_int], c_int),
         'sv_get_profile': ([vp, P(sv_profile)], c_int),
+        'sv_get_launch_times': ([vp, vp, vp, c_size_t, P(c_size_t)], c_int),
     }
     for name, (args, res) in sig.items():
         f = getattr(L, name)
@@ -115,8 +117,9 @@ def _check(status):
         raise SvError(status, lib().sv_last_error().decode())
 
 
-def options(precision=SV_PREC_PLAIN, fuse_k=0, tile_bits=0, low_bits=0, stream=None, autotune=0, jit=0):
-    return sv_options(fuse_k, precision, autotune, stream, tile_bits, low_bits, jit)
+def options(precision=SV_PREC_PLAIN, fuse_k=0, tile_bits=0, low_bits=0, stream=None, autotune=0, jit=0,
+            pipeline=0, norm_restore=0):
+    return sv_options(fuse_k, precision, autotune, stream, tile_bits, low_bits, jit, pipeline, norm_restore)
 
 
 def lattice(lat):
@@ -348,3 +351,13 @@ def sv_get_profile(h):
     p = sv_profile()
     _check(lib().sv_get_profile(h, ctypes.byref(p)))
     return p
+
+
+def sv_get_launch_times(h):
+    """(ms, bytes) numpy arrays, one entry per timed launch since profiling was turned on."""
+    n = c_size_t()
+    _check(lib().sv_get_launch_times(h, None, None, 0, ctypes.byref(n)))
+    ms = np.zeros(n.value, dtype=np.float64)
+    by = np.zeros(n.value, dtype=np.float64)
+    _check(lib().sv_get_launch_times(h, ms.ctypes.data, by.ctypes.data, n.value, ctypes.byref(n)))
+    return ms, by

@@ -31,22 +31,34 @@ def rel_l2(a, b):
     return float(np.linalg.norm(a - b) / np.linalg.norm(b))
 
 
-def test_30q_depth20_full_state_matches_oracle():
+# Raw tensor-core results (norm restore off): rel-L2 against the oracle is the pass
+# criterion; the norm is only bounded loosely (the truncating fp32 accumulation drifts it
+# by about 1e-7 per stage) and recorded.
+RAW_NORM_BOUND = 1e-4
+
+
+def test_30q_depth20_full_state_matches_oracle(record_property):
     lat = inputs.C30
     n, gates = oc.generate(lat.rows, lat.cols, lat.removed_mask, lat.depth, lat.seed)
     want = csim.run(n, gates)
     g = sv.sv_generate_circuit(lat)
-    for prec in (sv.SV_PREC_PLAIN, sv.SV_PREC_TF32X3):
-        h = sv.sv_create(n, sv.options(precision=prec))
+    modes = [('plain', dict()), ('plain_previous_kernel', dict(pipeline=-1)),
+             ('tf32x3', dict(precision=sv.SV_PREC_TF32X3)), ('f16x3', dict(precision=sv.SV_PREC_F16X3)),
+             ('tf32x3_raw', dict(precision=sv.SV_PREC_TF32X3, norm_restore=-1)),
+             ('f16x3_raw', dict(precision=sv.SV_PREC_F16X3, norm_restore=-1))]
+    for name, kw in modes:
+        h = sv.sv_create(n, sv.options(**kw))
         try:
             sv.sv_apply_circuit(h, g)
             norm2, sp2 = sv.sv_norm(h)
             psi = sv.sv_copy_state(h, n)
         finally:
             sv.sv_destroy(h)
-        diff = np.linalg.norm(psi.astype(np.complex128) - want)
-        assert diff <= REL_L2, (prec, diff)          # the oracle state has norm 1
-        assert abs(norm2 - 1) <= NORM_TOL
+        diff = np.linalg.norm(psi.astype(np.complex128) - want)   # the oracle state has norm 1
+        fid = abs(np.vdot(want, psi.astype(np.complex128))) ** 2 / float(norm2)
+        record_property(name, {'rel_l2': float(diff), 'norm_err': float(norm2 - 1), '1-fidelity': 1 - fid})
+        assert diff <= REL_L2, (name, diff)
+        assert abs(norm2 - 1) <= (RAW_NORM_BOUND if name.endswith('_raw') else NORM_TOL), (name, norm2)
         assert 1.9 < (1 << n) * sp2 < 2.1
         del psi
 
