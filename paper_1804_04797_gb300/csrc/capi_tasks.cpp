@@ -140,6 +140,68 @@ sv_status plan_cut(const sv_lattice *lat, const sv_cut *cut, CutPlan *C, bool al
   return SV_OK;
 }
 
+// One half of the decomposition as a branch tree (branch-prefix sharing, §2.1: every
+// branch of a half runs the same gates until its first crossing CZ).  The half's gate list
+// runs on `full` (n_base + t qubits, branch bits n_base..): gates are taken in list
+// order on the smallest prefix of the state that holds every branch bit touched so far
+// -- the branch bits above it are still |+> (the leading H), so the state is the prefix
+// times their uniform slices -- and when a gate first touches a higher branch bit the
+// prefix is forked (replicated into the new slices, times 2^{-1/2} per new bit).  The
+// result is the state the whole list would give on all n_base + t qubits; the work before
+// each fork is done once instead of once per branch.
+sv_status run_branch_tree(sv_state *full, int n_base, const std::vector<svp::Gate> &g) {
+  const int n_all = full->n;
+  int active = 0;  // branch bits in the prefix
+  std::vector<svp::Gate> seg;
+  bool first = true;
+  auto flush = [&]() -> sv_status {
+    if (seg.empty() && !first) return SV_OK;
+    sv_state view;  // the prefix: n_base + active qubits of the same buffer
+    view.n = n_base + active;
+    view.psi = full->psi;
+    view.owns = false;
+    view.opts = full->opts;
+    view.stream = full->stream;
+    view.device = full->device;
+    view.fresh = first;
+    view.user_writes = true;
+    const sv_status st = apply_gates(&view, seg);
+    const sv_status werr = st == SV_OK ? take_pending_error(&view) : st;
+    if (view.d_plan) cudaFree(view.d_plan);
+    if (view.d_scratch) cudaFree(view.d_scratch);
+    if (view.d_sums) cudaFree(view.d_sums);
+    for (cudaEvent_t ev : view.events) cudaEventDestroy(ev);
+    seg.clear();
+    first = false;
+    return werr;
+  };
+  for (size_t i = 0; i < g.size(); ++i) {
+    const svp::Gate &x = g[i];
+    // the leading H of a branch bit is what puts it in |+>: a fork does it
+    if (i < (size_t)n_all && x.kind == svp::K_H && x.q0 >= n_base) continue;
+    int top = -1;
+    if (x.q0 >= n_base) top = x.q0 - n_base;
+    if (svp::kind_two_qubit(x.kind) && x.q1 >= n_base) top = std::max(top, x.q1 - n_base);
+    if (top >= active) {
+      sv_status st = flush();
+      if (st != SV_OK) return st;
+      const cudaError_t e = svk::launch_fork(full->psi, n_base + active, n_base + top + 1, full->stream);
+      if (e != cudaSuccess) { full->broken = true; return cuda_fail(e, "branch fork"); }
+      active = top + 1;
+    }
+    seg.push_back(x);
+  }
+  sv_status st = flush();
+  if (st != SV_OK) return st;
+  if (active < n_all - n_base) {  // branch bits no gate touches: still |+>
+    const cudaError_t e = svk::launch_fork(full->psi, n_base + active, n_all, full->stream);
+    if (e != cudaSuccess) { full->broken = true; return cuda_fail(e, "branch fork"); }
+  }
+  full->fresh = false;
+  full->sums_valid = false;
+  return SV_OK;
+}
+
 }  // namespace
 
 extern "C" sv_status sv_branch_counts(const sv_lattice *lat, const sv_cut *cut, int counts[5]) {
@@ -173,8 +235,8 @@ extern "C" sv_status sv_branch_amplitudes(const sv_lattice *lat, const sv_cut *c
   Holder A, B;
   if ((st = sv_create(na + C.ta, &o, &A.s)) != SV_OK) return st;
   if ((st = sv_create(nb + C.tb, &o, &B.s)) != SV_OK) return st;
-  if ((st = apply_gates(A.s, C.ga)) != SV_OK) return st;
-  if ((st = apply_gates(B.s, C.gb)) != SV_OK) return st;
+  if ((st = run_branch_tree(A.s, na, C.ga)) != SV_OK) return st;
+  if ((st = run_branch_tree(B.s, nb, C.gb)) != SV_OK) return st;
   if (m == 0) return SV_OK;
   // bitstring -> half indices, with the implicit branch bits fixed by the output bits
   std::vector<uint64_t> xab(2 * m);
@@ -316,8 +378,8 @@ extern "C" sv_status sv_branch_full_state(const sv_lattice *lat, const sv_cut *c
   Holder A, B;
   if ((st = sv_create(C.na + C.ta, &o, &A.s)) != SV_OK) return st;
   if ((st = sv_create(C.nb + C.tb, &o, &B.s)) != SV_OK) return st;
-  if ((st = apply_gates(A.s, C.ga)) != SV_OK) return st;
-  if ((st = apply_gates(B.s, C.gb)) != SV_OK) return st;
+  if ((st = run_branch_tree(A.s, C.na, C.ga)) != SV_OK) return st;
+  if ((st = run_branch_tree(B.s, C.nb, C.gb)) != SV_OK) return st;
   if ((st = set_device(out)) != SV_OK) return st;
   cudaError_t e = cudaStreamSynchronize(A.s->stream);
   if (e == cudaSuccess) e = cudaStreamSynchronize(B.s->stream);

@@ -37,6 +37,9 @@ constexpr int kPipeSlots12 = 6;
 bool pipe_shape(int m, int *groups, int *slots);
 // Whether pass `pass` of P runs on the pipelined kernel (layout-1 plan, at least one stage).
 bool pass_is_pipelined(const svp::Plan &P, int pass);
+// Threads of the pipelined kernel's CTA for a pass: the compute groups, the producer warp
+// and, where the last stage's output goes out by TMA stores, the storer warp.
+int pipe_threads(const svp::Plan &P, int kpr, int pass, bool inner);
 // CUDA source of the pipelined kernel ("sv_pass") of one pass of a layout-1 packed plan.
 std::string pipe_pass_source(const svp::Plan &P, int kpr, int pass, bool inner = false);
 

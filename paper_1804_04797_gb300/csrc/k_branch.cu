@@ -6,6 +6,8 @@
 // sum_l A[xa_j, l] * B[xb_j, l] in fp64 with a fixed reduction tree (deterministic).
 #include <cuda_runtime.h>
 
+#include <cmath>
+
 #include "kernels.h"
 
 namespace svk {
@@ -99,7 +101,39 @@ __global__ void __launch_bounds__(256) outer_sum_kernel(const float2 *__restrict
   }
 }
 
+// A fork of the branch tree: the first 2^n_cur amplitudes (every branch bit above them
+// still in |+>) replicated into all 2^(n_new - n_cur) slices of new branch bits, each
+// times 2^{-(n_new - n_cur)/2} (the H that put those bits in |+>): psi[i + (c << n_cur)]
+// = f psi[i].  Two amplitudes per 16-byte vector; f applied as hi + lo (one rounding).
+__global__ void fork_kernel(float4 *__restrict__ psi, uint64_t pairs, int copies_log2, int n_cur, float f_hi,
+                            float f_lo) {
+  const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+  for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < pairs; i += stride) {
+    float4 v = psi[i];
+    v.x = fmaf(v.x, f_hi, v.x * f_lo);
+    v.y = fmaf(v.y, f_hi, v.y * f_lo);
+    v.z = fmaf(v.z, f_hi, v.z * f_lo);
+    v.w = fmaf(v.w, f_hi, v.w * f_lo);
+    for (uint64_t c = 0; c < (1ull << copies_log2); ++c) psi[i + (c << (n_cur - 1))] = v;
+  }
+}
+
 }  // namespace
+
+cudaError_t launch_fork(float2 *psi, int n_cur, int n_new, cudaStream_t st) {
+  if (n_new <= n_cur) return cudaSuccess;
+  if (n_cur < 1) return cudaErrorInvalidValue;
+  const int k = n_new - n_cur;
+  // f = 2^{-k/2}: exact for even k; for odd k, 1/sqrt2 as the float nearest plus the rest
+  const double f = std::ldexp(1.0, -(k / 2)) * ((k & 1) ? 0.70710678118654752440 : 1.0);
+  const float hi = (float)f, lo = (float)(f - (double)hi);
+  const uint64_t pairs = 1ull << (n_cur - 1);
+  uint64_t grid = (pairs + 255) / 256;
+  const uint64_t cap = (uint64_t)device_sm_count() * 16;
+  if (grid > cap) grid = cap;
+  fork_kernel<<<(unsigned)grid, 256, 0, st>>>(reinterpret_cast<float4 *>(psi), pairs, k, n_cur, hi, lo);
+  return cudaGetLastError();
+}
 
 cudaError_t launch_outer_sum(const float2 *A, int nA, const float2 *B, int nB, int t, float scale, float2 *out,
                              cudaStream_t st) {

@@ -59,6 +59,10 @@ cudaError_t launch_branch_sum(const float2 *A, int nA, const float2 *B, int nB, 
 
 int device_sm_count();
 
+// Fork of a branch tree: psi[i + (c << n_cur)] = 2^{-(n_new - n_cur)/2} psi[i] for every
+// slice c of the branch bits n_cur..n_new-1 (they were |+> until now), in place.
+cudaError_t launch_fork(float2 *psi, int n_cur, int n_new, cudaStream_t st);
+
 // Full state from two batched half-states (Eqs. 6-7): out[x_A + (x_B << nA)] = scale *
 // sum_l A[x_A + (l << nA)] B[x_B + (l << nB)] over 2^t branches (fp32).
 cudaError_t launch_outer_sum(const float2 *A, int nA, const float2 *B, int nB, int t, float scale, float2 *out,

@@ -214,10 +214,30 @@ bool build_plan(int n, const std::vector<Gate> &gates, const Options &opt, bool 
     int local_of[64];
     for (int q = 0; q < 64; ++q) local_of[q] = -1;
     {
+      // Layout 1: tile bits 4..6 are the rows of the 8-row TMA boxes, the only high tile
+      // bits that toggle shared-memory bank groups.  They go to the three high tile qubits
+      // with the fewest non-diagonal gates in the pass (seldom register qubits of a stage,
+      // so they are free to serve as conflict-free lane bits); the rest follow ascending.
+      std::vector<int> high;
+      for (int q = c; q < n; ++q)
+        if (S & (1ull << q)) high.push_back(q);
+      if (opt.layout == 1 && high.size() >= 3) {
+        std::vector<int> nd(n, 0);
+        for (int gi : now)
+          if (!kind_is_diag(gates[gi].kind)) ++nd[gates[gi].q0];
+        std::vector<int> rows = high;
+        std::stable_sort(rows.begin(), rows.end(), [&](int a, int b) { return nd[a] < nd[b]; });
+        rows.resize(3);
+        std::sort(rows.begin(), rows.end());
+        std::vector<int> rest;
+        for (int q : high)
+          if (std::find(rows.begin(), rows.end(), q) == rows.end()) rest.push_back(q);
+        high = rows;
+        high.insert(high.end(), rest.begin(), rest.end());
+      }
       int li = 0;
       for (int q = 0; q < c; ++q) { dp.tq[li] = (uint8_t)q; local_of[q] = li++; }
-      for (int q = c; q < n; ++q)
-        if (S & (1ull << q)) { dp.tq[li] = (uint8_t)q; local_of[q] = li++; }
+      for (int q : high) { dp.tq[li] = (uint8_t)q; local_of[q] = li++; }
       int ni = 0;
       for (int q = 0; q < n; ++q)
         if (!(S & (1ull << q))) dp.ntq[ni++] = (uint8_t)q;
@@ -304,10 +324,15 @@ bool build_plan(int n, const std::vector<Gate> &gates, const Options &opt, bool 
         std::vector<char> tmp = done;
         cur = run_stage(Rm, tmp, nullptr, nullptr);
       }
+      // candidates in ascending global qubit (ties go to the lower qubit whatever the
+      // tile's bit order, so a layout's reordering of the tile bits changes no stage)
+      std::vector<int> by_qubit;
+      for (int bb = 0; bb < m; ++bb) by_qubit.push_back(bb);
+      std::sort(by_qubit.begin(), by_qubit.end(), [&](int a, int b) { return dp.tq[a] < dp.tq[b]; });
       for (int round = 0; round < r; ++round) {
         int best = -1;
         std::pair<int, int> bs = cur;
-        for (int bb = 0; bb < m; ++bb) {
+        for (int bb : by_qubit) {
           if ((Rm >> bb) & 1u) continue;
           std::vector<char> tmp = done;
           const std::pair<int, int> sc = run_stage(Rm | (1u << bb), tmp, nullptr, nullptr);
@@ -504,58 +529,6 @@ bool build_plan(int n, const std::vector<Gate> &gates, const Options &opt, bool 
       const int pass_index = (int)P.passes.size();
       for (int gi : inner) { P.order.push_back(gi); P.pass_of.push_back(pass_index); }
       for (int gi : post) { P.order.push_back(gi); P.pass_of.push_back(pass_index); }
-    }
-    // Layout 1 (the pipelined kernels store the last stage's registers straight to HBM):
-    // a last stage that holds any of tile bits 1..3 in registers would scatter 16-byte
-    // pieces over many 128-byte lines per store instruction, so the pass ends with a
-    // data-only stage instead (no ops; register slots on the four highest tile bits, lane
-    // bits 1..3), one more trip through shared memory, after which every quarter warp
-    // stores whole 128-byte lines.
-    if (opt.layout == 1 && P.stages.size() > dp.stage_begin) {
-      const DevStage &ls = P.stages.back();
-      bool low = false;
-      for (int j = 0; j < rk; ++j) low = low || (ls.rbit[j] >= 1 && ls.rbit[j] <= 3);
-      if (low) {
-        DevStage ds;
-        std::memset(&ds, 0, sizeof(ds));
-        ds.r = 0;
-        std::vector<int> rb, nonr;
-        for (int b = m - 1; (int)rb.size() < rk; --b) rb.push_back(b);
-        for (int j = 0; j < rk; ++j) ds.rbit[j] = (uint8_t)rb[j];
-        for (int b = 1; b < m; ++b)
-          if (std::find(rb.begin(), rb.end(), b) == rb.end()) nonr.push_back(b);
-        order_group_bits_packed(nonr, ds.nonr, opt.layout, true);
-        const int group_bits = (int)nonr.size();
-        for (int half = 0; half < kRegEntry / 16; ++half) {
-          for (int v = 0; v < 16; ++v) {
-            DevGroupEntry ge;
-            std::memset(&ge, 0, sizeof(ge));
-            for (int i = 0; i < 4; ++i) {
-              const int gi = 4 * half + i;
-              if (!((v >> i) & 1) || gi >= group_bits) continue;
-              ge.L ^= pack_offset(ds.nonr[gi], opt.layout);
-              ge.G |= 1ull << dp.tq[ds.nonr[gi]];
-            }
-            P.gtab.push_back(ge);
-          }
-        }
-        for (int e = kRegEntry; e < kGroupEntries; ++e) {
-          DevGroupEntry ge;
-          std::memset(&ge, 0, sizeof(ge));
-          const int j = e - kRegEntry;
-          if (j < rk) {
-            ge.L = pack_offset(rb[j], opt.layout);
-            ge.G = 1ull << dp.tq[rb[j]];
-          }
-          P.gtab.push_back(ge);
-        }
-        ds.op_begin = (uint32_t)P.ops.size();
-        ds.op_count = 0;
-        ds.diag_only = 1;
-        P.stages.push_back(ds);
-        P.stage_gates.emplace_back();
-        P.stage_post.emplace_back();
-      }
     }
     dp.stage_count = (uint16_t)(P.stages.size() - dp.stage_begin);
     {

@@ -539,6 +539,9 @@ __device__ __forceinline__ void load_group_rx(const float4 *tile, uint32_t a0, c
     I[p] = kCopied ? f2(x.y, x.w) : f2(x.z, x.w);
   }
 }
+// kGlobal: store each pair as (re, im, re', im'), the order of the state in memory (a
+// tile that a TMA copy then writes out as it is).
+template <bool kGlobal = false>
 __device__ __forceinline__ void store_group_rx(float4 *tile, uint32_t a0, const uint32_t (&rx)[kPR], const Regs &R,
                                                const Regs &I) {
   char *tb = reinterpret_cast<char *>(tile);
@@ -548,7 +551,8 @@ __device__ __forceinline__ void store_group_rx(float4 *tile, uint32_t a0, const 
 #pragma unroll
     for (int j = 0; j < kPR; ++j)
       if ((p >> j) & 1) a ^= rx[j];
-    *reinterpret_cast<float4 *>(tb + a) = make_float4(R[p].x, R[p].y, I[p].x, I[p].y);
+    *reinterpret_cast<float4 *>(tb + a) =
+        kGlobal ? make_float4(R[p].x, I[p].x, R[p].y, I[p].y) : make_float4(R[p].x, R[p].y, I[p].x, I[p].y);
   }
 }
 

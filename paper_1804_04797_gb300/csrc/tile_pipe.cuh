@@ -5,10 +5,14 @@
 // 128-byte rows per copy, the copy engine's 128-byte swizzle) and signals each slot's
 // "full" mbarrier through the copies' transaction count; G compute groups (2^(m-1-kpr)
 // threads each) take the CTA's tiles in turn, run the pass's stages on the slot through
-// registers (tile_pack.cuh), and release the slot on its "empty" mbarrier as soon as the
-// last stage has read its registers.  The last stage stores straight from registers to
-// HBM.  So a group never waits for a tile read (the producer runs ahead by S - G slots)
-// and the copy engine, not the compute warps, moves the input.
+// registers (tile_pack.cuh), and hand the slot back on its "empty" mbarrier.  When the
+// last stage's quarter warps hold whole 128-byte rows (its lane bits are tile bits 1..3),
+// it stores straight from registers to HBM and releases the slot as soon as it has read
+// it; otherwise it writes the tile back into the slot in memory order and the producer
+// writes the slot out with TMA tensor stores before it reloads it.  So a group never waits
+// for a tile read (each group owns S / G slots: one computes while the others load) and
+// the copy engine, not the compute warps, moves the input (and, in the second case, the
+// output).
 //
 // Every wait is bounded (kWaitNs): a wait that gives up makes the CTA stop, set the
 // plan's error word and return.
@@ -90,6 +94,22 @@ __device__ __forceinline__ void tma_load_5d(void *dst, const TmaDesc *map, int c
       "l"(reinterpret_cast<unsigned long long>(map)), "r"(c0), "r"(c1), "r"(c2), "r"(c3), "r"(c4), "r"(smem_u32(bar))
       : "memory");
 }
+
+// The reverse: the box at dst's coordinates written from shared memory at src (one bulk
+// group per commit; the source must not change until the group has been read).
+__device__ __forceinline__ void tma_store_5d(const TmaDesc *map, int c0, int c1, int c2, int c3, int c4,
+                                             const void *src) {
+  asm volatile(
+      "cp.async.bulk.tensor.5d.global.shared::cta.tile.bulk_group [%0, {%1, %2, %3, %4, %5}], [%6];" ::"l"(
+          reinterpret_cast<unsigned long long>(map)),
+      "r"(c0), "r"(c1), "r"(c2), "r"(c3), "r"(c4), "r"(smem_u32(src))
+      : "memory");
+}
+__device__ __forceinline__ void bulk_commit() { asm volatile("cp.async.bulk.commit_group;" ::: "memory"); }
+// Wait until every committed bulk group has finished reading its shared-memory source.
+__device__ __forceinline__ void bulk_wait_read_all() { asm volatile("cp.async.bulk.wait_group.read 0;" ::: "memory"); }
+// Wait until every committed bulk group has completed (its writes are done).
+__device__ __forceinline__ void bulk_wait_all() { asm volatile("cp.async.bulk.wait_group 0;" ::: "memory"); }
 
 // Global index offset of group g's element 0 in a stage (the G half of the stage's
 // group-addressing entries).
