@@ -455,6 +455,8 @@ def main():
     ap.add_argument('--depth', type=int, default=0, help='override the lattice depth (profiling of smaller cases)')
     ap.add_argument('--pipeline', type=int, default=0, help='plain path: 0 = pipelined persistent kernel, '
                                                             '-1 = one CTA per tile in flight')
+    ap.add_argument('--autotune', type=int, default=1, help='plain path: 1 = tile size and per-pass kernel shape '
+                                                            'picked by timing on the first call (cached), 0 = defaults')
     ap.add_argument('--no-cpu', action='store_true', help='skip the oracle legs (and the 30q accuracy block)')
     ap.add_argument('--no-extra', action='store_true', help='skip the secondary workloads')
     args = ap.parse_args()
@@ -544,6 +546,7 @@ def main():
             kw = dict(known[name])
             if name == 'plain':
                 kw['pipeline'] = args.pipeline
+                kw['autotune'] = args.autotune
             # the headline path takes the requested steps; the others fewer (secondary)
             steps, warmup = (args.steps, args.warmup) if name == 'plain' else (min(args.steps, 3), 1)
             if name.endswith('_raw'):
@@ -578,7 +581,7 @@ def main():
             sv.sv_apply_circuit(hh, sv.sv_generate_circuit(lat))
             sv.sv_get_amplitudes(hh, bits)
             sv.sv_norm(hh)
-        sv.sv_set_options(h, sv.options(stream=stream.cuda_stream, pipeline=args.pipeline))
+        sv.sv_set_options(h, sv.options(stream=stream.cuda_stream, pipeline=args.pipeline, autotune=args.autotune))
         e2e_steps = max(1, min(args.steps, 3))
         e_ms, e_wall, e_prof, _, _ = timed(h, e2e_steps, 1, step_e2e)
         e2e = {'value': e_wall / e2e_steps, 'unit': UNIT,

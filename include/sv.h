@@ -75,7 +75,12 @@ typedef struct {
                   /* compiled per plan use at most 4).  The tensor-core precisions    */
                   /* take 5 only: any other value is SV_ERR_ARG.                       */
   int precision;  /* SV_PREC_*                                            [PLAIN]       */
-  int autotune;   /* reserved: 1 = pick tile_bits by timing (sv_apply_batch)  [0]      */
+  int autotune;   /* 1 = pick shapes by timing, kept in a JSON cache (SV_AUTOTUNE_CACHE, */
+                  /* default autotune.json beside the library) [0].  sv_apply_circuit  */
+                  /* on a fresh state with plan-specialised kernels and tile_bits 0:   */
+                  /* the tile size (12 or 13 qubits) and each pass's compute groups of */
+                  /* the pipelined kernel, timed on the circuit itself (its first call */
+                  /* runs the plan a few times); sv_apply_batch: the tile size.        */
   void *stream;   /* cudaStream_t used by the handle                      [legacy 0]    */
   int tile_bits;  /* qubits per gathered tile, 6..14 (14: plan-specialised kernels    */
                   /* only) [12 on plan-specialised and tensor-core kernels, 13 on the  */

@@ -346,6 +346,115 @@ sv_status check_fused_error(sv_state *s, const svk::DevPlanView &view) {
   return SV_OK;
 }
 
+// ---- autotuning of the plain path on plan-specialised kernels ------------------------
+// (sv_options.autotune = 1, a fresh state, the pipelined kernels): the tile size (12 or 13
+// qubits) and, per pass, the pipelined kernel's compute groups (3 or 2 on 12-qubit tiles;
+// the slots stay six) are picked by timing this circuit -- whole runs of its plan, CUDA
+// events around every pass launch -- and the choice is kept in the JSON cache under
+// "<device>|circuit|<n>|<hash of the gate list and options>" (entries |m, |passes and |p<i>).
+
+namespace {
+
+struct PlainTune {
+  int m = 0;
+  std::vector<uint8_t> groups;
+};
+
+std::string circuit_tune_key(const sv_state *s, const std::vector<svp::Gate> &g, const svp::Options &po) {
+  cudaDeviceProp prop;
+  cudaGetDeviceProperties(&prop, s->device);
+  uint64_t h = 1469598103934665603ull;
+  auto mix = [&h](const void *p, size_t len) {
+    const unsigned char *b = static_cast<const unsigned char *>(p);
+    for (size_t i = 0; i < len; ++i) h = (h ^ b[i]) * 1099511628211ull;
+  };
+  const int head[4] = {s->n, po.rk, po.r, po.c};
+  mix(head, sizeof(head));
+  if (!g.empty()) mix(g.data(), g.size() * sizeof(svp::Gate));
+  char buf[sizeof(prop.name) + 64];
+  std::snprintf(buf, sizeof(buf), "%s|circuit|%d|%016llx", prop.name, s->n, (unsigned long long)h);
+  for (char *p = buf; *p; ++p)
+    if (*p == '"' || *p == '\\') *p = '_';
+  return buf;
+}
+
+// Two runs of the plan (the first warms the kernels); per-pass device times of the second.
+sv_status time_plan(sv_state *s, const svp::Plan &P, const svk::DevPlanView &view, const svj::Module *jit,
+                    std::vector<float> *ms) {
+  const size_t np = P.passes.size();
+  std::vector<cudaEvent_t> ev(2 * np);
+  for (cudaEvent_t &e : ev) cudaEventCreate(&e);
+  cudaError_t e = cudaSuccess;
+  for (int rep = 0; rep < 2 && e == cudaSuccess; ++rep)
+    for (size_t p = 0; p < np && e == cudaSuccess; ++p) {
+      if (rep) cudaEventRecord(ev[2 * p], s->stream);
+      e = svj::launch_pass(jit, s->psi, s->n, view, (int)p, P.passes[p], s->stream);
+      if (rep) cudaEventRecord(ev[2 * p + 1], s->stream);
+    }
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s->stream);
+  ms->assign(np, 0.f);
+  for (size_t p = 0; p < np && e == cudaSuccess; ++p) e = cudaEventElapsedTime(&(*ms)[p], ev[2 * p], ev[2 * p + 1]);
+  for (cudaEvent_t &x : ev) cudaEventDestroy(x);
+  if (e != cudaSuccess) return cuda_fail(e, "autotune run");
+  s->err_pending = view.err;
+  return take_pending_error(s);
+}
+
+sv_status autotune_plain(sv_state *s, const std::vector<svp::Gate> &g, const svp::Options &base, PlainTune *out) {
+  const std::string key = circuit_tune_key(s, g, base);
+  std::map<std::string, int> cache = read_autotune_cache();
+  auto m_it = cache.find(key + "|m"), np_it = cache.find(key + "|passes");
+  if (m_it != cache.end() && np_it != cache.end()) {
+    out->m = m_it->second;
+    out->groups.assign((size_t)np_it->second, 0);
+    for (size_t p = 0; p < out->groups.size(); ++p) {
+      auto it = cache.find(key + "|p" + std::to_string(p));
+      out->groups[p] = it == cache.end() ? 0 : (uint8_t)it->second;
+    }
+    return SV_OK;
+  }
+  double best_total = 1e300;
+  for (int m : {12, 13}) {
+    if (m > s->n) continue;
+    svp::Options po = base;
+    po.m = m;
+    svp::Plan P;
+    const char *err = nullptr;
+    if (!svp::build_plan(s->n, g, po, true, &P, &err)) return fail(SV_ERR_ARG, err ? err : "planning failed");
+    const size_t np = P.passes.size();
+    std::vector<float> best(np, 1e30f);
+    std::vector<uint8_t> best_g(np, 0);
+    for (int groups : (m == 12 ? std::vector<int>{3, 2} : std::vector<int>{1})) {
+      P.pipe_groups.assign(np, (uint8_t)groups);
+      std::string jerr;
+      const svj::Module *M = svj::get_module(P, po.rk, &jerr);
+      if (!M) return fail(SV_ERR_CUDA, jerr.c_str());
+      svk::DevPlanView view;
+      sv_status st = upload_plan(s, P, &view);
+      if (st != SV_OK) return st;
+      std::vector<float> ms;
+      if ((st = time_plan(s, P, view, M, &ms)) != SV_OK) return st;
+      for (size_t p = 0; p < np; ++p)
+        if (ms[p] < best[p]) { best[p] = ms[p]; best_g[p] = (uint8_t)groups; }
+    }
+    double total = 0;
+    for (float x : best) total += x;
+    if (total < best_total) {
+      best_total = total;
+      out->m = m;
+      out->groups = best_g;
+    }
+  }
+  if (out->m == 0) return fail(SV_ERR_ARG, "autotune: no candidate tile size");
+  cache[key + "|m"] = out->m;
+  cache[key + "|passes"] = (int)out->groups.size();
+  for (size_t p = 0; p < out->groups.size(); ++p) cache[key + "|p" + std::to_string(p)] = out->groups[p];
+  write_autotune_cache(cache);
+  return SV_OK;
+}
+
+}  // namespace
+
 sv_status apply_gates(sv_state *s, const std::vector<svp::Gate> &g) {
   sv_status st;
   if ((st = set_device(s)) != SV_OK) return st;
@@ -364,8 +473,8 @@ sv_status apply_gates(sv_state *s, const std::vector<svp::Gate> &g) {
     const unsigned char *b = static_cast<const unsigned char *>(p);
     for (size_t i = 0; i < len; ++i) key = (key ^ b[i]) * 1099511628211ull;
   };
-  const int head[9] = {s->n, s->fresh ? 1 : 0, s->opts.precision, s->opts.fuse_k, s->opts.tile_bits,
-                       s->opts.low_bits, s->opts.jit, s->opts.pipeline, s->opts.norm_restore};
+  const int head[10] = {s->n, s->fresh ? 1 : 0, s->opts.precision, s->opts.fuse_k, s->opts.tile_bits,
+                        s->opts.low_bits, s->opts.jit, s->opts.pipeline, s->opts.norm_restore, s->opts.autotune};
   mix(head, sizeof(head));
   if (!g.empty()) mix(g.data(), g.size() * sizeof(svp::Gate));
   if (s->plan_valid && s->plan_key == key) {
@@ -382,7 +491,13 @@ sv_status apply_gates(sv_state *s, const std::vector<svp::Gate> &g) {
   const char *err = nullptr;
   bool want_jit = false;
   svp::Options po = apply_plan_options(s->opts, s->n, &want_jit);
+  PlainTune tune;
+  if (s->opts.autotune == 1 && want_jit && po.layout == 1 && s->fresh && s->opts.tile_bits == 0) {
+    if ((st = autotune_plain(s, g, po, &tune)) != SV_OK) return st;
+    po.m = tune.m;
+  }
   if (!svp::build_plan(s->n, g, po, s->fresh, &P, &err)) return fail(SV_ERR_ARG, err ? err : "planning failed");
+  if (tune.m && tune.groups.size() == P.passes.size()) P.pipe_groups = tune.groups;
   // a tensor-core request on a state (or tile) below 12 qubits runs the plain kernel
   s->plan_fallback = (s->opts.precision == SV_PREC_TF32X3 || s->opts.precision == SV_PREC_F16X3) && !po.fused;
   const svj::Module *jit = nullptr;

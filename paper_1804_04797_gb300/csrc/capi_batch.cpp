@@ -27,6 +27,61 @@
 
 using namespace svc;
 
+namespace svc {
+
+std::string autotune_cache_path() {
+  if (const char *p = std::getenv("SV_AUTOTUNE_CACHE")) return p;
+  Dl_info info;
+  if (dladdr(reinterpret_cast<void *>(&sv_apply_batch), &info) && info.dli_fname) {
+    std::string f = info.dli_fname;
+    const size_t slash = f.rfind('/');
+    if (slash != std::string::npos) return f.substr(0, slash) + "/autotune.json";
+  }
+  return "autotune.json";
+}
+
+// The file is a flat JSON object {"key": tile_bits, ...}; keys are "<device>|<hash>".
+std::map<std::string, int> read_autotune_cache() {
+  std::map<std::string, int> out;
+  FILE *f = std::fopen(autotune_cache_path().c_str(), "r");
+  if (!f) return out;
+  std::string s;
+  char buf[4096];
+  size_t got;
+  while ((got = std::fread(buf, 1, sizeof(buf), f)) > 0) s.append(buf, got);
+  std::fclose(f);
+  size_t i = 0;
+  while ((i = s.find('"', i)) != std::string::npos) {
+    const size_t j = s.find('"', i + 1);
+    if (j == std::string::npos) break;
+    const std::string k = s.substr(i + 1, j - i - 1);
+    const size_t c = s.find(':', j);
+    if (c == std::string::npos) break;
+    out[k] = std::atoi(s.c_str() + c + 1);
+    i = s.find_first_of(",}", c);
+    if (i == std::string::npos) break;
+  }
+  return out;
+}
+
+void write_autotune_cache(const std::map<std::string, int> &c) {
+  const std::string path = autotune_cache_path();
+  const std::string tmp = path + ".tmp";
+  FILE *f = std::fopen(tmp.c_str(), "w");
+  if (!f) return;
+  std::fprintf(f, "{");
+  bool first = true;
+  for (const auto &kv : c) {
+    std::fprintf(f, "%s\n  \"%s\": %d", first ? "" : ",", kv.first.c_str(), kv.second);
+    first = false;
+  }
+  std::fprintf(f, "\n}\n");
+  std::fclose(f);
+  std::rename(tmp.c_str(), path.c_str());
+}
+
+}  // namespace svc
+
 namespace {
 
 int lattice_qubits(const sv_lattice &lat) {
@@ -367,57 +422,6 @@ cudaError_t enqueue_batch(Batch *B, cudaStream_t st, bool with_stats) {
 
 // ---- autotune: tile size of the batch, timed, cached in a JSON file --------------------
 
-std::string cache_path() {
-  if (const char *p = std::getenv("SV_AUTOTUNE_CACHE")) return p;
-  Dl_info info;
-  if (dladdr(reinterpret_cast<void *>(&sv_apply_batch), &info) && info.dli_fname) {
-    std::string f = info.dli_fname;
-    const size_t slash = f.rfind('/');
-    if (slash != std::string::npos) return f.substr(0, slash) + "/autotune.json";
-  }
-  return "autotune.json";
-}
-
-// The file is a flat JSON object {"key": tile_bits, ...}; keys are "<device>|<hash>".
-std::map<std::string, int> read_cache() {
-  std::map<std::string, int> out;
-  FILE *f = std::fopen(cache_path().c_str(), "r");
-  if (!f) return out;
-  std::string s;
-  char buf[4096];
-  size_t got;
-  while ((got = std::fread(buf, 1, sizeof(buf), f)) > 0) s.append(buf, got);
-  std::fclose(f);
-  size_t i = 0;
-  while ((i = s.find('"', i)) != std::string::npos) {
-    const size_t j = s.find('"', i + 1);
-    if (j == std::string::npos) break;
-    const std::string k = s.substr(i + 1, j - i - 1);
-    const size_t c = s.find(':', j);
-    if (c == std::string::npos) break;
-    out[k] = std::atoi(s.c_str() + c + 1);
-    i = s.find_first_of(",}", c);
-    if (i == std::string::npos) break;
-  }
-  return out;
-}
-
-void write_cache(const std::map<std::string, int> &c) {
-  const std::string path = cache_path();
-  const std::string tmp = path + ".tmp";
-  FILE *f = std::fopen(tmp.c_str(), "w");
-  if (!f) return;
-  std::fprintf(f, "{");
-  bool first = true;
-  for (const auto &kv : c) {
-    std::fprintf(f, "%s\n  \"%s\": %d", first ? "" : ",", kv.first.c_str(), kv.second);
-    first = false;
-  }
-  std::fprintf(f, "\n}\n");
-  std::fclose(f);
-  std::rename(tmp.c_str(), path.c_str());
-}
-
 std::string tune_key(const sv_lattice *circs, size_t count, int jit) {
   cudaDeviceProp prop;
   int dev = 0;
@@ -435,7 +439,7 @@ std::string tune_key(const sv_lattice *circs, size_t count, int jit) {
 
 sv_status autotune_tile_bits(const sv_lattice *circs, size_t count, int jit, int *m_out) {
   const std::string key = tune_key(circs, count, jit);
-  std::map<std::string, int> cache = read_cache();
+  std::map<std::string, int> cache = read_autotune_cache();
   auto it = cache.find(key);
   if (it != cache.end() && it->second >= 10 && it->second <= 13) { *m_out = it->second; return SV_OK; }
   const int cand[3] = {11, 12, 13};
@@ -462,7 +466,7 @@ sv_status autotune_tile_bits(const sv_lattice *circs, size_t count, int jit, int
   cudaEventDestroy(a);
   cudaEventDestroy(b);
   cache[key] = best_m;
-  write_cache(cache);
+  write_autotune_cache(cache);
   *m_out = best_m;
   return SV_OK;
 }

@@ -35,6 +35,8 @@ constexpr int kTileBits = 12;
 constexpr int kPipeGroups12 = 3;
 constexpr int kPipeSlots12 = 6;
 bool pipe_shape(int m, int *groups, int *slots);
+// The shape of pass `pass` of P: the tile size's default, or the plan's pipe_groups entry.
+bool pass_pipe_shape(const svp::Plan &P, int pass, int *groups, int *slots);
 // Whether pass `pass` of P runs on the pipelined kernel (layout-1 plan, at least one stage).
 bool pass_is_pipelined(const svp::Plan &P, int pass);
 // Threads of the pipelined kernel's CTA for a pass: the compute groups, the producer warp

@@ -560,6 +560,19 @@ bool build_plan(int n, const std::vector<Gate> &gates, const Options &opt, bool 
     if (P.stages.back().op_count == 65535) { *err = "stage too large"; return false; }
     P.stages.back().op_count += 1;
   }
+  // packed plans: the rounding constant of every T / T-adjoint op (arg 1: the fp32 value
+  // above 1/sqrt2, 0: the one below), in plan order, each chosen to bring the running sum
+  // of the relative errors back toward zero (see DT1 in tile_pack.cuh)
+  if (pack) {
+    const double s2 = 0.70710678118654752440;
+    const double e_dn = (double)0.70710677f / s2 - 1.0, e_up = (double)0.70710683f / s2 - 1.0;
+    double bias = 0.0;
+    for (DevOp &o : P.ops) {
+      if (o.code < P_DIAG || o.code >= P_DIAG + 12) continue;
+      o.arg = bias < 0.0 ? 1 : 0;
+      bias += o.arg ? e_up : e_dn;
+    }
+  }
   // a no-op past the last op: kernels may load the op after a stage's last one
   DevOp end;
   std::memset(&end, 0, sizeof(end));

@@ -3,6 +3,8 @@
 
 #include <cuda_runtime.h>
 
+#include <map>
+#include <string>
 #include <vector>
 
 #include "../../include/sv.h"
@@ -92,6 +94,12 @@ sv_status apply_gates(sv_state *s, const std::vector<svp::Gate> &g);
 sv_status set_device(sv_state *s);
 // Write |0..0> if the state is still the never-written initial one.
 sv_status materialize(sv_state *s);
+// The autotuner's JSON cache (SV_AUTOTUNE_CACHE, default autotune.json beside the
+// library): a flat object {"key": integer, ...}.
+std::string autotune_cache_path();
+std::map<std::string, int> read_autotune_cache();
+void write_autotune_cache(const std::map<std::string, int> &c);
+
 // The error word of a plan run whose kernels wait with a limit, if one is due: reads it
 // (synchronising the stream) and returns SV_ERR_TIMEOUT (handle marked unusable) if a
 // wait gave up, else SV_OK.

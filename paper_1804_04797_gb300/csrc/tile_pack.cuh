@@ -56,12 +56,14 @@ struct Ops<float2> {
   __device__ __forceinline__ static float2 add(float2 a, float2 b) { return add2(a, b); }
   __device__ __forceinline__ static float2 sub(float2 a, float2 b) { return sub2(a, b); }
   __device__ __forceinline__ static float2 rs(float2 a) { return rs2x2(a); }
+  __device__ __forceinline__ static float2 scale(float2 a, float c) { return mul2(a, f2(c, c)); }
 };
 template <>
 struct Ops<float> {
   __device__ __forceinline__ static float add(float a, float b) { return a + b; }
   __device__ __forceinline__ static float sub(float a, float b) { return a - b; }
   __device__ __forceinline__ static float rs(float a) { return rs2(a); }
+  __device__ __forceinline__ static float scale(float a, float c) { return a * c; }
 };
 
 // Each gate is written on s = x + y and d = x - y (its out()): f() forms them with adds,
@@ -170,20 +172,30 @@ struct GSYDG {  // x' = x + y, y' = y - x
 };
 
 // ---- diagonal phases on one element (r, i) ----------------------------------------------
-struct DT {  // times e^{i pi/4}
+// T and its adjoint multiply by e^{+-i pi/4} = (1 +- i)/sqrt2: two additions, then the
+// factor 1/sqrt2 as ONE multiplication by c, one of the two fp32 values that bracket it
+// (kS2up = 0.70710683, above by 6.7e-8 relative; kS2dn = 0.70710677, below by 1.7e-8).
+// The planner picks c gate by gate so that the running sum of these relative errors over
+// the plan's T gates stays next to zero: their effect on the norm cancels instead of
+// adding up (always rounding one way shrank the 34-qubit norm by 1.3e-6), at two packed
+// operations per pair fewer than the correctly rounded hi + lo product.
+constexpr float kS2dn = 0.70710677f, kS2up = 0.70710683f;
+struct DT1 {  // times e^{i pi/4}
   template <class T>
-  __device__ __forceinline__ static void f(T &r, T &i) {
+  __device__ __forceinline__ static void f(T &r, T &i, float c) {
     using O = Ops<T>;
     const T a = O::sub(r, i), b = O::add(r, i);
-    r = O::rs(a); i = O::rs(b);
+    r = O::scale(a, c);
+    i = O::scale(b, c);
   }
 };
-struct DTDG {  // times e^{-i pi/4}
+struct DTDG1 {  // times e^{-i pi/4}
   template <class T>
-  __device__ __forceinline__ static void f(T &r, T &i) {
+  __device__ __forceinline__ static void f(T &r, T &i, float c) {
     using O = Ops<T>;
     const T a = O::add(r, i), b = O::sub(i, r);
-    r = O::rs(a); i = O::rs(b);
+    r = O::scale(a, c);
+    i = O::scale(b, c);
   }
 };
 
@@ -254,20 +266,20 @@ __device__ __forceinline__ void pairs_pack_signed(Regs &R, Regs &I, float s) {
 #pragma unroll
   for (int p = 0; p < kP; ++p) G::fs(R[p].x, I[p].x, R[p].y, I[p].y, s);
 }
-// phase D where register slot J is 1
+// phase D (T or its adjoint, rounding constant c) where register slot J is 1
 template <class D, int J>
-__device__ __forceinline__ void diag(Regs &R, Regs &I) {
+__device__ __forceinline__ void diag(Regs &R, Regs &I, float c) {
   if constexpr (J < kPR) {
 #pragma unroll
     for (int p = 0; p < kP; ++p)
-      if (p & (1 << J)) D::f(R[p], I[p]);
+      if (p & (1 << J)) D::f(R[p], I[p], c);
   }
 }
 // phase D where the pack bit is 1
 template <class D>
-__device__ __forceinline__ void diag_pack(Regs &R, Regs &I) {
+__device__ __forceinline__ void diag_pack(Regs &R, Regs &I, float c) {
 #pragma unroll
-  for (int p = 0; p < kP; ++p) D::f(R[p].y, I[p].y);
+  for (int p = 0; p < kP; ++p) D::f(R[p].y, I[p].y, c);
 }
 // factor f (a sign or a 0/1 projector) where register slot J equals B
 template <int J, int B>
@@ -376,7 +388,7 @@ __device__ __forceinline__ void phase_all(Regs &R, Regs &I, int p) {
 // general 2x2 op for the gate set.
 #define SV_P6(M, A) M(A, 0) M(A, 1) M(A, 2) M(A, 3) M(A, 4)
 #define SV_PAIR_CASE(G, J) case svp::P_PAIR + 6 * G##_I + J: pairs<G, J>(R, I); break;
-#define SV_DIAG_CASE(D, J) case svp::P_DIAG + 6 * D##_I + J: diag<D, J>(R, I); break;
+#define SV_DIAG_CASE(D, J) case svp::P_DIAG + 6 * D##_I + J: diag<D, J>(R, I, tc); break;
 #define SV_Z_CASE(X, J) \
   case svp::P_DIAG + 12 + J: factor<J, 1>(R, I, fz); break; \
   case svp::P_DIAG + 18 + J: factor<J, 1>(R, I, f0); break; \
@@ -385,13 +397,14 @@ __device__ __forceinline__ void phase_all(Regs &R, Regs &I, int p) {
   case svp::P_CZ + 6 * J + K: two<J, K, false>(R, I); break; \
   case svp::P_PEQ + 6 * J + K: two<J, K, true>(R, I); break;
 
-constexpr int GH_I = 0, GSX_I = 1, GSY_I = 2, GSXDG_I = 3, GSYDG_I = 4, DT_I = 0, DTDG_I = 1;
+constexpr int GH_I = 0, GSX_I = 1, GSY_I = 2, GSXDG_I = 3, GSYDG_I = 4, DT1_I = 0, DTDG1_I = 1;
 
 // The op's code and argument (the first word of its 16-byte head).
 __device__ __forceinline__ void apply_op(Regs &R, Regs &I, uint32_t code, uint32_t arg, bool cond, int &ph,
                                          bool &zero) {
   using namespace svp;
   const float fz = cond ? -1.f : 1.f, f0 = cond ? 0.f : 1.f;
+  const float tc = arg ? kS2up : kS2dn;  // T ops: the plan's rounding choice
   switch (code) {
     SV_P6(SV_PAIR_CASE, GH)
     case P_PAIR + 0 + kPackSlot: pairs_pack<GH>(R, I); break;
@@ -403,10 +416,10 @@ __device__ __forceinline__ void apply_op(Regs &R, Regs &I, uint32_t code, uint32
     case P_PAIR + 18 + kPackSlot: pairs_pack<GSXDG>(R, I); break;
     SV_P6(SV_PAIR_CASE, GSYDG)
     case P_PAIR + 24 + kPackSlot: pairs_pack<GSYDG>(R, I); break;
-    SV_P6(SV_DIAG_CASE, DT)
-    case P_DIAG + 0 + kPackSlot: diag_pack<DT>(R, I); break;
-    SV_P6(SV_DIAG_CASE, DTDG)
-    case P_DIAG + 6 + kPackSlot: diag_pack<DTDG>(R, I); break;
+    SV_P6(SV_DIAG_CASE, DT1)
+    case P_DIAG + 0 + kPackSlot: diag_pack<DT1>(R, I, tc); break;
+    SV_P6(SV_DIAG_CASE, DTDG1)
+    case P_DIAG + 6 + kPackSlot: diag_pack<DTDG1>(R, I, tc); break;
     SV_P6(SV_Z_CASE, 0)
     case P_DIAG + 12 + kPackSlot: factor_pack<1>(R, I, fz); break;
     case P_DIAG + 18 + kPackSlot: factor_pack<1>(R, I, f0); break;

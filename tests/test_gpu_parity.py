@@ -580,3 +580,54 @@ def test_repeated_circuit_reuses_its_plan(kw):
         sv.sv_destroy(h)
     assert np.array_equal(a1.view(np.uint32), a2.view(np.uint32))
     assert rel_l2(a3, a1) <= 2e-5
+
+
+def test_autotuned_plain_path_caches_its_choice_and_matches_the_oracle(tmp_path, monkeypatch):
+    """sv_options.autotune = 1 on a fresh state: the tile size and each pass's compute
+    groups are picked by timing and kept in the JSON cache; the tuned run matches the
+    oracle, and a second handle takes the cached choice (same plan, bitwise the same
+    state)."""
+    import json
+    cache = tmp_path / 'autotune.json'
+    monkeypatch.setenv('SV_AUTOTUNE_CACHE', str(cache))
+    lat = inputs.lattice_for(4, 6, 16, seed=13)
+    n, gates = oracle_gates(lat)
+    want = csim.run(n, gates)
+    psi1, norm2, _ = run_gpu(lat, jit=1, autotune=1)
+    assert rel_l2(psi1, want) <= REL_L2
+    assert abs(norm2 - 1) <= NORM_TOL
+    entries = json.loads(cache.read_text())
+    keys = [k for k in entries if '|circuit|%d|' % n in k]
+    m = [entries[k] for k in keys if k.endswith('|m')]
+    passes = [entries[k] for k in keys if k.endswith('|passes')]
+    assert m and m[0] in (12, 13)
+    assert passes and all(k.rsplit('|', 1)[0] + '|p%d' % i in entries for k in keys if k.endswith('|passes')
+                          for i in range(passes[0]))
+    psi2, _, _ = run_gpu(lat, jit=1, autotune=1)
+    assert np.array_equal(psi1.view(np.uint32), psi2.view(np.uint32))
+
+
+def test_state_on_a_torch_owned_buffer_matches_the_oracle():
+    """sv_create_from_ptr on a torch-allocated complex64 tensor (PyTorch owns the device
+    memory; the library only runs kernels on it): |0...0> written by torch, the circuit
+    applied by the library, the tensor read back by torch and checked against the oracle;
+    a misaligned view is refused."""
+    import torch
+    lat = inputs.lattice_for(4, 5, 14, seed=5)
+    n, gates = oracle_gates(lat)
+    want = csim.run(n, gates)
+    buf = torch.zeros(1 << n, dtype=torch.complex64, device='cuda')
+    buf[0] = 1
+    stream = torch.cuda.current_stream()
+    h = sv.sv_create_from_ptr(n, buf.data_ptr(), stream.cuda_stream)
+    try:
+        sv.sv_apply_circuit(h, sv.sv_generate_circuit(lat))
+        norm2, _ = sv.sv_norm(h)
+    finally:
+        sv.sv_destroy(h)
+    torch.cuda.synchronize()
+    psi = buf.cpu().numpy()
+    assert rel_l2(psi, want) <= REL_L2
+    assert abs(norm2 - 1) <= NORM_TOL
+    with pytest.raises(sv.SvError, match='aligned'):
+        sv.sv_create_from_ptr(n - 1, buf[1:].data_ptr(), stream.cuda_stream)
