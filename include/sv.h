@@ -118,6 +118,10 @@ typedef struct {
 typedef struct {
   uint64_t half_a_mask;
   int full_decomposition;
+  int depth;  /* sv_branch_full_state: 0 = every layer in the two halves; d > 0 = layers     */
+              /* 0..d in the halves (parts A and B of §2.1, Fig. 2), the layers after d   */
+              /* (part C, Eq. 3) applied to the reconstructed full state.  Must be 0 for  */
+              /* sv_branch_amplitudes and sv_branch_counts.                               */
 } sv_cut;
 
 typedef struct sv_state sv_state;
@@ -235,7 +239,9 @@ sv_status sv_get_probabilities(sv_state *s, const uint64_t *bits, size_t m, doub
 sv_status sv_branch_amplitudes(const sv_lattice *lat, const sv_cut *cut, const uint64_t *bits,
                                size_t m, const sv_options *opts, double *out_re_im);
 
-/* The full state from the cut decomposition in tensor form (§2, Eqs. 6-7): the two
+/* The full state from the cut decomposition in tensor form (§2, Eqs. 6-7), continued by
+ * the circuit's part C when cut->depth > 0 (Eq. 3: the decomposed layers 0..depth give the
+ * state psi_AB, the remaining layers run on it as ordinary passes): the two
  * halves' batched branch states A (n_A + t qubits) and B (n_B + t) give
  * psi[x_A + (x_B << n_A)] = sum_l A_l[x_A] B_l[x_B], a complex matrix product over the
  * 2^t branches, written into out (an n-qubit handle on the same device; fp32

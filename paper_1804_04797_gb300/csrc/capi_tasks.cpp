@@ -49,6 +49,7 @@ struct CutPlan {
   int tf = 0;         // branch bits in both halves (summed over)
   int ta = 0, tb = 0; // branch bits of half A / half B (tf + implicit ones of the other side)
   std::vector<svp::Gate> ga, gb;
+  std::vector<svp::Gate> part_c;  // layers after the cut depth, on the full state (qubits as in the lattice)
   // output signs (-1)^{x_a x_b} of absorbed CZs; bits of x fixing implicit branch bits
   std::vector<std::pair<int, int>> signs;
   std::vector<std::pair<int, int>> fix_a;  // (branch bit index in A above na + tf, qubit of x)
@@ -69,6 +70,8 @@ sv_status plan_cut(const sv_lattice *lat, const sv_cut *cut, CutPlan *C, bool al
     C->local[q] = C->in_a[q] ? na++ : nb++;
   }
   if (na < 1 || nb < 1) return fail(SV_ERR_ARG, "sv_branch_amplitudes: both halves need qubits");
+  if (cut->depth < 0) return fail(SV_ERR_ARG, "sv_cut: depth must be >= 0");
+  const uint32_t depth = cut->depth > 0 ? (uint32_t)cut->depth : 0xffffffffu;
   // last non-diagonal gate of each qubit (H, square roots)
   std::vector<long> last_nd(n, -1);
   for (size_t i = 0; i < g.size(); ++i) {
@@ -80,7 +83,7 @@ sv_status plan_cut(const sv_lattice *lat, const sv_cut *cut, CutPlan *C, bool al
   std::vector<int> role;
   for (size_t i = 0; i < g.size(); ++i) {
     const sv_gate &x = g[i];
-    if (x.kind != SV_CZ || C->in_a[x.q0] == C->in_a[x.q1]) continue;
+    if (x.kind != SV_CZ || C->in_a[x.q0] == C->in_a[x.q1] || x.layer > depth) continue;
     const int qa = C->in_a[x.q0] ? x.q0 : x.q1, qb = C->in_a[x.q0] ? x.q1 : x.q0;
     const bool qa_quiet = last_nd[qa] < (long)i, qb_quiet = last_nd[qb] < (long)i;
     int r = 0;
@@ -107,6 +110,10 @@ sv_status plan_cut(const sv_lattice *lat, const sv_cut *cut, CutPlan *C, bool al
   for (int q = 0; q < nb + C->tb; ++q) C->gb.push_back(svp::Gate{svp::K_H, (uint8_t)q, 0});
   int jf = 0, ja = 0, jb = 0, c = 0;
   for (const sv_gate &x : g) {
+    if (x.layer > depth) {  // part C: the full state's own gates
+      C->part_c.push_back(svp::Gate{x.kind, x.q0, (uint8_t)(x.kind == SV_CZ ? x.q1 : 0)});
+      continue;
+    }
     if (x.kind == SV_H && x.layer == 0) continue;  // already the leading H layer
     if (x.kind == SV_CZ && C->in_a[x.q0] != C->in_a[x.q1]) {
       const int qa = C->in_a[x.q0] ? x.q0 : x.q1, qb = C->in_a[x.q0] ? x.q1 : x.q0;
@@ -207,6 +214,7 @@ sv_status run_branch_tree(sv_state *full, int n_base, const std::vector<svp::Gat
 extern "C" sv_status sv_branch_counts(const sv_lattice *lat, const sv_cut *cut, int counts[5]) {
   clear_error();
   if (!lat || !cut || !counts) return fail(SV_ERR_ARG, "sv_branch_counts: NULL argument");
+  if (cut->depth != 0) return fail(SV_ERR_ARG, "sv_branch_counts: cut depth must be 0");
   CutPlan C;
   sv_status st = plan_cut(lat, cut, &C);
   if (st != SV_OK) return st;
@@ -223,6 +231,8 @@ extern "C" sv_status sv_branch_amplitudes(const sv_lattice *lat, const sv_cut *c
   clear_error();
   if (!lat || !cut || (m && (!bits || !out_re_im)))
     return fail(SV_ERR_ARG, "sv_branch_amplitudes: NULL argument");
+  if (cut->depth != 0)
+    return fail(SV_ERR_ARG, "sv_branch_amplitudes: cut depth must be 0 (a part C needs the full state)");
   CutPlan C;
   sv_status st = plan_cut(lat, cut, &C);
   if (st != SV_OK) return st;
@@ -392,9 +402,12 @@ extern "C" sv_status sv_branch_full_state(const sv_lattice *lat, const sv_cut *c
   out->fresh = false;
   if (out->prof) out->other_launches += 1;
   // the crossing CZs taken as output signs act on the product state like any CZ
+  // (they commute with part C: neither qubit meets a non-diagonal gate after them)
   std::vector<svp::Gate> signs;
   for (const auto &sg : C.signs) signs.push_back(svp::Gate{svp::K_CZ, (uint8_t)sg.first, (uint8_t)sg.second});
   if (!signs.empty() && (st = apply_gates(out, signs)) != SV_OK) return st;
+  // part C (Eq. 3): the layers after the cut depth on the reconstructed state
+  if (!C.part_c.empty() && (st = apply_gates(out, C.part_c)) != SV_OK) return st;
   e = cudaStreamSynchronize(out->stream);
   if (e != cudaSuccess) return cuda_fail(e, "sv_branch_full_state");
   return SV_OK;

@@ -315,6 +315,76 @@ bool build_plan(int n, const std::vector<Gate> &gates, const Options &opt, bool 
       }
       return {nd, tot};
     };
+    // The register qubits of every stage, by the same greedy choice as below on copies of
+    // the schedule (they do not depend on the tile's bit order).
+    auto stage_register_qubits = [&]() {
+      std::vector<uint64_t> sets;
+      std::vector<char> dn = done;
+      size_t lf = left;
+      std::vector<int> by_qubit;
+      for (int bb = 0; bb < m; ++bb) by_qubit.push_back(bb);
+      std::sort(by_qubit.begin(), by_qubit.end(), [&](int a, int b) { return dp.tq[a] < dp.tq[b]; });
+      while (lf > 0) {
+        uint32_t Rm = pack ? 1u : 0u;
+        std::pair<int, int> cur;
+        {
+          std::vector<char> tmp = dn;
+          cur = run_stage(Rm, tmp, nullptr, nullptr);
+        }
+        for (int round = 0; round < r; ++round) {
+          int best = -1;
+          std::pair<int, int> bs = cur;
+          for (int bb : by_qubit) {
+            if ((Rm >> bb) & 1u) continue;
+            std::vector<char> tmp = dn;
+            const std::pair<int, int> sc = run_stage(Rm | (1u << bb), tmp, nullptr, nullptr);
+            if (sc.first > bs.first || (sc.first == bs.first && sc.second > bs.second)) { bs = sc; best = bb; }
+          }
+          if (best < 0) break;
+          Rm |= 1u << best;
+          cur = bs;
+        }
+        const std::pair<int, int> placed = run_stage(Rm, dn, nullptr, nullptr);
+        if (placed.second == 0) break;
+        lf -= (size_t)placed.second;
+        uint64_t q = 0;
+        for (int bb = 1; bb < m; ++bb)
+          if ((Rm >> bb) & 1u) q |= 1ull << dp.tq[bb];
+        sets.push_back(q);
+      }
+      return sets;
+    };
+    // Layout 1: the three box rows (tile bits 4, 5, 6; bank groups like qubits 1, 2, 3) are
+    // chosen so that the fewest stages lack a group (lane) qubit of some bank group: a stage
+    // has one for group k unless both qubit k+1 and row k are among its register qubits.
+    // Ties: the rows with the fewest non-diagonal gates (the order above).
+    if (opt.layout == 1 && m - c >= 3 && c == 4) {
+      const std::vector<uint64_t> regs = stage_register_qubits();
+      std::vector<int> high(dp.tq + 4, dp.tq + m);  // current order: quietest rows first
+      int best_miss = 1 << 30;
+      int best[3] = {high[0], high[1], high[2]};
+      for (size_t a = 0; a < high.size(); ++a)
+        for (size_t b = 0; b < high.size(); ++b)
+          for (size_t d = 0; d < high.size(); ++d) {
+            if (a == b || a == d || b == d) continue;
+            const int rows[3] = {high[a], high[b], high[d]};
+            int miss = 0;
+            for (uint64_t R : regs)
+              for (int k = 0; k < 3; ++k)
+                if (((R >> (k + 1)) & 1ull) && ((R >> rows[k]) & 1ull)) ++miss;
+            if (miss < best_miss) {
+              best_miss = miss;
+              for (int k = 0; k < 3; ++k) best[k] = rows[k];
+            }
+          }
+      std::vector<int> order(best, best + 3);
+      for (int q : high)
+        if (q != best[0] && q != best[1] && q != best[2]) order.push_back(q);
+      for (int i = 0; i < m - c; ++i) {
+        dp.tq[c + i] = (uint8_t)order[(size_t)i];
+        local_of[order[(size_t)i]] = c + i;
+      }
+    }
     while (left > 0) {
       // register bits by greedy lookahead: add the tile bit that lets the stage place the
       // most non-diagonal gates (then the most gates), up to r bits
@@ -357,8 +427,17 @@ bool build_plan(int n, const std::vector<Gate> &gates, const Options &opt, bool 
       // bits with unused tile bits (the fused kernel uses the first r of them)
       std::vector<int> rb = R;
       const int rpad = rk;
-      for (int b = pack ? 1 : 0; (int)rb.size() < rpad && b < m; ++b)
+      // layout 1: padding from the tile bits that toggle no bank group (7 and up) first,
+      // so that the ones that do (1..6) stay group bits, free to be conflict-free lanes
+      std::vector<int> pad_order;
+      if (opt.layout == 1)
+        for (int b = m - 1; b >= 1; --b) pad_order.push_back(b);
+      else
+        for (int b = pack ? 1 : 0; b < m; ++b) pad_order.push_back(b);
+      for (int b : pad_order) {
+        if ((int)rb.size() >= rpad) break;
         if (std::find(rb.begin(), rb.end(), b) == rb.end()) rb.push_back(b);
+      }
       for (int j = 0; j < rpad; ++j) ds.rbit[j] = (uint8_t)rb[j];
       std::vector<int> nonr;
       for (int b = pack ? 1 : 0; b < m; ++b)

@@ -40,7 +40,7 @@ class sv_lattice(ctypes.Structure):
 
 
 class sv_cut(ctypes.Structure):
-    _fields_ = [('half_a_mask', c_uint64), ('full_decomposition', c_int)]
+    _fields_ = [('half_a_mask', c_uint64), ('full_decomposition', c_int), ('depth', c_int)]
 
 
 class sv_plan_summary(ctypes.Structure):
@@ -236,7 +236,7 @@ def sv_norm(h):
 
 def sv_branch_amplitudes(lat, half_a_mask, bits, opts=None, full_decomposition=False):
     L = lat if isinstance(lat, sv_lattice) else lattice(lat)
-    cut = sv_cut(half_a_mask, int(bool(full_decomposition)))
+    cut = sv_cut(half_a_mask, int(bool(full_decomposition)), 0)
     b = np.ascontiguousarray(bits, dtype=np.uint64)
     out = np.zeros(2 * b.size, dtype=np.float64)
     _check(lib().sv_branch_amplitudes(ctypes.byref(L), ctypes.byref(cut), b.ctypes.data, b.size,
@@ -244,10 +244,11 @@ def sv_branch_amplitudes(lat, half_a_mask, bits, opts=None, full_decomposition=F
     return out.view(np.complex128)
 
 
-def sv_branch_full_state(lat, half_a_mask, h, opts=None, full_decomposition=False):
-    """Write sum_l A_l (x) B_l (the full state) into handle h."""
+def sv_branch_full_state(lat, half_a_mask, h, opts=None, full_decomposition=False, depth=0):
+    """Write sum_l A_l (x) B_l (the full state) into handle h; depth > 0: the halves take
+    layers 0..depth and the remaining layers (part C) run on the result."""
     L = lat if isinstance(lat, sv_lattice) else lattice(lat)
-    cut = sv_cut(half_a_mask, int(bool(full_decomposition)))
+    cut = sv_cut(half_a_mask, int(bool(full_decomposition)), int(depth))
     _check(lib().sv_branch_full_state(ctypes.byref(L), ctypes.byref(cut),
                                       ctypes.byref(opts) if opts is not None else None, h))
 
@@ -255,7 +256,7 @@ def sv_branch_full_state(lat, half_a_mask, h, opts=None, full_decomposition=Fals
 def sv_branch_counts(lat, half_a_mask, full_decomposition=False):
     """(crossing CZs, absorbed signs, branch bits of A, of B, summed branch bits)."""
     L = lat if isinstance(lat, sv_lattice) else lattice(lat)
-    cut = sv_cut(half_a_mask, int(bool(full_decomposition)))
+    cut = sv_cut(half_a_mask, int(bool(full_decomposition)), 0)
     out = np.zeros(5, dtype=np.int32)
     _check(lib().sv_branch_counts(ctypes.byref(L), ctypes.byref(cut), out.ctypes.data))
     return tuple(int(v) for v in out)

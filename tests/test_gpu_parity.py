@@ -232,24 +232,31 @@ def test_plan_kernels_bitwise_equal_to_interpreter(lat, gl):
     """The kernels compiled for a plan run the interpreter's arithmetic op for op.  Same
     stages for both: 13-qubit tiles (the largest the interpreter takes) and stages of
     qubit 0 + 3 (fuse_k = 3; the two kernels differ only in how many qubits a thread
-    holds, which changes no amplitude's sequence of operations)."""
+    holds, which changes no amplitude's sequence of operations).  The pipelined kernels
+    lay the tile out for the TMA copies and fill a stage's spare register slots with other
+    qubits, so a diagonal gate on such a qubit may run in registers instead of as a phase
+    at the stage's end (the same values to rounding): equal to 1e-6 and to the oracle."""
     if lat is not None:
         n, g = lat.n_qubits, sv.sv_generate_circuit(lat)
     else:
         n, g = 19, _to_lib(gl)
     out = {}
-    for jit in (-1, 1):
-        h = sv.sv_create(n, sv.options(jit=jit, tile_bits=13, fuse_k=3))
+    for key, kw in (('interp', dict(jit=-1)), ('plan', dict(jit=1, pipeline=-1)), ('pipelined', dict(jit=1))):
+        h = sv.sv_create(n, sv.options(tile_bits=13, fuse_k=3, **kw))
         try:
             sv.sv_set_profiling(h, True)
             sv.sv_apply_circuit(h, g)
             prof = sv.sv_get_profile(h)
-            out[jit] = sv.sv_copy_state(h, n)
+            out[key] = sv.sv_copy_state(h, n)
         finally:
             sv.sv_destroy(h)
-        assert (prof.jit_launches > 0) == (jit == 1)
-        assert prof.jit_launches == (prof.launches if jit == 1 else 0)
-    assert np.array_equal(out[-1].view(np.uint32), out[1].view(np.uint32))
+        assert (prof.jit_launches > 0) == (key != 'interp')
+        assert prof.jit_launches == (prof.launches if key != 'interp' else 0)
+    assert np.array_equal(out['interp'].view(np.uint32), out['plan'].view(np.uint32))
+    assert rel_l2(out['pipelined'], out['interp']) <= 1e-6
+    if lat is not None:
+        n_, gates = oracle_gates(lat)
+        assert rel_l2(out['pipelined'], csim.run(n_, gates)) <= REL_L2
 
 
 def test_amplitudes_and_probabilities_gather():
@@ -533,6 +540,44 @@ def test_branch_full_state_matches_oracle(full):
         sv.sv_destroy(h)
     assert rel_l2(got, want) <= REL_L2
     assert abs(n2 - 1) <= NORM_TOL
+
+
+@pytest.mark.parametrize('depth', [3, 6])
+@pytest.mark.parametrize('full', [False, True])
+def test_branch_full_state_with_part_c_matches_oracle(full, depth):
+    """Eq. 3: layers 0..depth through the tensor form of the cut decomposition (parts A
+    and B), the remaining layers (part C) on the reconstructed state."""
+    lat = inputs.lattice_for(4, 4, 11, seed=37)
+    half_a = (1 << 8) - 1
+    n, gates = oracle_gates(lat)
+    want = csim.run(n, gates)
+    h = sv.sv_create(n)
+    try:
+        sv.sv_branch_full_state(lat, half_a, h, full_decomposition=full, depth=depth)
+        got = sv.sv_copy_state(h, n)
+        n2, _ = sv.sv_norm(h)
+    finally:
+        sv.sv_destroy(h)
+    assert rel_l2(got, want) <= REL_L2
+    assert abs(n2 - 1) <= NORM_TOL
+
+
+def test_branch_full_state_28q_with_part_c_equals_direct_run():
+    """The 28-qubit check lattice cut after layer 5: parts A and B by the decomposition,
+    part C (layers 6..10) on the full 2^28 state, against the direct run."""
+    lat = inputs.C28
+    n = lat.n_qubits
+    a, b = sv.sv_create(n), sv.sv_create(n)
+    try:
+        sv.sv_branch_full_state(lat, inputs.C28_HALF_A, a, depth=5)
+        sv.sv_apply_circuit(b, sv.sv_generate_circuit(lat))
+        ip = sv.sv_inner_product(b, a)
+        n2a, _ = sv.sv_norm(a)
+    finally:
+        sv.sv_destroy(a)
+        sv.sv_destroy(b)
+    assert abs(n2a - 1) <= NORM_TOL
+    assert 1 - abs(ip) ** 2 / n2a <= 1e-9
 
 
 def test_branch_full_state_28q_equals_direct_run():
