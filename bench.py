@@ -67,9 +67,9 @@ def _peaks():
 # DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) per algorithmic byte of the
 # dominant kernels, from one ncu capture each on one pass of the 28-qubit depth-30 circuit
 # (2^28 amplitudes); a pass moves each amplitude once in and once out, so traffic scales
-# with the amplitudes.  None where no capture of the current kernel exists.
+# with the amplitudes.
 TRAFFIC_PER_ALGORITHMIC_BYTE = {
-    'sv_pass (pipelined)': None,
+    'sv_pass (pipelined)': (2.147896576e9 + 2.086447616e9) / (16.0 * 2 ** 28),
     'sv_pass': (2.147776e9 + 2.128476e9) / (16.0 * 2 ** 28),
     'fused_pass_kernel<f16>': (2.147810e9 + 2.087095e9) / (16.0 * 2 ** 28),
 }
