@@ -446,8 +446,8 @@ def main():
     ap.add_argument('--impl', default='ours', choices=['ours', 'reference'])
     ap.add_argument('--qubits', type=int, default=34, help='34 (headline); 30, 28 or 16 for smaller cases (profiling)')
     ap.add_argument('--paths', default='plain,f16x3,tf32x3,f16x3_raw,tf32x3_raw',
-                    help='comma list of plain, tf32x3, f16x3, tf32x3_raw, f16x3_raw, pergate, plain_interp, '
-                         'plain_previous')
+                    help='comma list of plain, tf32x3, f16x3, tf32x3_raw, f16x3_raw, f16x3_k4, tf32x3_k4, '
+                         'pergate, plain_interp, plain_previous')
     ap.add_argument('--tile-bits', type=int, default=0, help='tile qubits of the tile passes (0 = default)')
     ap.add_argument('--workload', default='34q', choices=['34q', 'batch', 'branch42', 'inner34', 'tensor28'],
                     help='34q: the headline line (with everything else inside it); the others print only '
@@ -536,6 +536,8 @@ def main():
     known = {'plain': dict(), 'tf32x3': dict(precision=sv.SV_PREC_TF32X3), 'f16x3': dict(precision=sv.SV_PREC_F16X3),
              'tf32x3_raw': dict(precision=sv.SV_PREC_TF32X3, norm_restore=-1),
              'f16x3_raw': dict(precision=sv.SV_PREC_F16X3, norm_restore=-1),
+             'f16x3_k4': dict(precision=sv.SV_PREC_F16X3, fuse_k=4),
+             'tf32x3_k4': dict(precision=sv.SV_PREC_TF32X3, fuse_k=4),
              'pergate': dict(precision=sv.SV_PREC_PERGATE), 'plain_interp': dict(jit=-1),
              'plain_previous': dict(pipeline=-1)}
     modes = [p for p in args.paths.split(',') if p in known]
@@ -659,24 +661,26 @@ def main():
         'cpu_baseline': cpu,
         'paths': results,
     }
-    # the tensor-core paths' own roofline: HBM and the tensor pipe (3 products of a
-    # 128 x 64 x 64 real GEMM per tile and stage with gates in its register qubits)
+    # the tensor-core paths' own roofline: HBM and the tensor pipe. A stage of k qubits
+    # with gates in it is, per 2^m-amplitude tile, a real GEMM of 2^(m-k) rows against a
+    # 2^(k+1) x 2^(k+1) matrix taken as 3 split products: 3 * 2^(m+k+3) flops.
     tc = {}
-    for name in ('f16x3', 'tf32x3'):
+    for name in ('f16x3', 'tf32x3', 'f16x3_k4', 'tf32x3_k4'):
         r = results.get(name, {})
         if 's_per_circuit' not in r:
             continue
-        summ, *_ = sv.sv_plan(n, gates, sv.options(precision=sv.SV_PREC_F16X3 if name == 'f16x3'
-                                                   else sv.SV_PREC_TF32X3))
-        m = 12
-        tflops = summ.matrix_stages * 2.0 ** (n - m) * 3 * 2 * (2 ** m // 32) * 64 * 64 / r['s_per_circuit'] / 1e12
-        peak = bf16_peak * TENSOR_RATIO[name]
+        kw = dict(known[name])
+        summ, *_ = sv.sv_plan(n, gates, sv.options(**kw))
+        m, k = 12, kw.get('fuse_k', 0) or 5
+        tflops = summ.matrix_stages * 2.0 ** (n - m) * 3 * 2.0 ** (m + k + 3) / r['s_per_circuit'] / 1e12
+        kind = name.split('_')[0]
+        peak = bf16_peak * TENSOR_RATIO[kind]
         tc[name] = {'hbm': {'achieved': r['achieved_gbs'], 'peak': hbm_peak, 'unit': 'GB/s',
                             'frac': r['achieved_gbs'] / hbm_peak},
                     'tensor': {'achieved': tflops, 'peak': peak, 'unit': 'TFLOP/s', 'frac': tflops / peak,
                                'peak_kind': 'measured bf16 burst x nominal %s/bf16 rate ratio %.3f'
-                                            % (name[:-2], TENSOR_RATIO[name]),
-                               'matrix_stages': summ.matrix_stages}}
+                                            % (kind[:-2], TENSOR_RATIO[kind]),
+                               'matrix_stages': summ.matrix_stages, 'k': k}}
     if tc:
         line['roofline_tensor_core_paths'] = tc
     if accuracy is not None:

@@ -73,7 +73,8 @@ typedef struct {
   int fuse_k;     /* qubits per register group besides qubit 0 (plain) or per fused   */
                   /* block (tensor cores), 1..5; 0 = the default 5 (plain kernels     */
                   /* compiled per plan use at most 4).  The tensor-core precisions    */
-                  /* take 5 only: any other value is SV_ERR_ARG.                       */
+                  /* take 5 (32x32 stage unitaries) or 4 (16x16, 12-qubit tiles only);  */
+                  /* any other value is SV_ERR_ARG.                                    */
   int precision;  /* SV_PREC_*                                            [PLAIN]       */
   int autotune;   /* 1 = pick shapes by timing, kept in a JSON cache (SV_AUTOTUNE_CACHE, */
                   /* default autotune.json beside the library) [0].  sv_apply_circuit  */

@@ -53,8 +53,9 @@ svp::Options plan_options(const sv_options &o) {
   p.m = o.tile_bits > 0 ? o.tile_bits : p.fused ? 12 : 13;
   p.c = o.low_bits > 0 ? o.low_bits : 4;
   p.pack = !p.fused;  // the plain kernel runs packed plans
-  // register qubits per thread of the tile kernels (packed: besides qubit 0)
-  p.rk = p.pack ? svk::tile_pass_register_slots() : 5;
+  // register qubits per thread of the tile kernels (packed: besides qubit 0; tensor
+  // cores: the block size, 5 or 4 qubits)
+  p.rk = p.pack ? svk::tile_pass_register_slots() : (o.fuse_k == 4 ? 4 : 5);
   p.r = std::min(o.fuse_k > 0 ? o.fuse_k : p.rk, p.rk);
   return p;
 }
@@ -92,8 +93,10 @@ sv_status check_options(const sv_options &o) {
   if (o.tile_bits != 0 && (o.tile_bits < 6 || o.tile_bits > svp::kMaxTileBits))
     return fail(SV_ERR_ARG, "options: tile_bits must be 0 or 6..14");
   const bool fused = o.precision == SV_PREC_TF32X3 || o.precision == SV_PREC_F16X3;
-  if (fused && o.fuse_k != 0 && o.fuse_k != 5)
-    return fail(SV_ERR_ARG, "options: the tensor-core precisions apply 5-qubit blocks (fuse_k 0 or 5)");
+  if (fused && o.fuse_k != 0 && o.fuse_k != 5 && o.fuse_k != 4)
+    return fail(SV_ERR_ARG, "options: the tensor-core precisions apply 5- or 4-qubit blocks (fuse_k 0, 5 or 4)");
+  if (fused && o.fuse_k == 4 && o.tile_bits != 0 && o.tile_bits != 12)
+    return fail(SV_ERR_ARG, "options: 4-qubit tensor-core blocks take 12-qubit tiles");
   if (o.tile_bits == 14 && (fused || o.jit < 0))
     return fail(SV_ERR_ARG, "options: 14-qubit tiles need the plain path's plan-specialised kernels");
   if (o.low_bits < 0 || o.low_bits > 13) return fail(SV_ERR_ARG, "options: low_bits must be 0..13");
@@ -303,7 +306,7 @@ sv_status run_plan(sv_state *s, const svp::Plan &P, const svk::DevPlanView &view
     const double bytes = (hp.flags & (svp::PF_INIT_UNIFORM | svp::PF_INIT_ZERO)) ? 8.0 * amps : 16.0 * amps;
     double *partials = sums && p + 1 == P.passes.size() ? s->d_sums + 2 : nullptr;
     prof_begin(s);
-    cudaError_t e = fused ? svk::launch_fused_pass(s->psi, s->n, view, (int)p, hp, s->stream, f16)
+    cudaError_t e = fused ? svk::launch_fused_pass(s->psi, s->n, view, (int)p, hp, s->stream, f16, P.rk)
                     : jit ? svj::launch_pass(jit, s->psi, s->n, view, (int)p, hp, s->stream, partials, &grid)
                           : svk::launch_tile_pass(s->psi, s->n, view, (int)p, hp, s->stream);
     prof_end(s, bytes);

@@ -27,10 +27,13 @@ int tile_pass_register_slots();
 // take up to svp::kMaxTileBits.
 int tile_pass_max_bits();
 
-// K4 fused tensor-core tile pass (tcgen05, split-TF32).
-// tile_bits 12 or 13; f16: F16x3 operands, else TF32x3
+// K4 fused tensor-core tile pass (tcgen05, split-TF32 or split-FP16).
+// r = register qubits of a stage: 5 (tile_bits 12 or 13) or 4 (tile_bits 12); f16: F16x3
+// operands, else TF32x3
 cudaError_t launch_fused_pass(float2 *psi, int n, const DevPlanView &plan, int pass_index,
-                              const svp::DevPass &host_pass, cudaStream_t st, bool f16);
+                              const svp::DevPass &host_pass, cudaStream_t st, bool f16, int r);
+cudaError_t launch_fused_pass_r5(float2 *psi, int n, const DevPlanView &plan, int pass_index,
+                                 const svp::DevPass &host_pass, cudaStream_t st, bool f16);
 bool fused_supported();
 
 // Per-gate sweeps (K2 one-qubit pair update, K3 diagonal factor on a bit pattern).

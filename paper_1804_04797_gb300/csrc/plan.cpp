@@ -174,6 +174,7 @@ bool build_plan(int n, const std::vector<Gate> &gates, const Options &opt, bool 
   const int rk = std::min(opt.rk, pack ? m - 1 : m);
   const int r = std::min(std::min(opt.r, rk), m);
   if (m > kMaxTileBits || rk > kMaxReg || r < 1 || c < 0 || m - rk > 12) { *err = "bad tile shape"; return false; }
+  P.rk = rk;
   if (pack && (rk < 1 || m < rk + 1 || c < 1)) { *err = "packed plan needs tiles of >= rk + 1 qubits"; return false; }
   if (opt.layout == 1 && (!pack || c != 4 || m < 7 || m > 13)) { *err = "TMA tile layout needs packed tiles of 7..13 qubits with 4 low ones"; return false; }
 

@@ -69,6 +69,7 @@ struct Plan {
   bool init_uniform = false;
   double hbm_bytes = 0;
   int layout = 0;  // shared-memory layout of the packed tiles (Options::layout)
+  int rk = 0;      // register qubits a thread holds per stage (Options::rk, capped by the tile)
   // layout 1: compute groups of each pass's pipelined kernel (0 = the default for the tile
   // size); set by the autotuner, read by the kernel generator
   std::vector<uint8_t> pipe_groups;

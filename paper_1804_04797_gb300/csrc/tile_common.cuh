@@ -1,23 +1,27 @@
 // Device code shared by the tile-pass kernels (plain and fused): the register-group
 // gate actions of the plain path (also used for the fused path's diagonal epilogue),
-// the shared-memory swizzle, and the gathered-tile load/store.
-#pragma once
+// the shared-memory swizzle, and the gathered-tile load/store.  A translation unit picks
+// the row width (SV_TILE_R) and the namespace its copy lives in (SV_TILE_NS), so that
+// kernels of several widths link into one library.
 
 #include <cuda_runtime.h>
 
 #include "kernels.h"
 
+#ifndef SV_TILE_NS
+#define SV_TILE_NS tile
+#endif
+
 namespace svk {
-namespace tile {
+namespace SV_TILE_NS {
 
 using svp::DevOp;
 using svp::DevPass;
 using svp::DevStage;
 
 // Register qubits per thread (each thread holds 2^kR amplitudes of a stage).  Every
-// translation unit that includes this header picks its width; all kernels use 5 (32
-// amplitudes, 256 threads per 2^13 tile; for the tensor-core kernel one row of the 32x32
-// unitary per thread).  Width 4 (twice the warps, twice the stages) measured 40 % slower.
+// translation unit that includes this header picks its width: the tensor-core kernels
+// take 5 (one row of the 32x32 stage unitary per thread) or 4 (16x16 blocks).
 #ifndef SV_TILE_R
 #define SV_TILE_R 5
 #endif
@@ -484,5 +488,5 @@ __device__ __forceinline__ void process_tile_plain(float2 *__restrict__ psi, con
   __syncthreads();
 }
 
-}  // namespace tile
+}  // namespace SV_TILE_NS
 }  // namespace svk
