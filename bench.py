@@ -446,8 +446,9 @@ def main():
     ap.add_argument('--impl', default='ours', choices=['ours', 'reference'])
     ap.add_argument('--qubits', type=int, default=34, help='34 (headline); 30, 28 or 16 for smaller cases (profiling)')
     ap.add_argument('--paths', default='plain,f16x3,tf32x3,f16x3_raw,tf32x3_raw',
-                    help='comma list of plain, tf32x3, f16x3, tf32x3_raw, f16x3_raw, f16x3_k4, tf32x3_k4, '
-                         'pergate, plain_interp, plain_previous')
+                    help='comma list of plain, tf32x3, f16x3, tf32x3_raw, f16x3_raw (tensor cores in the '
+                         'pipelined plan kernels), f16x3_tile, tf32x3_tile, f16x3_k4, tf32x3_k4 (the tile '
+                         'kernel), pergate, plain_interp, plain_previous')
     ap.add_argument('--tile-bits', type=int, default=0, help='tile qubits of the tile passes (0 = default)')
     ap.add_argument('--workload', default='34q', choices=['34q', 'batch', 'branch42', 'inner34', 'tensor28'],
                     help='34q: the headline line (with everything else inside it); the others print only '
@@ -536,6 +537,8 @@ def main():
     known = {'plain': dict(), 'tf32x3': dict(precision=sv.SV_PREC_TF32X3), 'f16x3': dict(precision=sv.SV_PREC_F16X3),
              'tf32x3_raw': dict(precision=sv.SV_PREC_TF32X3, norm_restore=-1),
              'f16x3_raw': dict(precision=sv.SV_PREC_F16X3, norm_restore=-1),
+             'f16x3_tile': dict(precision=sv.SV_PREC_F16X3, pipeline=-1),
+             'tf32x3_tile': dict(precision=sv.SV_PREC_TF32X3, pipeline=-1),
              'f16x3_k4': dict(precision=sv.SV_PREC_F16X3, fuse_k=4),
              'tf32x3_k4': dict(precision=sv.SV_PREC_TF32X3, fuse_k=4),
              'pergate': dict(precision=sv.SV_PREC_PERGATE), 'plain_interp': dict(jit=-1),
@@ -665,7 +668,7 @@ def main():
     # with gates in it is, per 2^m-amplitude tile, a real GEMM of 2^(m-k) rows against a
     # 2^(k+1) x 2^(k+1) matrix taken as 3 split products: 3 * 2^(m+k+3) flops.
     tc = {}
-    for name in ('f16x3', 'tf32x3', 'f16x3_k4', 'tf32x3_k4'):
+    for name in ('f16x3', 'tf32x3', 'f16x3_tile', 'tf32x3_tile', 'f16x3_k4', 'tf32x3_k4'):
         r = results.get(name, {})
         if 's_per_circuit' not in r:
             continue

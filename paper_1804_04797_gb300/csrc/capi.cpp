@@ -62,6 +62,20 @@ svp::Options plan_options(const sv_options &o) {
 
 svp::Options apply_plan_options(const sv_options &o, int n, bool *want_jit) {
   svp::Options po = plan_options(o);
+  // tensor cores on the pipelined plan kernels (the default for 5-qubit blocks on
+  // 12-qubit tiles): a fused packed plan -- stages of tile bit 0 and four register slots,
+  // the TMA tile layout -- whose matrix stages the generated kernels run on tcgen05
+  if (po.fused && n >= 12 && o.pipeline >= 0 && o.jit >= 0 && (o.fuse_k == 0 || o.fuse_k == 5) &&
+      (o.tile_bits == 0 || o.tile_bits == 12) && (o.low_bits == 0 || o.low_bits == 4)) {
+    po.pack = true;
+    po.layout = 1;
+    po.m = 12;
+    po.c = 4;
+    po.rk = 4;
+    po.r = 4;
+    *want_jit = true;
+    return po;
+  }
   // the tensor-core kernel takes 12- or 13-qubit tiles; smaller states use the plain one
   if (po.fused && std::min(po.m, n) < 12) {
     po.fused = false;
@@ -325,7 +339,6 @@ sv_status run_plan(sv_state *s, const svp::Plan &P, const svk::DevPlanView &view
   return SV_OK;
 }
 
-sv_status build_stage_mats(svp::Plan *P, const std::vector<svp::Gate> &g, int r);
 
 }  // namespace svc
 
@@ -482,12 +495,13 @@ sv_status apply_gates(sv_state *s, const std::vector<svp::Gate> &g) {
   if (!g.empty()) mix(g.data(), g.size() * sizeof(svp::Gate));
   if (s->plan_valid && s->plan_key == key) {
     const bool f16 = s->opts.precision == SV_PREC_F16X3;
-    if ((st = run_plan(s, s->plan, s->plan_view, s->plan_po.fused, f16, s->plan_jit)) != SV_OK) {
+    const bool kfused = s->plan_po.fused && !s->plan_jit;  // the tensor-core tile kernel
+    if ((st = run_plan(s, s->plan, s->plan_view, kfused, f16, s->plan_jit)) != SV_OK) {
       s->plan_valid = false;
       return st;
     }
     s->fresh = false;
-    return s->plan_po.fused ? check_fused_error(s, s->plan_view) : SV_OK;
+    return kfused ? check_fused_error(s, s->plan_view) : SV_OK;
   }
   s->plan_valid = false;
   svp::Plan P;
@@ -495,7 +509,7 @@ sv_status apply_gates(sv_state *s, const std::vector<svp::Gate> &g) {
   bool want_jit = false;
   svp::Options po = apply_plan_options(s->opts, s->n, &want_jit);
   PlainTune tune;
-  if (s->opts.autotune == 1 && want_jit && po.layout == 1 && s->fresh && s->opts.tile_bits == 0) {
+  if (s->opts.autotune == 1 && want_jit && !po.fused && po.layout == 1 && s->fresh && s->opts.tile_bits == 0) {
     if ((st = autotune_plain(s, g, po, &tune)) != SV_OK) return st;
     po.m = tune.m;
   }
@@ -504,11 +518,28 @@ sv_status apply_gates(sv_state *s, const std::vector<svp::Gate> &g) {
   // a tensor-core request on a state (or tile) below 12 qubits runs the plain kernel
   s->plan_fallback = (s->opts.precision == SV_PREC_TF32X3 || s->opts.precision == SV_PREC_F16X3) && !po.fused;
   const svj::Module *jit = nullptr;
+  const bool f16 = s->opts.precision == SV_PREC_F16X3;
   if (want_jit) {
+    if (po.fused) {  // matrix stages of the plan kernels: their B operands (and the
+      // norm restore choice, which the generated code bakes in)
+      P.mma = f16 ? 1 : 2;
+      if ((st = build_stage_mats_packed(&P, g, f16)) != SV_OK) return st;
+      if (s->opts.norm_restore < 0)
+        for (svp::DevPass &dp : P.passes) dp.flags |= svp::PF_RAW;
+    }
     std::string jerr;
     jit = svj::get_module(P, po.rk, &jerr);
     if (!jit && s->opts.jit == 1) return fail(SV_ERR_CUDA, jerr.c_str());
-    if (!jit) {
+    if (!jit && po.fused) {
+      // no compiler: the tensor-core tile kernel with its own plan
+      sv_options o = s->opts;
+      o.pipeline = -1;
+      bool unused = false;
+      po = apply_plan_options(o, s->n, &unused);
+      P = svp::Plan();
+      if (!svp::build_plan(s->n, g, po, s->fresh, &P, &err))
+        return fail(SV_ERR_ARG, err ? err : "planning failed");
+    } else if (!jit) {
       // no compiler: the interpreting kernel, with its register width, on tiles it takes
       po.m = std::min(po.m, svk::tile_pass_max_bits());
       po.layout = 0;
@@ -519,18 +550,18 @@ sv_status apply_gates(sv_state *s, const std::vector<svp::Gate> &g) {
         return fail(SV_ERR_ARG, err ? err : "planning failed");
     }
   }
-  const bool f16 = s->opts.precision == SV_PREC_F16X3;
-  if (po.fused && (st = build_stage_mats(&P, g, std::min(po.r, std::min(po.m, s->n)), f16)) != SV_OK) return st;
-  if (po.fused && s->opts.norm_restore < 0)
+  const bool kfused = po.fused && !jit;  // the tensor-core tile kernel
+  if (kfused && (st = build_stage_mats(&P, g, std::min(po.r, std::min(po.m, s->n)), f16)) != SV_OK) return st;
+  if (kfused && s->opts.norm_restore < 0)
     for (svp::DevPass &dp : P.passes) dp.flags |= svp::PF_RAW;
-  if (po.fused)
+  if (kfused)
     for (const svp::DevPass &dp : P.passes)
       if (dp.stage_count > 256) return fail(SV_ERR_ARG, "fused path: more than 256 stages in one pass");
   svk::DevPlanView view;
   if ((st = upload_plan(s, P, &view)) != SV_OK) return st;
-  if ((st = run_plan(s, P, view, po.fused, f16, jit)) != SV_OK) return st;
+  if ((st = run_plan(s, P, view, kfused, f16, jit)) != SV_OK) return st;
   s->fresh = false;
-  if (po.fused && (st = check_fused_error(s, view)) != SV_OK) return st;
+  if (kfused && (st = check_fused_error(s, view)) != SV_OK) return st;
   s->plan = std::move(P);
   s->plan_po = po;
   s->plan_jit = jit;
@@ -896,21 +927,35 @@ sv_status sv_jit_check(int n_qubits, const sv_gate *gates, size_t n_gates, const
   if (st != SV_OK) return st;
   std::vector<svp::Gate> g;
   if ((st = convert_gates(n_qubits, gates, n_gates, false, &g)) != SV_OK) return st;
-  svp::Options po = plan_options(o);
-  po.fused = false;
-  po.pack = true;
-  po.rk = svj::register_slots();
-  po.r = std::min(po.r, po.rk);
-  if (o.tile_bits == 0) po.m = svj::kTileBits;
-  if (o.pipeline >= 0 && po.c == 4 && std::min(po.m, n_qubits) >= 10 && std::min(po.m, n_qubits) <= 13) po.layout = 1;
+  // the tensor-core precisions: the plan kernels with matrix stages, as sv_apply_circuit
+  // builds them; otherwise the plain path's plan kernels
+  bool want_jit = false;
+  svp::Options po = apply_plan_options(o, n_qubits, &want_jit);
+  const bool tc = po.fused && po.pack;
+  if (!tc) {
+    po = plan_options(o);
+    po.fused = false;
+    po.pack = true;
+    po.rk = svj::register_slots();
+    po.r = std::min(po.r, po.rk);
+    if (o.tile_bits == 0) po.m = svj::kTileBits;
+    if (o.pipeline >= 0 && po.c == 4 && std::min(po.m, n_qubits) >= 10 && std::min(po.m, n_qubits) <= 13) po.layout = 1;
+  }
   svp::Plan P;
   const char *err = nullptr;
   if (!svp::build_plan(n_qubits, g, po, fresh_state != 0, &P, &err))
     return fail(SV_ERR_ARG, err ? err : "planning failed");
+  if (tc) {
+    const bool f16 = o.precision == SV_PREC_F16X3;
+    P.mma = f16 ? 1 : 2;
+    if ((st = build_stage_mats_packed(&P, g, f16)) != SV_OK) return st;
+    if (o.norm_restore < 0)
+      for (svp::DevPass &dp : P.passes) dp.flags |= svp::PF_RAW;
+  }
   std::vector<std::string> cubins;
   std::string lg;
   bool ok = svj::compile_plan(P, po.rk, "sm_103a", &cubins, &lg, "");
-  if (ok && !P.passes.empty()) {
+  if (ok && !P.passes.empty() && !tc) {
     // and the last pass as the inner-product variant (the backward states of the
     // inner-product amplitudes)
     std::string cubin, lg2;

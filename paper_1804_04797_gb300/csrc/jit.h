@@ -37,6 +37,10 @@ constexpr int kPipeSlots12 = 6;
 bool pipe_shape(int m, int *groups, int *slots);
 // The shape of pass `pass` of P: the tile size's default, or the plan's pipe_groups entry.
 bool pass_pipe_shape(const svp::Plan &P, int pass, int *groups, int *slots);
+// Matrix stages of a pass that run on the tensor cores (Plan::mma), and the shared memory
+// of their B buffers.
+int pass_matrix_stages(const svp::Plan &P, int pass);
+size_t pass_mma_smem(const svp::Plan &P, int pass);
 // Whether pass `pass` of P runs on the pipelined kernel (layout-1 plan, at least one stage).
 bool pass_is_pipelined(const svp::Plan &P, int pass);
 // Threads of the pipelined kernel's CTA for a pass: the compute groups, the producer warp

@@ -143,4 +143,61 @@ sv_status build_stage_mats(svp::Plan *P, const std::vector<svp::Gate> &g, int r,
   return SV_OK;
 }
 
+// The same for the matrix stages of the pipelined plan kernels (packed plans): a stage's
+// 5-qubit unitary U (matrix bit 0 = tile bit 0, bit j + 1 = register slot j) as B[k][n]
+// with k, n = 32 * (re/im) + j, i.e. [[Re U^T, Im U^T], [-Im U^T, Re U^T]], stored as rows
+// n of K in the K-major layout; per matrix stage the hi part, then the lo part.
+sv_status build_stage_mats_packed(svp::Plan *P, const std::vector<svp::Gate> &g, bool f16) {
+  P->mats.clear();
+  std::vector<double> u;
+  constexpr int d = 32, kK = 64;
+  const int part_bytes = kK * kK * (f16 ? 2 : 4);
+  const size_t stage_floats = (size_t)2 * part_bytes / 4;
+  const double bscale = f16 ? std::ldexp(1.0, svk::kF16BExp) : 1.0;
+  for (size_t s = 0; s < P->stages.size(); ++s) {
+    svp::DevStage &ds = P->stages[s];
+    ds.unitary = 1;
+    if (P->stage_gates[s].empty()) {
+      ds.diag_only = 1;
+      continue;
+    }
+    ds.diag_only = 0;
+    for (int gi : P->stage_gates[s]) {
+      const int k = g[gi].kind;
+      if (k == svp::K_P0 || k == svp::K_P1 || k == svp::K_PEQ) ds.unitary = 0;
+    }
+    svp::stage_unitary(*P, g, (int)s, 5, &u);
+    const size_t off = P->mats.size();
+    ds.mat_begin = (uint32_t)off;
+    P->mats.resize(off + stage_floats, 0.f);
+    char *hi = reinterpret_cast<char *>(P->mats.data() + off);
+    char *lo = hi + part_bytes;
+    for (int jo = 0; jo < d; ++jo) {
+      for (int ji = 0; ji < d; ++ji) {
+        const double ur = u[2 * ((size_t)jo * d + ji)], ui = u[2 * ((size_t)jo * d + ji) + 1];
+        const double b[2][2] = {{ur, ui}, {-ui, ur}};  // [re/im of the input k][re/im of the output n]
+        for (int ri = 0; ri < 2; ++ri) {
+          for (int ro = 0; ro < 2; ++ro) {
+            const double x = b[ri][ro] * bscale;
+            const int n = 32 * ro + jo, k = 32 * ri + ji;
+            const uint32_t o = b_offset(n, k, kK, f16);
+            if (f16) {
+              const __half h = __float2half_rn((float)x);
+              const __half l = __float2half_rn((float)(x - (double)__half2float(h)));
+              std::memcpy(hi + o, &h, 2);
+              std::memcpy(lo + o, &l, 2);
+            } else {
+              const float h = tf32_round_host((float)x);
+              const float l = tf32_round_host((float)(x - (double)h));
+              std::memcpy(hi + o, &h, 4);
+              std::memcpy(lo + o, &l, 4);
+            }
+          }
+        }
+      }
+    }
+  }
+  return SV_OK;
+}
+
 }  // namespace svc

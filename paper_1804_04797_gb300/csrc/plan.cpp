@@ -674,9 +674,13 @@ void stage_unitary(const Plan &P, const std::vector<Gate> &gates, int stage, int
   int local_of[64];
   for (int q = 0; q < 64; ++q) local_of[q] = -1;
   for (int i = 0; pass && i < pass->m; ++i) local_of[pass->tq[i]] = i;
+  // packed plans: matrix bit 0 is tile bit 0 (the pack bit), bit j + 1 register slot j
+  const bool packed = pass && (pass->flags & PF_PACKED);
   auto reg_of = [&](int q) {
-    for (int j = 0; j < r; ++j)
-      if (local_of[q] >= 0 && ds.rbit[j] == local_of[q]) return j;
+    if (local_of[q] < 0) return -1;
+    if (packed && local_of[q] == 0) return 0;
+    for (int j = 0; j < (packed ? r - 1 : r); ++j)
+      if (ds.rbit[j] == local_of[q]) return packed ? j + 1 : j;
     return -1;
   };
   for (int gi : P.stage_gates[stage]) {

@@ -73,6 +73,9 @@ struct Plan {
   // layout 1: compute groups of each pass's pipelined kernel (0 = the default for the tile
   // size); set by the autotuner, read by the kernel generator
   std::vector<uint8_t> pipe_groups;
+  // plan kernels of a fused packed plan: its matrix stages run on the tensor cores
+  // (0 = none, 1 = F16x3, 2 = TF32x3; B operands in `mats`, set with the plan's matrices)
+  int mma = 0;
 };
 
 // Build the plan.  fresh_state: the state is |0..0> and was never written, so a
@@ -86,7 +89,8 @@ bool build_plan(int n, const std::vector<Gate> &gates, const Options &opt, bool 
 void kind_matrix(int kind, double m[8]);
 
 // The unitary of a stage's inner ops on its r register bits: 2^r x 2^r complex
-// (row-major, re/im interleaved; row/column bit j = register bit j), in double precision.
+// (row-major, re/im interleaved; row/column bit j = register bit j; in a packed plan bit 0
+// is tile bit 0 and bit j + 1 register slot j), in double precision.
 void stage_unitary(const Plan &plan, const std::vector<Gate> &gates, int stage, int r,
                    std::vector<double> *u);
 

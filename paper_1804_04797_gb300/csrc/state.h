@@ -106,5 +106,7 @@ void write_autotune_cache(const std::map<std::string, int> &c);
 sv_status take_pending_error(sv_state *s);
 // Fused path: the stage unitaries as split-TF32 operands (see k_fused.cu).
 sv_status build_stage_mats(svp::Plan *P, const std::vector<svp::Gate> &g, int r, bool f16);
+// B operands of a fused packed plan's matrix stages (the pipelined plan kernels).
+sv_status build_stage_mats_packed(svp::Plan *P, const std::vector<svp::Gate> &g, bool f16);
 
 }  // namespace svc

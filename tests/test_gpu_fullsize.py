@@ -46,6 +46,9 @@ def test_30q_depth20_full_state_matches_oracle(record_property):
              ('tf32x3', dict(precision=sv.SV_PREC_TF32X3)), ('f16x3', dict(precision=sv.SV_PREC_F16X3)),
              ('tf32x3_raw', dict(precision=sv.SV_PREC_TF32X3, norm_restore=-1)),
              ('f16x3_raw', dict(precision=sv.SV_PREC_F16X3, norm_restore=-1)),
+             ('tf32x3_tile_kernel', dict(precision=sv.SV_PREC_TF32X3, pipeline=-1)),
+             ('f16x3_tile_kernel', dict(precision=sv.SV_PREC_F16X3, pipeline=-1)),
+             ('f16x3_tile_kernel_raw', dict(precision=sv.SV_PREC_F16X3, pipeline=-1, norm_restore=-1)),
              ('tf32x3_k4', dict(precision=sv.SV_PREC_TF32X3, fuse_k=4)),
              ('f16x3_k4', dict(precision=sv.SV_PREC_F16X3, fuse_k=4)),
              ('f16x3_k4_raw', dict(precision=sv.SV_PREC_F16X3, fuse_k=4, norm_restore=-1))]

@@ -89,18 +89,23 @@ def test_sizes_match_oracle(lat):
         assert abs(norm2 - 1) <= NORM_TOL
 
 
-@pytest.mark.parametrize('k', [5, 4], ids=['k5', 'k4'])
+# the tensor-core kernels: matrix stages of the pipelined plan kernels (5-qubit blocks, the
+# default), and the tile kernel with 5- and 4-qubit blocks
+TC_KERNELS = {'k5_plan': dict(fuse_k=5), 'k5_tile': dict(fuse_k=5, pipeline=-1), 'k4_tile': dict(fuse_k=4)}
+
+
+@pytest.mark.parametrize('kernel', list(TC_KERNELS))
 @pytest.mark.parametrize('restore', [0, -1], ids=['restored', 'raw'])
 @pytest.mark.parametrize('prec', [TC, H16], ids=['tf32x3', 'f16x3'])
 @pytest.mark.parametrize('lat', [inputs.C16, inputs.lattice_for(4, 5, 18, seed=11)], ids=['16q', '20q'])
-def test_tensor_core_paths_with_and_without_the_norm_restore(lat, prec, restore, k):
-    """Both tensor-core formats and block sizes (32x32 and 16x16 stage unitaries) against
-    the oracle, with the per-tile norm restore on and off: rel-L2 is the criterion in both
-    cases; without the restore the norm shows the raw drift of the truncating
-    accumulation (bounded loosely, recorded)."""
+def test_tensor_core_paths_with_and_without_the_norm_restore(lat, prec, restore, kernel):
+    """Both tensor-core formats, both kernels and both block sizes (32x32 and 16x16 stage
+    unitaries) against the oracle, with the per-tile norm restore on and off: rel-L2 is
+    the criterion in both cases; without the restore the norm shows the raw drift of the
+    truncating accumulation (bounded loosely, recorded)."""
     n, gates = oracle_gates(lat)
     want = csim.run(n, gates)
-    psi, norm2, _ = run_gpu(lat, precision=prec, norm_restore=restore, fuse_k=k)
+    psi, norm2, _ = run_gpu(lat, precision=prec, norm_restore=restore, **TC_KERNELS[kernel])
     assert rel_l2(psi, want) <= REL_L2
     assert abs(norm2 - 1) <= (NORM_TOL if restore == 0 else 1e-4)
 

@@ -149,10 +149,18 @@ def _all_kind_gates(n, count, seed):
     return sv.gates_from_tuples(out)
 
 
-@pytest.mark.parametrize('case', ['16q_d10', '30q_d20', 'all_kinds_18q', 'tile9_all_kinds_14q', 'projectors_12q'])
+@pytest.mark.parametrize('case', ['16q_d10', '30q_d20', 'all_kinds_18q', 'tile9_all_kinds_14q', 'projectors_12q',
+                                  'f16x3_34q_d30', 'tf32x3_16q_d10', 'f16x3_raw_all_kinds_14q'])
 def test_plan_kernels_compile_without_a_device(case):
-    """The code generator's kernels compile for sm_103a (NVRTC, no GPU needed)."""
-    if case == '16q_d10':
+    """The code generator's kernels compile for sm_103a (NVRTC, no GPU needed), with
+    tensor-core matrix stages for the split-precision modes."""
+    if case == 'f16x3_34q_d30':
+        n, g, o = 34, sv.sv_generate_circuit(inputs.C34), sv.options(precision=sv.SV_PREC_F16X3)
+    elif case == 'tf32x3_16q_d10':
+        n, g, o = 16, sv.sv_generate_circuit(inputs.C16), sv.options(precision=sv.SV_PREC_TF32X3)
+    elif case == 'f16x3_raw_all_kinds_14q':
+        n, g, o = 14, _all_kind_gates(14, 120, 6), sv.options(precision=sv.SV_PREC_F16X3, norm_restore=-1)
+    elif case == '16q_d10':
         n, g, o = 16, sv.sv_generate_circuit(inputs.C16), None
     elif case == '30q_d20':
         n, g, o = 30, sv.sv_generate_circuit(inputs.C30), None
