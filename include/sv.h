@@ -79,9 +79,12 @@ typedef struct {
   int autotune;   /* 1 = pick shapes by timing, kept in a JSON cache (SV_AUTOTUNE_CACHE, */
                   /* default autotune.json beside the library) [0].  sv_apply_circuit  */
                   /* on a fresh state with plan-specialised kernels and tile_bits 0:   */
-                  /* the tile size (12 or 13 qubits) and each pass's compute groups of */
-                  /* the pipelined kernel, timed on the circuit itself (its first call */
-                  /* runs the plan a few times); sv_apply_batch: the tile size.        */
+                  /* the tile size and the fusion width -- 12- or 13-qubit tiles with  */
+                  /* 5-qubit stages, or 12-qubit tiles with 6-qubit stages (fuse_k 0   */
+                  /* only; otherwise the width stays fuse_k) -- and each pass's        */
+                  /* compute groups of the pipelined kernel, timed on the circuit      */
+                  /* itself (its first call runs the candidate plans a few times);     */
+                  /* sv_apply_batch: the tile size.                                    */
   void *stream;   /* cudaStream_t used by the handle                      [legacy 0]    */
   int tile_bits;  /* qubits per gathered tile, 6..14 (14: plan-specialised kernels    */
                   /* only) [12 on plan-specialised and tensor-core kernels, 13 on the  */

@@ -364,15 +364,18 @@ sv_status check_fused_error(sv_state *s, const svk::DevPlanView &view) {
 
 // ---- autotuning of the plain path on plan-specialised kernels ------------------------
 // (sv_options.autotune = 1, a fresh state, the pipelined kernels): the tile size (12 or 13
-// qubits) and, per pass, the pipelined kernel's compute groups (3 or 2 on 12-qubit tiles;
-// the slots stay six) are picked by timing this circuit -- whole runs of its plan, CUDA
-// events around every pass launch -- and the choice is kept in the JSON cache under
-// "<device>|circuit|<n>|<hash of the gate list and options>" (entries |m, |passes and |p<i>).
+// qubits), the fusion width (stages of 5 or 6 qubits: 4 or 5 register slots besides the
+// pack bit) and, per pass, the pipelined kernel's compute groups (3 or 2 on 12-qubit
+// tiles; the slots stay six) are picked by timing this circuit -- whole runs of each
+// candidate plan, CUDA events around every pass launch -- and the choice is kept in the
+// JSON cache under "<device>|circuit|<n>|<hash of the gate list and options>" (entries
+// |m, |k (qubits per stage), |passes and |p<i>).
 
 namespace {
 
 struct PlainTune {
   int m = 0;
+  int kpr = 0;  // register slots besides the pack bit: stages of kpr + 1 qubits (the fusion width)
   std::vector<uint8_t> groups;
 };
 
@@ -419,9 +422,10 @@ sv_status time_plan(sv_state *s, const svp::Plan &P, const svk::DevPlanView &vie
 sv_status autotune_plain(sv_state *s, const std::vector<svp::Gate> &g, const svp::Options &base, PlainTune *out) {
   const std::string key = circuit_tune_key(s, g, base);
   std::map<std::string, int> cache = read_autotune_cache();
-  auto m_it = cache.find(key + "|m"), np_it = cache.find(key + "|passes");
-  if (m_it != cache.end() && np_it != cache.end()) {
+  auto m_it = cache.find(key + "|m"), np_it = cache.find(key + "|passes"), k_it = cache.find(key + "|k");
+  if (m_it != cache.end() && np_it != cache.end() && k_it != cache.end()) {
     out->m = m_it->second;
+    out->kpr = k_it->second - 1;
     out->groups.assign((size_t)np_it->second, 0);
     for (size_t p = 0; p < out->groups.size(); ++p) {
       auto it = cache.find(key + "|p" + std::to_string(p));
@@ -430,10 +434,16 @@ sv_status autotune_plain(sv_state *s, const std::vector<svp::Gate> &g, const svp
     return SV_OK;
   }
   double best_total = 1e300;
-  for (int m : {12, 13}) {
+  // candidates: (tile qubits, register slots) -- 12- and 13-qubit tiles with stages of
+  // five qubits, 12-qubit tiles with stages of six (64 amplitudes a thread)
+  const int cand[3][2] = {{12, 4}, {13, 4}, {12, 5}};
+  for (const auto &c : cand) {
+    const int m = c[0], kpr = c[1];
     if (m > s->n) continue;
     svp::Options po = base;
     po.m = m;
+    po.rk = kpr;
+    if (s->opts.fuse_k == 0) po.r = kpr;
     svp::Plan P;
     const char *err = nullptr;
     if (!svp::build_plan(s->n, g, po, true, &P, &err)) return fail(SV_ERR_ARG, err ? err : "planning failed");
@@ -458,11 +468,13 @@ sv_status autotune_plain(sv_state *s, const std::vector<svp::Gate> &g, const svp
     if (total < best_total) {
       best_total = total;
       out->m = m;
+      out->kpr = kpr;
       out->groups = best_g;
     }
   }
   if (out->m == 0) return fail(SV_ERR_ARG, "autotune: no candidate tile size");
   cache[key + "|m"] = out->m;
+  cache[key + "|k"] = out->kpr + 1;
   cache[key + "|passes"] = (int)out->groups.size();
   for (size_t p = 0; p < out->groups.size(); ++p) cache[key + "|p" + std::to_string(p)] = out->groups[p];
   write_autotune_cache(cache);
@@ -512,6 +524,8 @@ sv_status apply_gates(sv_state *s, const std::vector<svp::Gate> &g) {
   if (s->opts.autotune == 1 && want_jit && !po.fused && po.layout == 1 && s->fresh && s->opts.tile_bits == 0) {
     if ((st = autotune_plain(s, g, po, &tune)) != SV_OK) return st;
     po.m = tune.m;
+    po.rk = tune.kpr;
+    if (s->opts.fuse_k == 0) po.r = tune.kpr;
   }
   if (!svp::build_plan(s->n, g, po, s->fresh, &P, &err)) return fail(SV_ERR_ARG, err ? err : "planning failed");
   if (tune.m && tune.groups.size() == P.passes.size()) P.pipe_groups = tune.groups;

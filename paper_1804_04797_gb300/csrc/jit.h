@@ -40,6 +40,7 @@ bool pass_pipe_shape(const svp::Plan &P, int pass, int *groups, int *slots);
 // Matrix stages of a pass that run on the tensor cores (Plan::mma), and the shared memory
 // of their B buffers.
 int pass_matrix_stages(const svp::Plan &P, int pass);
+int pass_streams(const svp::Plan &P, int pass);
 size_t pass_mma_smem(const svp::Plan &P, int pass);
 // Whether pass `pass` of P runs on the pipelined kernel (layout-1 plan, at least one stage).
 bool pass_is_pipelined(const svp::Plan &P, int pass);

@@ -136,6 +136,11 @@ __device__ __forceinline__ float row_norm2(const float2 (&R)[N], const float2 (&
   return (s.x + s.y) + (t.x + t.y);
 }
 
+__device__ __forceinline__ void tmem_st8(uint32_t taddr, const uint32_t (&r)[8]) {
+  asm volatile("tcgen05.st.sync.aligned.32x32b.x8.b32 [%0], {%1,%2,%3,%4,%5,%6,%7,%8};" ::"r"(taddr), "r"(r[0]),
+               "r"(r[1]), "r"(r[2]), "r"(r[3]), "r"(r[4]), "r"(r[5]), "r"(r[6]), "r"(r[7])
+               : "memory");
+}
 __device__ __forceinline__ void tmem_st16(uint32_t taddr, const uint32_t (&r)[16]) {
   asm volatile(
       "tcgen05.st.sync.aligned.32x32b.x16.b32 [%0], {%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,%16};" ::"r"(
@@ -159,18 +164,20 @@ __device__ __forceinline__ uint32_t store_a(const float2 (&R)[N], const float2 (
     h = h < -100 ? -100 : (h > 100 ? 100 : h);
     const float sc = __uint_as_float((uint32_t)(127 + kRowExp - h) << 23);
     const float2 sc2 = make_float2(sc, sc);
+    // eight columns (pairs) at a time: few registers live besides the row
 #pragma unroll
-    for (int part = 0; part < 2; ++part) {
-      uint32_t hi[16], lo[16];
+    for (int c = 0; c < 4; ++c) {
+      uint32_t hi[8], lo[8];
 #pragma unroll
-      for (int p = 0; p < N; ++p) {
-        const float2 x = mul2(part ? I[p] : R[p], sc2);
-        hi[p] = f16x2(x.x, x.y);
-        const float2 d = sub2(x, f16x2_f32(hi[p]));
-        lo[p] = f16x2(d.x, d.y);
+      for (int e = 0; e < 8; ++e) {
+        const int p = 8 * (c & 1) + e;
+        const float2 x = mul2(c >> 1 ? I[p] : R[p], sc2);
+        hi[e] = f16x2(x.x, x.y);
+        const float2 d = sub2(x, f16x2_f32(hi[e]));
+        lo[e] = f16x2(d.x, d.y);
       }
-      tmem_st16(ta_hi + 16 * part, hi);
-      tmem_st16(ta_lo + 16 * part, lo);
+      tmem_st8(ta_hi + 8 * c, hi);
+      tmem_st8(ta_lo + 8 * c, lo);
     }
     return (uint32_t)(127 - kRowExp - kBExp + h);
   } else {

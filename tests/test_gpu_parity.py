@@ -635,10 +635,10 @@ def test_repeated_circuit_reuses_its_plan(kw):
 
 
 def test_autotuned_plain_path_caches_its_choice_and_matches_the_oracle(tmp_path, monkeypatch):
-    """sv_options.autotune = 1 on a fresh state: the tile size and each pass's compute
-    groups are picked by timing and kept in the JSON cache; the tuned run matches the
-    oracle, and a second handle takes the cached choice (same plan, bitwise the same
-    state)."""
+    """sv_options.autotune = 1 on a fresh state: the tile size, the fusion width (qubits
+    per stage) and each pass's compute groups are picked by timing and kept in the JSON
+    cache; the tuned run matches the oracle, and a second handle takes the cached choice
+    (same plan, bitwise the same state)."""
     import json
     cache = tmp_path / 'autotune.json'
     monkeypatch.setenv('SV_AUTOTUNE_CACHE', str(cache))
@@ -652,7 +652,9 @@ def test_autotuned_plain_path_caches_its_choice_and_matches_the_oracle(tmp_path,
     keys = [k for k in entries if '|circuit|%d|' % n in k]
     m = [entries[k] for k in keys if k.endswith('|m')]
     passes = [entries[k] for k in keys if k.endswith('|passes')]
+    k = [entries[k] for k in keys if k.endswith('|k')]
     assert m and m[0] in (12, 13)
+    assert k and (m[0], k[0]) in ((12, 5), (13, 5), (12, 6))
     assert passes and all(k.rsplit('|', 1)[0] + '|p%d' % i in entries for k in keys if k.endswith('|passes')
                           for i in range(passes[0]))
     psi2, _, _ = run_gpu(lat, jit=1, autotune=1)
