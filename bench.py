@@ -347,26 +347,53 @@ def branch_workload(steps, warmup, paths=('plain', 'tf32x3', 'plain_full_decompo
 def tensor_workload(steps, warmup):
     """The full 28-qubit state (4x7 lattice, depth 10) from the cut decomposition in tensor
     form: two batched half-states (14 + t qubits) and the branch sum of their outer
-    products, a complex (2^14 x 2^t) x (2^t x 2^14) product written as 2^28 amplitudes."""
+    products, a complex (2^14 x 2^t) x (2^t x 2^14) product written as 2^28 amplitudes --
+    on the CUDA cores (plain) and on the tensor cores (TF32x3 tcgen05 GEMM), for the
+    default decomposition and the full one (every crossing CZ summed: 2^7 branches)."""
+    import numpy as np
     import torch
     from paper_1804_04797_gb300 import inputs, sv
     lat = inputs.C28
-    h = sv.sv_create(lat.n_qubits)
+    n = lat.n_qubits
+    hbm_peak, bf16_peak, _ = _peaks()
+    out = {}
+    h = sv.sv_create(n)
     try:
-        for _ in range(max(1, warmup)):
-            sv.sv_branch_full_state(lat, inputs.C28_HALF_A, h)
-        torch.cuda.synchronize()
-        t0 = time.perf_counter()
-        for _ in range(steps):
-            sv.sv_branch_full_state(lat, inputs.C28_HALF_A, h)
-        torch.cuda.synchronize()
-        dt = (time.perf_counter() - t0) / steps
-        norm2, _ = sv.sv_norm(h)
+        for full in (False, True):
+            counts = sv.sv_branch_counts(lat, inputs.C28_HALF_A, full_decomposition=full)
+            tf = counts[4]
+            for name, opts in (('cuda_cores', None), ('tensor_cores', sv.options(precision=sv.SV_PREC_TF32X3))):
+                for _ in range(max(1, warmup)):
+                    sv.sv_branch_full_state(lat, inputs.C28_HALF_A, h, opts, full_decomposition=full)
+                torch.cuda.synchronize()
+                sv.sv_set_profiling(h, True)
+                t0 = time.perf_counter()
+                for _ in range(steps):
+                    sv.sv_branch_full_state(lat, inputs.C28_HALF_A, h, opts, full_decomposition=full)
+                torch.cuda.synchronize()
+                dt = (time.perf_counter() - t0) / steps
+                ms, _ = sv.sv_get_launch_times(h)
+                sv.sv_set_profiling(h, False)
+                norm2, _ = sv.sv_norm(h)
+                prod_ms = float(np.mean(ms)) if len(ms) else float('nan')
+                r = {'s_per_state': dt, 'product_ms': prod_ms, 'norm_err': norm2 - 1.0, 'summed_branch_bits': tf,
+                     'product_hbm_gbs': 8.0 * 2 ** n / (prod_ms * 1e-3) / 1e9,
+                     'product_hbm_frac': 8.0 * 2 ** n / (prod_ms * 1e-3) / 1e9 / hbm_peak}
+                if name == 'tensor_cores':
+                    kpad = max(32, -(-2 * 2 ** tf // 32) * 32)
+                    na = nb = n // 2
+                    tflops = 3 * 2 * 2 ** nb * 2 * 2 ** na * kpad / (prod_ms * 1e-3) / 1e12
+                    r['tensor'] = {'achieved': tflops, 'unit': 'TFLOP/s', 'peak': bf16_peak * TENSOR_RATIO['tf32x3'],
+                                   'frac': tflops / (bf16_peak * TENSOR_RATIO['tf32x3']),
+                                   'note': 'executed TF32x3 products (3 x 2 M N K, K padded to %d)' % kpad}
+                out[('full_' if full else '') + name] = r
     finally:
         sv.sv_destroy(h)
+    best = out['cuda_cores']['s_per_state']
     return {'metric': '28q full state by the tensor form of the cut decomposition, s per state',
-            'value': dt, 'unit': 's/state', 'norm_err': abs(norm2 - 1),
-            'config': {'workload': '4x7 lattice, depth 10, cut rows 1|2',
+            'value': best, 'unit': 's/state', 'paths': out,
+            'config': {'workload': '4x7 lattice, depth 10, cut rows 1|2 (default decomposition: 2^4 summed '
+                                   'branches; full: 2^7)',
                        'counts': sv.sv_branch_counts(lat, inputs.C28_HALF_A)}}
 
 

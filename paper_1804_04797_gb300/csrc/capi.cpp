@@ -211,6 +211,15 @@ void prof_end(sv_state *s, double bytes) {
   s->ev_used += 2;
 }
 
+}  // namespace
+
+namespace svc {
+void profile_begin(sv_state *s) { prof_begin(s); }
+void profile_end(sv_state *s, double bytes) { prof_end(s, bytes); }
+}  // namespace svc
+
+namespace {
+
 // one full sweep per gate (precision SV_PREC_PERGATE and tiny states)
 sv_status apply_pergate(sv_state *s, const std::vector<svp::Gate> &g) {
   size_t start = 0;

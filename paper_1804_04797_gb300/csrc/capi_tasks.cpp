@@ -395,10 +395,38 @@ extern "C" sv_status sv_branch_full_state(const sv_lattice *lat, const sv_cut *c
   if (e == cudaSuccess) e = cudaStreamSynchronize(B.s->stream);
   // each branch slice carries 2^{-t/2} per half
   const float scale = std::ldexp(1.0f, C.tf);
-  if (e == cudaSuccess)
+  // the tensor-core precisions: the product on tcgen05 (TF32x3), else on the CUDA cores
+  const bool tc = (o.precision == SV_PREC_TF32X3 || o.precision == SV_PREC_F16X3) &&
+                  svk::fused_supported() && svk::outer_sum_tc_supported(C.na, C.nb, C.tf);
+  void *scratch = nullptr;
+  int *d_err = nullptr;
+  if (e == cudaSuccess && tc) {
+    e = cudaMalloc(&scratch, svk::outer_sum_tc_scratch(C.na, C.nb, C.tf) + 256);
+    if (e == cudaSuccess) {
+      d_err = reinterpret_cast<int *>(static_cast<char *>(scratch) + svk::outer_sum_tc_scratch(C.na, C.nb, C.tf));
+      e = cudaMemsetAsync(d_err, 0, sizeof(int), out->stream);
+    } else {
+      scratch = nullptr;
+    }
+    if (e == cudaSuccess) {
+      profile_begin(out);
+      e = svk::launch_outer_sum_tc(A.s->psi, C.na, B.s->psi, C.nb, C.tf, scale, out->psi, scratch, d_err, out->stream);
+      profile_end(out, std::ldexp(8.0, C.n));
+    }
+  } else if (e == cudaSuccess) {
+    profile_begin(out);
     e = svk::launch_outer_sum(A.s->psi, C.na, B.s->psi, C.nb, C.tf, scale, out->psi, out->stream);
+    profile_end(out, std::ldexp(8.0, C.n));
+  }
+  int h_err = 0;
+  if (d_err && e == cudaSuccess) {
+    e = cudaMemcpyAsync(&h_err, d_err, sizeof(int), cudaMemcpyDeviceToHost, out->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(out->stream);
+  }
+  if (scratch) cudaFree(scratch);
   out->sums_valid = false;
   if (e != cudaSuccess) { out->broken = true; return cuda_fail(e, "sv_branch_full_state"); }
+  if (h_err) { out->broken = true; return fail(SV_ERR_TIMEOUT, "sv_branch_full_state: a tensor-core wait gave up"); }
   out->fresh = false;
   if (out->prof) out->other_launches += 1;
   // the crossing CZs taken as output signs act on the product state like any CZ

@@ -68,6 +68,13 @@ cudaError_t launch_fork(float2 *psi, int n_cur, int n_new, cudaStream_t st);
 
 // Full state from two batched half-states (Eqs. 6-7): out[x_A + (x_B << nA)] = scale *
 // sum_l A[x_A + (l << nA)] B[x_B + (l << nB)] over 2^t branches (fp32).
+// The same product on the tensor cores (TF32x3, k_outer_tc.cu): half states of >= 7
+// qubits; scratch: outer_sum_tc_scratch bytes of device memory for the operand images;
+// err: a device int set non-zero if a bounded wait gave up.
+bool outer_sum_tc_supported(int nA, int nB, int t);
+size_t outer_sum_tc_scratch(int nA, int nB, int t);
+cudaError_t launch_outer_sum_tc(const float2 *A, int nA, const float2 *B, int nB, int t, float scale, float2 *out,
+                                void *scratch, int *err, cudaStream_t st);
 cudaError_t launch_outer_sum(const float2 *A, int nA, const float2 *B, int nB, int t, float scale, float2 *out,
                              cudaStream_t st);
 

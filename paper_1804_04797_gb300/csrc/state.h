@@ -106,6 +106,11 @@ void write_autotune_cache(const std::map<std::string, int> &c);
 sv_status take_pending_error(sv_state *s);
 // Fused path: the stage unitaries as split-TF32 operands (see k_fused.cu).
 sv_status build_stage_mats(svp::Plan *P, const std::vector<svp::Gate> &g, int r, bool f16);
+// A launch timed by CUDA events on the handle's stream when profiling is on (its entry of
+// sv_get_launch_times carries `bytes`).
+void profile_begin(sv_state *s);
+void profile_end(sv_state *s, double bytes);
+
 // B operands of a fused packed plan's matrix stages (the pipelined plan kernels).
 sv_status build_stage_mats_packed(svp::Plan *P, const std::vector<svp::Gate> &g, bool f16);
 

@@ -531,8 +531,17 @@ def test_inner_product_and_basis_state():
         sv.sv_destroy(h4)
 
 
+# the tensor-form product on the CUDA cores (plain) and on the tensor cores (TF32x3).  The
+# tensor-core accumulation truncates toward zero; the product has no unitary structure
+# whose norm could be restored per tile, so its norm keeps that drift (~1e-6 at 28
+# qubits): rel-L2 and fidelity are its criteria, the norm is bounded loosely.
+PRODUCT = {'cuda_cores': None, 'tensor_cores': sv.options(precision=TC)}
+PRODUCT_NORM_TOL = {'cuda_cores': NORM_TOL, 'tensor_cores': 1e-5}
+
+
 @pytest.mark.parametrize('full', [False, True])
-def test_branch_full_state_matches_oracle(full):
+@pytest.mark.parametrize('product', list(PRODUCT))
+def test_branch_full_state_matches_oracle(full, product):
     """Eqs. 6-7: the full state as the sum over branches of A_l (x) B_l."""
     lat = inputs.lattice_for(4, 4, 9, seed=31)
     half_a = (1 << 8) - 1
@@ -540,18 +549,19 @@ def test_branch_full_state_matches_oracle(full):
     want = csim.run(n, gates)
     h = sv.sv_create(n)
     try:
-        sv.sv_branch_full_state(lat, half_a, h, full_decomposition=full)
+        sv.sv_branch_full_state(lat, half_a, h, PRODUCT[product], full_decomposition=full)
         got = sv.sv_copy_state(h, n)
         n2, _ = sv.sv_norm(h)
     finally:
         sv.sv_destroy(h)
     assert rel_l2(got, want) <= REL_L2
-    assert abs(n2 - 1) <= NORM_TOL
+    assert abs(n2 - 1) <= PRODUCT_NORM_TOL[product]
 
 
+@pytest.mark.parametrize('product', list(PRODUCT))
 @pytest.mark.parametrize('depth', [3, 6])
 @pytest.mark.parametrize('full', [False, True])
-def test_branch_full_state_with_part_c_matches_oracle(full, depth):
+def test_branch_full_state_with_part_c_matches_oracle(full, depth, product):
     """Eq. 3: layers 0..depth through the tensor form of the cut decomposition (parts A
     and B), the remaining layers (part C) on the reconstructed state."""
     lat = inputs.lattice_for(4, 4, 11, seed=37)
@@ -560,39 +570,43 @@ def test_branch_full_state_with_part_c_matches_oracle(full, depth):
     want = csim.run(n, gates)
     h = sv.sv_create(n)
     try:
-        sv.sv_branch_full_state(lat, half_a, h, full_decomposition=full, depth=depth)
+        sv.sv_branch_full_state(lat, half_a, h, PRODUCT[product], full_decomposition=full, depth=depth)
         got = sv.sv_copy_state(h, n)
         n2, _ = sv.sv_norm(h)
     finally:
         sv.sv_destroy(h)
     assert rel_l2(got, want) <= REL_L2
-    assert abs(n2 - 1) <= NORM_TOL
+    assert abs(n2 - 1) <= PRODUCT_NORM_TOL[product]
 
 
-def test_branch_full_state_28q_with_part_c_equals_direct_run():
-    """The 28-qubit check lattice cut after layer 5: parts A and B by the decomposition,
-    part C (layers 6..10) on the full 2^28 state, against the direct run."""
+@pytest.mark.parametrize('full', [False, True])
+@pytest.mark.parametrize('product', list(PRODUCT))
+def test_branch_full_state_28q_with_part_c_equals_direct_run(product, full):
+    """The 28-qubit check lattice cut after layer 5: parts A and B by the decomposition
+    (the default one, and the full one: 2^7 summed branches), part C (layers 6..10) on
+    the full 2^28 state, against the direct run."""
     lat = inputs.C28
     n = lat.n_qubits
     a, b = sv.sv_create(n), sv.sv_create(n)
     try:
-        sv.sv_branch_full_state(lat, inputs.C28_HALF_A, a, depth=5)
+        sv.sv_branch_full_state(lat, inputs.C28_HALF_A, a, PRODUCT[product], full_decomposition=full, depth=5)
         sv.sv_apply_circuit(b, sv.sv_generate_circuit(lat))
         ip = sv.sv_inner_product(b, a)
         n2a, _ = sv.sv_norm(a)
     finally:
         sv.sv_destroy(a)
         sv.sv_destroy(b)
-    assert abs(n2a - 1) <= NORM_TOL
+    assert abs(n2a - 1) <= PRODUCT_NORM_TOL[product]
     assert 1 - abs(ip) ** 2 / n2a <= 1e-9
 
 
-def test_branch_full_state_28q_equals_direct_run():
+@pytest.mark.parametrize('product', list(PRODUCT))
+def test_branch_full_state_28q_equals_direct_run(product):
     lat = inputs.C28
     n = lat.n_qubits
     a, b = sv.sv_create(n), sv.sv_create(n)
     try:
-        sv.sv_branch_full_state(lat, inputs.C28_HALF_A, a)
+        sv.sv_branch_full_state(lat, inputs.C28_HALF_A, a, PRODUCT[product])
         sv.sv_apply_circuit(b, sv.sv_generate_circuit(lat))
         ip = sv.sv_inner_product(b, a)
         n2a, _ = sv.sv_norm(a)
@@ -601,7 +615,7 @@ def test_branch_full_state_28q_equals_direct_run():
     finally:
         sv.sv_destroy(a)
         sv.sv_destroy(b)
-    assert abs(n2a - 1) <= NORM_TOL
+    assert abs(n2a - 1) <= PRODUCT_NORM_TOL[product]
     assert 1 - abs(ip) ** 2 / n2a <= 1e-9        # 1 - fidelity against the direct state
     h = sv.sv_create(n)
     try:
