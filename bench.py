@@ -656,7 +656,9 @@ def main():
     value = whole_job_s_per_circuit(best['s_per_circuit'], world)
     kname = {'plain': 'sv_pass (pipelined)' if args.pipeline >= 0 else 'sv_pass', 'plain_previous': 'sv_pass',
              'plain_interp': 'tile_pass_kernel', 'pergate': 'gate1q_kernel/diag_kernel'}
-    kernel = kname.get(best_name, 'fused_pass_kernel')
+    # the tensor-core paths: matrix stages of the pipelined plan kernels, or the tile kernel
+    kernel = kname.get(best_name, 'fused_pass_kernel' if best_name.endswith(('_tile', '_k4'))
+                       else 'sv_pass (matrix stages)')
     ratio = TRAFFIC_PER_ALGORITHMIC_BYTE.get(kernel)
     flops = algorithmic_flops_per_amplitude(gates) * 2.0 ** n
     sm_mhz = (best['clocks'] or {}).get('sm_max_mhz') or 2070.0
