@@ -273,8 +273,11 @@ def batch_workload(steps, warmup, variants=('default',)):
         torch.cuda.synchronize()
         dt = (time.perf_counter() - t0) / steps
         stats = sv.sv_apply_batch(lats, opts)
+        tile_bits, on_plan_kernels, persistent = sv.sv_batch_config()
         sv.sv_batch_free()
-        return dt, float(np.max(np.abs(stats[:, 0] - 1.0)))
+        tuned = {'tile_bits': tile_bits, 'circuits_on_plan_kernels': on_plan_kernels,
+                 'circuits_in_persistent_launch': persistent}
+        return dt, float(np.max(np.abs(stats[:, 0] - 1.0))), tuned
 
     def sequential(lats, jit):
         hs = [sv.sv_create(l.n_qubits, sv.options(jit=jit)) for l in lats]
@@ -294,10 +297,10 @@ def batch_workload(steps, warmup, variants=('default',)):
         return dt
 
     def compare(lats, jit):
-        g, err = graph(lats, jit)
+        g, err, tuned = graph(lats, jit)
         q = sequential(lats, jit)
         return {'graph_s_per_batch': g, 'circuits_per_s': len(lats) / g, 'sequential_s_per_batch': q,
-                'speedup_vs_sequential': q / g, 'max_norm_err': err}
+                'speedup_vs_sequential': q / g, 'max_norm_err': err, 'tuned_configuration': tuned}
 
     lats = inputs.batch(512)
     out = {'metric': 'uneven batch circuits/s (graph-captured batch vs one-at-a-time)', 'unit': 'circuits/s',

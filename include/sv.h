@@ -287,6 +287,12 @@ sv_status sv_batch_amplitudes(size_t circuit, const uint64_t *bits, size_t m, do
 /* Release the device memory and graph kept for the last batch. */
 sv_status sv_batch_free(void);
 
+/* The configuration the last batch ran with (host ints, any may be NULL): tile_bits =
+ * the tile size of its persistent launch (the autotuner's choice when it was asked for),
+ * plan_kernel_circuits = the circuits run on plan-specialised kernels, persistent_circuits
+ * = the circuits in the persistent launch.  SV_ERR_STATE if no batch has run. */
+sv_status sv_batch_config(int *tile_bits, int *plan_kernel_circuits, int *persistent_circuits);
+
 /* Failure-detection self-test, with no GPU fault: runs the batch kernel on a queue whose
  * single item waits for a pass that is never queued, with a wait limit of limit_ms
  * (1..10000).  Returns SV_ERR_TIMEOUT when the kernel gave up and reported it as designed

@@ -604,6 +604,16 @@ extern "C" sv_status sv_selftest_wait_timeout(int limit_ms) {
   return SV_OK;
 }
 
+extern "C" sv_status sv_batch_config(int *tile_bits, int *plan_kernel_circuits, int *persistent_circuits) {
+  clear_error();
+  std::lock_guard<std::mutex> lock(g_mu);
+  if (!g_batch) return fail(SV_ERR_STATE, "sv_batch_config: no batch has run");
+  if (tile_bits) *tile_bits = g_batch->m;
+  if (plan_kernel_circuits) *plan_kernel_circuits = (int)g_batch->jit.size();
+  if (persistent_circuits) *persistent_circuits = g_batch->count - (int)g_batch->jit.size();
+  return SV_OK;
+}
+
 extern "C" sv_status sv_batch_free(void) {
   clear_error();
   std::lock_guard<std::mutex> lock(g_mu);

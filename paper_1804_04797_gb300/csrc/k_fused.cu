@@ -153,7 +153,8 @@ sv_status build_stage_mats_packed(svp::Plan *P, const std::vector<svp::Gate> &g,
   constexpr int d = 32, kK = 64;
   const int part_bytes = kK * kK * (f16 ? 2 : 4);
   const size_t stage_floats = (size_t)2 * part_bytes / 4;
-  const double bscale = f16 ? std::ldexp(1.0, svk::kF16BExp) : 1.0;
+  // (unscaled: the matrix-stage kernel keeps each tile at one scale through its stages)
+  const double bscale = 1.0;
   for (size_t s = 0; s < P->stages.size(); ++s) {
     svp::DevStage &ds = P->stages[s];
     ds.unitary = 1;

@@ -12,8 +12,8 @@
 // (tcgen05.st), the kernel's MMA warp issues the products from TMEM (A) and shared memory
 // (B) and commits them to the group's mbarrier, and the thread reads its row of D back
 // (tcgen05.ld).  Split precision, three products accumulated in fp32 in tensor memory:
-//   F16x3   A = hi + lo in fp16 after scaling the row by a power of two (its norm near
-//           2^7: exact, undone after the product), B likewise split and scaled by 2^8;
+//   F16x3   A = hi + lo in fp16, the tile scaled once by a power of two (tile_scale:
+//           exact, undone after its last stage), B likewise split (unscaled);
 //           lo*hi + hi*lo + hi*hi (the lo*lo term is ~2^-22 relative).  K = 16 per MMA.
 //   TF32x3  hi = x rounded to the nearest TF32, lo = (x - hi) rounded likewise.  K = 8.
 #pragma once
@@ -51,8 +51,6 @@ struct MFmt<false> {
   static constexpr uint32_t kIdesc = (1u << 4) | (2u << 7) | (2u << 10) | (8u << 17) | (8u << 24);
 };
 
-constexpr int kRowExp = 7;  // a row's norm is scaled into [2^7, 2^8) (F16)
-constexpr int kBExp = 8;    // B is scaled by 2^8 (F16)
 
 // Shared-memory matrix descriptor of a K-major operand without swizzle: 8-row x 16-byte
 // core matrices, K-adjacent ones 128 B apart (leading byte offset), row groups sbo apart.
@@ -150,19 +148,31 @@ __device__ __forceinline__ void tmem_st16(uint32_t taddr, const uint32_t (&r)[16
       : "memory");
 }
 
+// The scale of a tile's amplitudes for the F16x3 products, from its norm^2 (the four warp
+// sums as hi + lo pairs): the power of two that brings the tile's norm into [2^13, 2^14),
+// so that no amplitude exceeds 2^14 (fp16 holds up to 65504) while the typical one, 1/64
+// of the norm, sits near 2^7, its lo part far above fp16's subnormal range.  A unitary
+// stage keeps every row's norm, so the scale holds for all the tile's stages: the tile is
+// scaled once before its first product and unscaled once after its last stage.
+__device__ __forceinline__ float tile_scale(const float2 (&s)[4]) {
+  const float n2 = (s[0].x + s[1].x) + (s[2].x + s[3].x);
+  int h = ((int)((__float_as_uint(n2) >> 23) & 0xFF) - 127) >> 1;  // n2 in [2^E, 2^(E+1)), h = floor(E/2)
+  h = h < -100 ? -100 : (h > 100 ? 100 : h);
+  return __uint_as_float((uint32_t)(127 + 13 - h) << 23);
+}
+
+// 1 / x for a power of two x (exact).
+__device__ __forceinline__ float inv_pow2(float x) { return __uint_as_float((254u << 23) - __float_as_uint(x)); }
+
 // The row of A into this thread's TMEM lane (hi at ta_hi, lo at ta_lo; the re pairs in
-// the first half of each part's columns, the im pairs in the second).  F16: returns the
-// biased exponent of the power of two that undoes the row's scale and B's 2^8 together.
-template <bool F16, int N>
-__device__ __forceinline__ uint32_t store_a(const float2 (&R)[N], const float2 (&I)[N], float n2, uint32_t ta_hi,
-                                            uint32_t ta_lo) {
+// the first half of each part's columns, the im pairs in the second).  F16 with SCALE: the
+// row is multiplied by the tile's scale `sc` first (its first product; the later ones find
+// it at that scale already).
+template <bool F16, bool SCALE, int N>
+__device__ __forceinline__ void store_a(const float2 (&R)[N], const float2 (&I)[N], float sc, uint32_t ta_hi,
+                                        uint32_t ta_lo) {
   static_assert(N == 16, "rows of 32 amplitudes");
   if (F16) {
-    // n2 in [2^E, 2^(E+1)): the norm is below 2^(h+1), h = floor(E / 2); scale by
-    // 2^(kRowExp - h) (every component then below 2^(kRowExp + 1))
-    int h = ((int)((__float_as_uint(n2) >> 23) & 0xFF) - 127) >> 1;
-    h = h < -100 ? -100 : (h > 100 ? 100 : h);
-    const float sc = __uint_as_float((uint32_t)(127 + kRowExp - h) << 23);
     const float2 sc2 = make_float2(sc, sc);
     // eight columns (pairs) at a time: few registers live besides the row
 #pragma unroll
@@ -171,7 +181,7 @@ __device__ __forceinline__ uint32_t store_a(const float2 (&R)[N], const float2 (
 #pragma unroll
       for (int e = 0; e < 8; ++e) {
         const int p = 8 * (c & 1) + e;
-        const float2 x = mul2(c >> 1 ? I[p] : R[p], sc2);
+        const float2 x = SCALE ? mul2(c >> 1 ? I[p] : R[p], sc2) : (c >> 1 ? I[p] : R[p]);
         hi[e] = f16x2(x.x, x.y);
         const float2 d = sub2(x, f16x2_f32(hi[e]));
         lo[e] = f16x2(d.x, d.y);
@@ -179,8 +189,8 @@ __device__ __forceinline__ uint32_t store_a(const float2 (&R)[N], const float2 (
       tmem_st8(ta_hi + 8 * c, hi);
       tmem_st8(ta_lo + 8 * c, lo);
     }
-    return (uint32_t)(127 - kRowExp - kBExp + h);
   } else {
+    (void)sc;
 #pragma unroll
     for (int part = 0; part < 2; ++part) {
       uint32_t hi[32], lo[32];
@@ -197,26 +207,25 @@ __device__ __forceinline__ uint32_t store_a(const float2 (&R)[N], const float2 (
       tmem_st32(ta_hi + 32 * part, hi);
       tmem_st32(ta_lo + 32 * part, lo);
     }
-    return 127u;
   }
 }
 
-// The first half of a matrix stage: this thread's row as A into its TMEM lane, then the
-// MMA warp is told (a_full).  Returns the F16 unscale exponent for matrix_post.
-template <bool F16, int N>
-__device__ __forceinline__ uint32_t matrix_pre(const float2 (&R)[N], const float2 (&I)[N], float n2, uint32_t ta_hi,
-                                               uint32_t ta_lo, unsigned long long *a_full) {
-  const uint32_t ue = store_a<F16, N>(R, I, n2, ta_hi, ta_lo);
+// The first half of a matrix stage: this thread's row as A into its TMEM lane (times sc,
+// F16), then the MMA warp is told (a_full).
+template <bool F16, bool SCALE, int N>
+__device__ __forceinline__ void matrix_pre(const float2 (&R)[N], const float2 (&I)[N], float sc, uint32_t ta_hi,
+                                           uint32_t ta_lo, unsigned long long *a_full) {
+  store_a<F16, SCALE, N>(R, I, sc, ta_hi, ta_lo);
   asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
   fence_before();
   mbar_arrive(a_full);
-  return ue;
 }
 
 // The second half: wait for the products (d_full, phase `parity`, bounded), D back into
-// R/I.  Returns false if the wait gave up (R/I then hold whatever tensor memory held).
+// R/I (at the tile's scale: the stage unitary keeps it).  Returns false if the wait gave
+// up (R/I then hold whatever tensor memory held).
 template <bool F16, int N>
-__device__ __forceinline__ bool matrix_post(float2 (&R)[N], float2 (&I)[N], uint32_t ue, uint32_t td,
+__device__ __forceinline__ bool matrix_post(float2 (&R)[N], float2 (&I)[N], uint32_t td,
                                             unsigned long long *d_full, uint32_t parity) {
   const bool ok = mbar_wait(d_full, parity, kWaitNs);
   fence_after();
@@ -225,20 +234,10 @@ __device__ __forceinline__ bool matrix_post(float2 (&R)[N], float2 (&I)[N], uint
   tmem_ld32(td + 32, im);
   asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
   fence_before();
-  if (F16) {
-    const float un = __uint_as_float(ue << 23);
-    const float2 un2 = make_float2(un, un);
 #pragma unroll
-    for (int p = 0; p < N; ++p) {
-      R[p] = mul2(make_float2(__uint_as_float(re[2 * p]), __uint_as_float(re[2 * p + 1])), un2);
-      I[p] = mul2(make_float2(__uint_as_float(im[2 * p]), __uint_as_float(im[2 * p + 1])), un2);
-    }
-  } else {
-#pragma unroll
-    for (int p = 0; p < N; ++p) {
-      R[p] = make_float2(__uint_as_float(re[2 * p]), __uint_as_float(re[2 * p + 1]));
-      I[p] = make_float2(__uint_as_float(im[2 * p]), __uint_as_float(im[2 * p + 1]));
-    }
+  for (int p = 0; p < N; ++p) {
+    R[p] = make_float2(__uint_as_float(re[2 * p]), __uint_as_float(re[2 * p + 1]));
+    I[p] = make_float2(__uint_as_float(im[2 * p]), __uint_as_float(im[2 * p + 1]));
   }
   return ok;
 }

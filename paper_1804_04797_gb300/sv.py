@@ -92,6 +92,7 @@ def lib():
         'sv_apply_batch': ([vp, c_size_t, P(sv_options), vp], c_int),
         'sv_batch_amplitudes': ([c_size_t, vp, c_size_t, vp], c_int),
         'sv_batch_free': ([], c_int),
+        'sv_batch_config': ([P(c_int), P(c_int), P(c_int)], c_int),
         'sv_selftest_wait_timeout': ([c_int], c_int),
         'sv_norm_noalloc': ([vp, c_int, vp, P(c_double), P(c_double)], c_int),
         'sv_plan': ([c_int, vp, c_size_t, P(sv_options), c_int, P(sv_plan_summary), vp, vp, vp,
@@ -283,6 +284,14 @@ def sv_batch_amplitudes(circuit, bits):
 def sv_selftest_wait_timeout(limit_ms):
     """Raw status of the bounded-wait self-test (SV_ERR_TIMEOUT expected)."""
     return lib().sv_selftest_wait_timeout(int(limit_ms))
+
+
+def sv_batch_config():
+    """(tile_bits, circuits on plan-specialised kernels, circuits in the persistent launch)
+    of the last batch."""
+    v = [c_int(), c_int(), c_int()]
+    _check(lib().sv_batch_config(ctypes.byref(v[0]), ctypes.byref(v[1]), ctypes.byref(v[2])))
+    return tuple(x.value for x in v)
 
 
 def sv_batch_free():

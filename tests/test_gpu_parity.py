@@ -395,9 +395,21 @@ def test_batch_amplitudes_and_replay_match_oracle(tmp_path, monkeypatch):
     tuned = sv.sv_apply_batch(lats, sv.options(autotune=1))
     assert cache.exists() and '|batch|' in cache.read_text()
     np.testing.assert_allclose(tuned[:, 0], 1.0, atol=NORM_TOL)
+    # the configuration it ran with: the cached tile size, every circuit accounted for
+    import json
+    tile_bits, on_plan, persistent = sv.sv_batch_config()
+    assert tile_bits in [v for k, v in json.loads(cache.read_text()).items() if '|batch|' in k]
+    assert 11 <= tile_bits <= 13 and on_plan + persistent == len(lats)
+    for i in (0, 11):
+        n, gates = oracle_gates(lats[i])
+        want = csim.run(n, gates)
+        bits = inputs.bitstrings(n, 16, seed=5)
+        assert rel_l2(sv.sv_batch_amplitudes(i, bits), want[np.array(bits, dtype=np.int64)]) <= REL_L2
     sv.sv_batch_free()
     with pytest.raises(sv.SvError):
         sv.sv_batch_amplitudes(0, [0])
+    with pytest.raises(sv.SvError):
+        sv.sv_batch_config()
 
 
 @pytest.mark.parametrize('jit', [0, 1])
