@@ -607,6 +607,9 @@ def main():
                 'norm_err': norm2 - 1.0, 'n_sum_p2': (2.0 ** n) * sp2, 'rel_l2_vs_plain_64amps': agree,
                 'clocks': clocks, 'launches_per_step': (prof.launches + prof.other_launches) / steps,
                 'plan_kernel_launches': prof.jit_launches, 'per_pass_ms': per_pass,
+                # the plan it ran (the autotuner's tile size and fusion width for plain)
+                'plan': {'tile_bits': prof.plan_tile_bits, 'stage_qubits': prof.plan_stage_qubits,
+                         'passes': prof.plan_passes},
             }
 
         # end to end through the public API with host buffers: gate list in, amplitudes

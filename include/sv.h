@@ -331,6 +331,9 @@ typedef struct {
   int jit_launches;   /* tile passes run on plan-specialised (run-time compiled) kernels */
   int plain_fallbacks; /* applies with a tensor-core precision that ran the plain kernel */
                        /* (states below 12 qubits)                                    */
+  int plan_tile_bits;    /* the last tile-pass plan: qubits per tile (the autotuner's   */
+  int plan_stage_qubits; /* choice when it ran) and per stage (the fusion width); 0    */
+  int plan_passes;       /* when no plan ran; its passes                                */
 } sv_profile;
 
 /* The basis state |x> (1 at index x, 0 elsewhere).  SV_ERR_ARG if x has bits >= n. */

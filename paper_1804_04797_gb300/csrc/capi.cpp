@@ -1023,6 +1023,15 @@ sv_status sv_get_profile(sv_state *s, sv_profile *out) {
   out->other_launches = s->other_launches;
   out->jit_launches = s->jit_launches;
   out->plain_fallbacks = s->plain_fallbacks;
+  out->plan_tile_bits = 0;
+  out->plan_stage_qubits = 0;
+  out->plan_passes = 0;
+  if (s->plan_valid && !s->plan.passes.empty()) {
+    out->plan_tile_bits = s->plan.passes[0].m;
+    // a packed stage holds tile bit 0 besides its register slots
+    out->plan_stage_qubits = s->plan.rk + ((s->plan.passes[0].flags & svp::PF_PACKED) ? 1 : 0);
+    out->plan_passes = (int)s->plan.passes.size();
+  }
   for (size_t i = 0; i + 1 < s->ev_used; i += 2) {
     float ms = 0;
     if (cudaEventElapsedTime(&ms, s->events[i], s->events[i + 1]) == cudaSuccess) out->ms += ms;

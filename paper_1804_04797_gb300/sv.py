@@ -51,7 +51,8 @@ class sv_plan_summary(ctypes.Structure):
 class sv_profile(ctypes.Structure):
     _fields_ = [('launches', c_int), ('ms', c_double), ('hbm_bytes', c_double), ('h2d_bytes', c_double),
                 ('d2h_bytes', c_double), ('other_launches', c_int), ('jit_launches', c_int),
-                ('plain_fallbacks', c_int)]
+                ('plain_fallbacks', c_int), ('plan_tile_bits', c_int), ('plan_stage_qubits', c_int),
+                ('plan_passes', c_int)]
 
 
 _lib = None

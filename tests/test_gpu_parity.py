@@ -685,6 +685,15 @@ def test_autotuned_plain_path_caches_its_choice_and_matches_the_oracle(tmp_path,
                           for i in range(passes[0]))
     psi2, _, _ = run_gpu(lat, jit=1, autotune=1)
     assert np.array_equal(psi1.view(np.uint32), psi2.view(np.uint32))
+    # the profile reports the plan the handle ran: the cached tile size and width
+    h = sv.sv_create(n, sv.options(jit=1, autotune=1))
+    try:
+        sv.sv_set_profiling(h, True)
+        sv.sv_apply_circuit(h, sv.sv_generate_circuit(lat))
+        prof = sv.sv_get_profile(h)
+    finally:
+        sv.sv_destroy(h)
+    assert (prof.plan_tile_bits, prof.plan_stage_qubits) == (m[0], k[0]) and prof.plan_passes == passes[0]
 
 
 def test_state_on_a_torch_owned_buffer_matches_the_oracle():
