@@ -14,8 +14,8 @@
 // 32-wide K chunk), so a CTA fetches each with one bulk copy.  The GEMM kernel is
 // persistent (two CTAs per SM: one stores its tile while the other computes): per output
 // tile of 128 x 128 amplitudes it loads the blocks of every K chunk, one thread issues the
-// 3 x 4 MMAs (M = 128, N = 256, K = 8) per chunk, and every thread writes its row of D
-// (one contiguous 1 KB run of the state) from tensor memory to HBM.  All waits are bounded.
+// 3 x 4 MMAs (M = 128, N = 256, K = 8) per chunk, and the warps move D from tensor memory
+// through shared memory to HBM in whole 128-byte runs of the state.  All waits are bounded.
 #include <cuda_runtime.h>
 
 #include <cstdint>
@@ -193,10 +193,15 @@ outer_mma_kernel(const unsigned char *__restrict__ aimg, const unsigned char *__
       if (stop) break;
     }
     if (stop) break;
-    // every thread: its row of D (x_B = rt * 128 + tid) from TMEM to the state
+    // D to the state: each warp holds 32 rows (x_B = rt * 128 + 32 warp + lane, one per
+    // lane); per 32-column chunk the lanes write their rows into shared memory (the
+    // operand buffers are free now: 4 KB per warp, 16-byte chunk q of row r at q ^ (r & 7),
+    // conflict-free both ways), then the warp writes four rows' 128-byte runs per store
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-    float2 *row = out + (((rt * kRows + (uint64_t)tid) << nA) + ct * kCols);
     const uint32_t taddr = tmem + ((uint32_t)(32 * warp) << 16);
+    const int lane = tid & 31;
+    float4 *stg = reinterpret_cast<float4 *>(sa) + warp * 256;
+    float2 *rows = out + (((rt * kRows + (uint64_t)(32 * warp)) << nA) + ct * kCols);
 #pragma unroll 1
     for (int c = 0; c < 256; c += 32) {
       uint32_t r[32];
@@ -210,13 +215,23 @@ outer_mma_kernel(const unsigned char *__restrict__ aimg, const unsigned char *__
           : "r"(taddr + (uint32_t)c)
           : "memory");
       asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-      float4 *dst = reinterpret_cast<float4 *>(row + c / 2);
 #pragma unroll
       for (int q = 0; q < 8; ++q)
-        dst[q] = make_float4(__uint_as_float(r[4 * q]) * scale, __uint_as_float(r[4 * q + 1]) * scale,
-                             __uint_as_float(r[4 * q + 2]) * scale, __uint_as_float(r[4 * q + 3]) * scale);
+        stg[lane * 8 + (q ^ (lane & 7))] =
+            make_float4(__uint_as_float(r[4 * q]) * scale, __uint_as_float(r[4 * q + 1]) * scale,
+                        __uint_as_float(r[4 * q + 2]) * scale, __uint_as_float(r[4 * q + 3]) * scale);
+      __syncwarp();
+#pragma unroll
+      for (int q = 0; q < 8; ++q) {
+        const int row = 4 * q + (lane >> 3), ch = lane & 7;
+        const float4 v = stg[row * 8 + (ch ^ (row & 7))];
+        *reinterpret_cast<float4 *>(rows + ((uint64_t)row << nA) + c / 2 + 2 * ch) = v;
+      }
+      __syncwarp();
     }
-    // the next tile's products overwrite D only after every thread has read it
+    // the next tile's products overwrite D only after every thread has read it, and its
+    // bulk copies refill the staging buffer only after these generic-proxy writes
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
     __syncthreads();
   }

@@ -178,7 +178,10 @@ def _oracle_apply(n, gl, psi):
                                   (13, dict(jit=1)), (18, dict(jit=1)), (18, dict(jit=1, tile_bits=9, low_bits=3)),
                                   (16, dict(precision=sv.SV_PREC_PERGATE)), (12, dict(precision=TC)),
                                   (17, dict(precision=TC)), (19, dict(precision=TC, tile_bits=12)),
-                                  (17, dict(precision=H16)), (19, dict(precision=H16, tile_bits=12))])
+                                  (17, dict(precision=H16)), (19, dict(precision=H16, tile_bits=12)),
+                                  (12, dict(precision=H16)), (13, dict(precision=H16)),
+                                  (17, dict(precision=H16, pipeline=-1)), (17, dict(precision=TC, fuse_k=4)),
+                                  (17, dict(precision=H16, norm_restore=-1))])
 def test_all_gate_kinds_from_zero_and_loaded_state(n, kw):
     gl = _random_gate_list(n, 120, seed=n)
     # from |0..0> (no H layer: the first pass generates |0..0>)
