@@ -85,7 +85,10 @@ PLAN_CASES = [(inputs.lattice_for(3, 4, 14, seed=3), dict()),
               (inputs.lattice_for(4, 4, 12, seed=8), dict(tile_bits=7, low_bits=1, fuse_k=2)),
               (inputs.lattice_for(2, 7, 20, seed=1), dict(tile_bits=9, low_bits=3, fuse_k=4)),
               (inputs.lattice_for(4, 4, 12, seed=8), dict(tile_bits=8, low_bits=4, fuse_k=5,
-                                                          precision=sv.SV_PREC_TF32X3))]
+                                                          precision=sv.SV_PREC_TF32X3)),
+              # the fused packed plan of the matrix-stage kernels (12-qubit TMA tiles)
+              (inputs.lattice_for(4, 4, 12, seed=8), dict(precision=sv.SV_PREC_F16X3)),
+              (inputs.lattice_for(2, 7, 20, seed=1), dict(precision=sv.SV_PREC_TF32X3))]
 
 
 @pytest.mark.parametrize('lat,kw', PLAN_CASES)
@@ -113,6 +116,26 @@ def test_planner_pass_counts_headline_workload():
     assert len(g) == 478
     assert summ.passes <= 12
     assert summ.hbm_bytes == pytest.approx(8.0 * 2 ** 34 + 16.0 * 2 ** 34 * (summ.passes - 1))
+
+
+def test_fused_plans_of_the_headline_workload():
+    """The 34-qubit circuit's tensor-core plans: the same 8 passes as the plain plan (the
+    passes do not depend on the stage form), every stage a matrix stage, more stages than
+    the plain plan (a diagonal gate joining a register qubit to an outside one after a
+    non-diagonal gate on it ends the stage); the tile kernel's unpacked plan (five free
+    register qubits) needs fewer than the packed one."""
+    g = sv.sv_generate_circuit(inputs.C34)
+    plain, *_ = sv.sv_plan(34, g, sv.options(jit=1))
+    packed, *_ = sv.sv_plan(34, g, sv.options(precision=sv.SV_PREC_F16X3))
+    tile, *_ = sv.sv_plan(34, g, sv.options(precision=sv.SV_PREC_F16X3, pipeline=-1))
+    assert plain.passes == packed.passes == tile.passes == 8
+    assert packed.matrix_stages == packed.stages
+    assert plain.stages < tile.matrix_stages < packed.matrix_stages
+
+
+def test_batch_config_needs_a_batch():
+    with pytest.raises(sv.SvError):
+        sv.sv_batch_config()
 
 
 def test_planner_rejects_invalid_gates():
