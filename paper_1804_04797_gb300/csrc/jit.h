@@ -28,6 +28,17 @@ int register_slots();
 // CTAs per SM) measured faster than 13 (7 passes, two CTAs) and 14 (6 passes, one).
 constexpr int kTileBits = 12;
 
+// Pipelined kernels: each CTA takes runs of 2^kTileRunLog neighbouring tiles per turn of
+// the grid (tile_of in tile_pipe.cuh; tile_run_log() reads the SV_TILE_RUN override).
+// Measured on 34 qubits (plain path, fixed kernel shapes): a pass whose tile leaves out
+// qubit 4 reads 128-byte rows, and with one tile per turn (runs of 1) such passes ran at
+// 0.77-0.81 of the copy bandwidth (5.0-5.4 TB/s) against 0.97 with qubit 4 in the tile;
+// runs of 2 took the circuit from 0.419 s to 0.382 s, runs of 4 and 8 measured the same.
+// The tensor-core passes (latency-bound) keep runs of 1: with runs of 2 the F16x3 circuit
+// measured 0.918 s against 0.907 s.
+constexpr int kTileRunLog = 1;
+int tile_run_log();
+
 // Pipelined kernels (plans with Options::layout = 1, tile_pipe.cuh): compute groups and
 // shared-memory tile slots per CTA for a tile size; false where the tile size has none.
 // 12-qubit tiles: three groups of 128 threads with two 32 KB slots each (one CTA per SM;

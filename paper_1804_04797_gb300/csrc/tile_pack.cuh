@@ -180,20 +180,35 @@ struct GSYDG {  // x' = x + y, y' = y - x
 // adding up (always rounding one way shrank the 34-qubit norm by 1.3e-6), at two packed
 // operations per pair fewer than the correctly rounded hi + lo product.
 constexpr float kS2dn = 0.70710677f, kS2up = 0.70710683f;
+// u(): the same without the factor: (1 +- i) times (r, i), two additions.
 struct DT1 {  // times e^{i pi/4}
+  template <class T>
+  __device__ __forceinline__ static void u(T r, T i, T &ur, T &ui) {
+    using O = Ops<T>;
+    ur = O::sub(r, i);
+    ui = O::add(r, i);
+  }
   template <class T>
   __device__ __forceinline__ static void f(T &r, T &i, float c) {
     using O = Ops<T>;
-    const T a = O::sub(r, i), b = O::add(r, i);
+    T a, b;
+    u(r, i, a, b);
     r = O::scale(a, c);
     i = O::scale(b, c);
   }
 };
 struct DTDG1 {  // times e^{-i pi/4}
   template <class T>
+  __device__ __forceinline__ static void u(T r, T i, T &ur, T &ui) {
+    using O = Ops<T>;
+    ur = O::add(r, i);
+    ui = O::sub(i, r);
+  }
+  template <class T>
   __device__ __forceinline__ static void f(T &r, T &i, float c) {
     using O = Ops<T>;
-    const T a = O::add(r, i), b = O::sub(i, r);
+    T a, b;
+    u(r, i, a, b);
     r = O::scale(a, c);
     i = O::scale(b, c);
   }
@@ -265,6 +280,38 @@ template <class G>
 __device__ __forceinline__ void pairs_pack_signed(Regs &R, Regs &I, float s) {
 #pragma unroll
   for (int p = 0; p < kP; ++p) G::fs(R[p].x, I[p].x, R[p].y, I[p].y, s);
+}
+// Phase D (T or its adjoint) where register slot J is 1, then gate G on slot J, as one
+// step: G's fused form fs() takes the slot-1 element as (1 +- i) y (two additions) times
+// the scalar s = (sign) c, c the phase's rounding constant, so the factor 1/sqrt2 rides on
+// G's fused operations instead of two multiplications per element (6 packed operations a
+// pair instead of 8).  Exact in the sign; c enters each output through one fused product.
+template <class G, class D, int J>
+__device__ __forceinline__ void pairs_diag(Regs &R, Regs &I, float s) {
+  if constexpr (J < kPR) {
+#pragma unroll
+    for (int p = 0; p < kP; ++p)
+      if (!(p & (1 << J))) {
+        constexpr int b = 1 << J;
+        float2 ur, ui;
+        D::u(R[p | b], I[p | b], ur, ui);
+        G::fs(R[p], I[p], ur, ui, s);
+        R[p | b] = ur;
+        I[p | b] = ui;
+      }
+  }
+}
+// the same on the pack bit (inside every pair)
+template <class G, class D>
+__device__ __forceinline__ void pairs_pack_diag(Regs &R, Regs &I, float s) {
+#pragma unroll
+  for (int p = 0; p < kP; ++p) {
+    float ur, ui;
+    D::u(R[p].y, I[p].y, ur, ui);
+    G::fs(R[p].x, I[p].x, ur, ui, s);
+    R[p].y = ur;
+    I[p].y = ui;
+  }
 }
 // phase D (T or its adjoint, rounding constant c) where register slot J is 1
 template <class D, int J>

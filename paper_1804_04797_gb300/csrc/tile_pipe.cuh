@@ -111,6 +111,26 @@ __device__ __forceinline__ void bulk_wait_read_all() { asm volatile("cp.async.bu
 // Wait until every committed bulk group has completed (its writes are done).
 __device__ __forceinline__ void bulk_wait_all() { asm volatile("cp.async.bulk.wait_group 0;" ::: "memory"); }
 
+// The tile of a CTA's turn i.  The CTAs take runs of 2^B neighbouring tile ids per turn
+// of the grid (B = 0 when num_tiles is not a multiple of 2^B): turns i and i + 1 of a CTA
+// are tiles t and t + 1, which differ in the lowest qubit outside the tile.  When that
+// qubit is qubit 4, their 128-byte rows are the two halves of 256-byte blocks, read (and
+// written) by one SM a turn apart instead of by two SMs whose turns drift apart over the
+// sweep.  For a fixed CTA the runs' first tiles increase with i, and a run lies wholly
+// below num_tiles or wholly at or above it.
+template <int B>
+__device__ __forceinline__ unsigned long long tile_of(unsigned long long i, unsigned long long num_tiles) {
+  const int b = (num_tiles & ((1ull << B) - 1)) ? 0 : B;
+  return ((blockIdx.x + (i >> b) * gridDim.x) << b) | (i & ((1ull << b) - 1));
+}
+// The number of tiles tile_of<B> gives this CTA.
+template <int B>
+__device__ __forceinline__ unsigned long long tiles_of_cta(unsigned long long num_tiles) {
+  const int b = (num_tiles & ((1ull << B) - 1)) ? 0 : B;
+  const unsigned long long runs = num_tiles >> b;
+  return (blockIdx.x < runs ? (runs - blockIdx.x + gridDim.x - 1) / gridDim.x : 0ull) << b;
+}
+
 // Global index offset of group g's element 0 in a stage (the G half of the stage's
 // group-addressing entries).
 __device__ __forceinline__ uint64_t group_global(const DevPlanView &plan, uint32_t si, int g) {
