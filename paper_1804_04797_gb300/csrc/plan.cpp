@@ -195,6 +195,26 @@ bool build_plan(int n, const std::vector<Gate> &gates, const Options &opt, bool 
   std::vector<int> rem;
   for (size_t i = start; i < gates.size(); ++i) rem.push_back((int)i);
 
+  // Plans for the plain pipelined kernels: a T (or its adjoint) on a qubit of the tile
+  // waits for the next non-diagonal gate on its qubit (succ) and is placed in the same
+  // pass and stage, right before it in the stage's ops, where the kernel applies both as
+  // one step (its factor 1/sqrt2 rides on the gate's fused operations).  A phase commutes
+  // with every gate between the two (diagonal gates on its qubit, any gate on others).
+  // (34 qubits, fixed kernel shapes: 0.381 s -> 0.371 s, pass 0 64 -> 57 ms.  Deferring
+  // also the phases on qubits outside the tile, which the pass applies as a scalar phase
+  // of the tile, measured the same with a larger norm drift.)
+  const bool lazy = pack && !opt.fused && opt.layout == 1;
+  std::vector<int> succ(gates.size(), -1);
+  if (lazy) {
+    std::vector<int> next_nd(n, -1);
+    for (size_t i = gates.size(); i-- > start;) {
+      const Gate &x = gates[i];
+      if (x.kind == K_T || x.kind == K_TDG) succ[i] = next_nd[x.q0];
+      if (!kind_is_diag(x.kind)) next_nd[x.q0] = (int)i;
+    }
+  }
+  auto lazy_phase = [&](int gi) { return lazy && succ[(size_t)gi] >= 0; };
+
   const double amps = std::ldexp(1.0, n);
   bool first_pass = true;
   // packed plans: the square roots' scalars not yet applied -- an odd factor 2^{-1/2}
@@ -204,8 +224,26 @@ bool build_plan(int n, const std::vector<Gate> &gates, const Options &opt, bool 
     const uint64_t S = choose_tile(n, m, c, gates, rem);
     std::vector<char> applied;
     run_trial(gates, rem, S, &applied);
+    if (lazy) {
+      // a waiting phase on a tile qubit goes to the pass of its successor
+      std::vector<char> app(gates.size(), 0), keep = applied;
+      for (size_t i = 0; i < rem.size(); ++i) app[(size_t)rem[i]] = applied[i];
+      bool any = false;
+      for (size_t i = 0; i < rem.size(); ++i) {
+        const Gate &x = gates[rem[i]];
+        if (applied[i] && lazy_phase(rem[i]) && ((S >> x.q0) & 1ull) && !app[(size_t)succ[(size_t)rem[i]]])
+          applied[i] = 0;
+        any = any || applied[i];
+      }
+      if (!any) applied = keep;  // (never: the tile holds a pending non-diagonal gate)
+    }
     std::vector<int> now, later;
     for (size_t i = 0; i < rem.size(); ++i) (applied[i] ? now : later).push_back(rem[i]);
+    std::vector<int> pos_in_now;  // gate index -> position in `now` (-1: not in this pass)
+    if (lazy) {
+      pos_in_now.assign(gates.size(), -1);
+      for (size_t i = 0; i < now.size(); ++i) pos_in_now[(size_t)now[i]] = (int)i;
+    }
 
     DevPass dp;
     std::memset(&dp, 0, sizeof(dp));
@@ -265,6 +303,7 @@ bool build_plan(int n, const std::vector<Gate> &gates, const Options &opt, bool 
                          std::vector<int> *post) -> std::pair<int, int> {
       uint32_t closed = 0;
       int nd = 0, tot = 0;
+      std::vector<size_t> here;  // positions placed by this call
       bool progress = true;
       while (progress) {
         progress = false;
@@ -308,10 +347,23 @@ bool build_plan(int n, const std::vector<Gate> &gates, const Options &opt, bool 
             dn[i] = 1;
             ++tot;
             progress = true;
+            here.push_back(i);
           } else {
             pend_any |= qm;
             if (!diag) pend_nd |= qm;
           }
+        }
+      }
+      if (lazy) {
+        // a waiting phase stays in this stage only with its successor (nothing placed
+        // here depends on it otherwise: the successor is the next non-commuting gate)
+        for (size_t i : here) {
+          if (!lazy_phase(now[i])) continue;
+          const int ps = pos_in_now[(size_t)succ[(size_t)now[i]]];
+          if (ps < 0 || dn[(size_t)ps]) continue;  // successor in a later pass, or placed too
+          dn[i] = 0;
+          --tot;
+          if (inner) inner->erase(std::find(inner->begin(), inner->end(), now[i]));
         }
       }
       return {nd, tot};
@@ -415,6 +467,7 @@ bool build_plan(int n, const std::vector<Gate> &gates, const Options &opt, bool 
       }
       std::vector<int> inner, post;
       const std::pair<int, int> placed = run_stage(Rm, done, &inner, &post);
+      if (placed.second == 0) { *err = "planner: a stage placed no gate"; return false; }
       left -= (size_t)placed.second;
       const bool last_stage = left == 0;
       std::vector<int> R;

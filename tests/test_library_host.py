@@ -88,7 +88,12 @@ PLAN_CASES = [(inputs.lattice_for(3, 4, 14, seed=3), dict()),
                                                           precision=sv.SV_PREC_TF32X3)),
               # the fused packed plan of the matrix-stage kernels (12-qubit TMA tiles)
               (inputs.lattice_for(4, 4, 12, seed=8), dict(precision=sv.SV_PREC_F16X3)),
-              (inputs.lattice_for(2, 7, 20, seed=1), dict(precision=sv.SV_PREC_TF32X3))]
+              (inputs.lattice_for(2, 7, 20, seed=1), dict(precision=sv.SV_PREC_TF32X3)),
+              # the plain pipelined kernels' plans (TMA tile layout; a T waits for the next
+              # non-diagonal gate on its qubit)
+              (inputs.lattice_for(4, 4, 12, seed=8), dict(jit=1)),
+              (inputs.lattice_for(2, 7, 20, seed=1), dict(jit=1)),
+              (inputs.lattice_for(3, 5, 16, seed=4), dict(jit=1, tile_bits=10))]
 
 
 @pytest.mark.parametrize('lat,kw', PLAN_CASES)
@@ -116,6 +121,36 @@ def test_planner_pass_counts_headline_workload():
     assert len(g) == 478
     assert summ.passes <= 12
     assert summ.hbm_bytes == pytest.approx(8.0 * 2 ** 34 + 16.0 * 2 ** 34 * (summ.passes - 1))
+
+
+def test_plain_plan_applies_each_t_in_the_pass_of_the_next_gate_on_its_qubit():
+    """Plans for the plain pipelined kernels: a T (or its adjoint) on a qubit of the tile
+    goes to the pass of the next non-diagonal gate on its qubit (where the kernel applies
+    both as one step); one on a qubit outside the tile stays a phase of the tile.  The
+    execution order stays a valid reordering (the oracle run in that order matches)."""
+    for lat in (inputs.C34, inputs.C30):
+        n = lat.n_qubits
+        gates = _lib_gates(lat)
+        g = sv.sv_generate_circuit(lat)
+        summ, order, pass_of, tiles = sv.sv_plan(n, g, sv.options(jit=1), fresh_state=True)
+        where = dict(zip(order.tolist(), pass_of.tolist()))
+        checked = 0
+        for i, (k, a, _b, _l) in enumerate(gates):
+            if k not in ('T', 'TDG'):
+                continue
+            succ = next((j for j in range(i + 1, len(gates))
+                         if gates[j][0] in ('SX', 'SY', 'H', 'SXDG', 'SYDG') and gates[j][1] == a), None)
+            if succ is None:
+                continue
+            p = where[i]
+            assert where[succ] >= p
+            if a in set(tiles[p][tiles[p] >= 0].tolist()):
+                assert where[succ] == p, (i, succ)
+                checked += 1
+        assert checked > 20
+        # waiting phases cost no pass: the same pass counts as with every phase placed as
+        # early as it could go
+        assert summ.passes == {34: 8, 30: 5}[n]
 
 
 def test_fused_plans_of_the_headline_workload():
