@@ -374,8 +374,8 @@ sv_status check_fused_error(sv_state *s, const svk::DevPlanView &view) {
 // ---- autotuning of the plain path on plan-specialised kernels ------------------------
 // (sv_options.autotune = 1, a fresh state, the pipelined kernels): the tile size (12 or 13
 // qubits), the fusion width (stages of 5 or 6 qubits: 4 or 5 register slots besides the
-// pack bit) and, per pass, the pipelined kernel's compute groups (3 or 2 on six slots, or
-// 4 on four, on 12-qubit tiles) are picked by timing this circuit -- whole runs of each
+// pack bit) and, per pass, the pipelined kernel's compute groups (3, 2 or 1 on six slots,
+// or 4 on four, on 12-qubit tiles) are picked by timing this circuit -- whole runs of each
 // candidate plan, CUDA events around every pass launch -- and the choice is kept in the
 // JSON cache under "<device>|circuit|<n>|<hash of the gate list and options>" (entries
 // |m, |k (qubits per stage), |passes and |p<i>).
@@ -460,8 +460,9 @@ sv_status autotune_plain(sv_state *s, const std::vector<svp::Gate> &g, const svp
     std::vector<float> best(np, 1e30f);
     std::vector<uint8_t> best_g(np, 0);
     // (34 qubits, fixed shapes: four groups ran the write-only first pass in 61 ms against
-    // 64 ms with three, and the read-write passes up to 15 ms slower)
-    for (int groups : (m == 12 ? std::vector<int>{3, 2, 4} : std::vector<int>{1})) {
+    // 64 ms with three, and the read-write passes up to 15 ms slower; one group, all six
+    // slots, ran the last pass (few gates) in 43.6 ms against 45.8 ms)
+    for (int groups : (m == 12 ? std::vector<int>{3, 2, 4, 1} : std::vector<int>{1})) {
       P.pipe_groups.assign(np, (uint8_t)groups);
       std::string jerr;
       const svj::Module *M = svj::get_module(P, po.rk, &jerr);
