@@ -248,9 +248,15 @@ bool build_plan(int n, const std::vector<Gate> &gates, const Options &opt, bool 
         if (!out0 || !out1) continue;
         (lazy_phase(rem[i]) ? n_t : n_other) += 1;
       }
-      if (n_other == 0 && n_t > 0 && n_t <= 2)
-        for (size_t i = 0; i < rem.size(); ++i)
-          if (applied[i] && lazy_phase(rem[i]) && !((S >> gates[rem[i]].q0) & 1ull)) applied[i] = 0;
+      if (n_other == 0 && n_t > 0 && n_t <= 2) {
+        std::vector<char> fewer = applied;
+        bool left_any = false;
+        for (size_t i = 0; i < rem.size(); ++i) {
+          if (fewer[i] && lazy_phase(rem[i]) && !((S >> gates[rem[i]].q0) & 1ull)) fewer[i] = 0;
+          left_any = left_any || fewer[i];
+        }
+        if (left_any) applied = fewer;
+      }
     }
     std::vector<int> now, later;
     for (size_t i = 0; i < rem.size(); ++i) (applied[i] ? now : later).push_back(rem[i]);
