@@ -114,6 +114,33 @@ def test_planner_order_is_a_valid_reordering(lat, kw):
     np.testing.assert_allclose(got, want, atol=1e-12)
 
 
+@pytest.mark.parametrize('kw', [dict(jit=1), dict(jit=1, tile_bits=10)])
+def test_plain_plan_of_a_random_gate_list_is_a_valid_reordering(kw):
+    """Random lists of the oracle's gate kinds (T before H, SX, SY or nothing on its qubit,
+    Z and CZ signs, no leading H layer) on 14 qubits: the plain pipelined kernels' plans,
+    where each T waits for the next non-diagonal gate on its qubit, run in their execution
+    order give the oracle's state."""
+    n = 14
+    rng = np.random.default_rng(5)
+    kinds = ['H', 'T', 'SX', 'SY', 'CZ', 'Z', 'T', 'T']
+    gates = []
+    for layer in range(220):
+        k = kinds[rng.integers(len(kinds))]
+        a = int(rng.integers(n))
+        b = -1
+        if k == 'CZ':
+            b = int(rng.integers(n - 1))
+            b = b + 1 if b >= a else b
+        gates.append((k, a, b, layer))
+    g = sv.gates_from_tuples([(oc.KIND_CODE[k], a, max(b, 0), l) for k, a, b, l in gates])
+    summ, order, pass_of, tiles = sv.sv_plan(n, g, sv.options(**kw), fresh_state=True)
+    assert sorted(order.tolist()) == list(range(len(gates)))
+    assert summ.passes >= 2
+    want = ov.run(n, gates)
+    got = _oracle_run_order(n, gates, order.tolist())
+    np.testing.assert_allclose(got, want, atol=1e-12)
+
+
 def test_planner_pass_counts_headline_workload():
     """The 34-qubit depth-30 circuit needs far fewer state sweeps than gates."""
     g = sv.sv_generate_circuit(inputs.C34)
