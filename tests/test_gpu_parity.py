@@ -49,7 +49,9 @@ MODES = [dict(), dict(tile_bits=14), dict(tile_bits=10, low_bits=4, fuse_k=5), d
          dict(tile_bits=12, low_bits=5, fuse_k=4), dict(precision=sv.SV_PREC_PERGATE),
          dict(precision=TC), dict(precision=TC, tile_bits=12), dict(precision=TC, tile_bits=12, low_bits=3),
          dict(precision=H16), dict(precision=H16, tile_bits=12),
-         dict(jit=1), dict(jit=1, tile_bits=12), dict(jit=1, tile_bits=8, low_bits=2, fuse_k=3), dict(jit=-1)]
+         dict(jit=1), dict(jit=1, tile_bits=12), dict(jit=1, tile_bits=8, low_bits=2, fuse_k=3), dict(jit=-1),
+         # pipelined plan kernels on 10- and 11-qubit tiles (four groups of one and two warps)
+         dict(jit=1, tile_bits=10), dict(jit=1, tile_bits=11)]
 
 
 @pytest.mark.parametrize('kw', MODES)
@@ -176,6 +178,7 @@ def _oracle_apply(n, gl, psi):
 
 @pytest.mark.parametrize('n,kw', [(7, {}), (13, {}), (18, {}), (18, dict(tile_bits=9, low_bits=3, fuse_k=2)),
                                   (13, dict(jit=1)), (18, dict(jit=1)), (18, dict(jit=1, tile_bits=9, low_bits=3)),
+                                  (18, dict(jit=1, tile_bits=10)), (17, dict(jit=1, tile_bits=11)),
                                   (16, dict(precision=sv.SV_PREC_PERGATE)), (12, dict(precision=TC)),
                                   (17, dict(precision=TC)), (19, dict(precision=TC, tile_bits=12)),
                                   (17, dict(precision=H16)), (19, dict(precision=H16, tile_bits=12)),
