@@ -258,6 +258,53 @@ bool build_plan(int n, const std::vector<Gate> &gates, const Options &opt, bool 
         if (left_any) applied = fewer;
       }
     }
+    if (lazy && first_pass && fresh_state) {
+      // The write-only first pass is bound by its arithmetic, the passes after it by HBM:
+      // on each qubit that this tile shares with the next pass's, the last non-diagonal
+      // gate (with the T waiting for it and the diagonal gates after it) moves to the next
+      // pass when nothing else here depends on it and the next tile stays the same.
+      std::vector<int> rest;
+      for (size_t i = 0; i < rem.size(); ++i)
+        if (!applied[i]) rest.push_back(rem[i]);
+      const uint64_t S1 = choose_tile(n, m, c, gates, rest);
+      std::vector<char> moved = applied;
+      for (int q = 0; q < n; ++q) {
+        if (!((S >> q) & 1ull) || !((S1 >> q) & 1ull)) continue;
+        int last = -1;  // position in rem of the last applied non-diagonal gate on q
+        for (size_t i = 0; i < rem.size(); ++i)
+          if (moved[i] && !kind_is_diag(gates[rem[i]].kind) && gates[rem[i]].q0 == q) last = (int)i;
+        if (last < 0) continue;
+        // what follows it on q here must be diagonal, and a CZ among it must have no
+        // applied non-diagonal gate after it on its other qubit
+        bool ok = true;
+        std::vector<size_t> with;
+        for (size_t i = (size_t)last + 1; i < rem.size() && ok; ++i) {
+          if (!moved[i]) continue;
+          const Gate &x = gates[rem[i]];
+          const bool on_q = x.q0 == q || (kind_two_qubit(x.kind) && x.q1 == q);
+          if (!on_q) continue;
+          if (!kind_is_diag(x.kind)) { ok = false; break; }
+          if (kind_two_qubit(x.kind)) {
+            const int o = x.q0 == q ? x.q1 : x.q0;
+            for (size_t k = i + 1; k < rem.size(); ++k)
+              if (moved[k] && !kind_is_diag(gates[rem[k]].kind) && gates[rem[k]].q0 == o) { ok = false; break; }
+          }
+          with.push_back(i);
+        }
+        if (!ok) continue;
+        moved[(size_t)last] = 0;
+        for (size_t i : with) moved[i] = 0;
+        for (size_t i = 0; i < rem.size(); ++i)  // the T that waits for it
+          if (moved[i] && lazy_phase(rem[i]) && succ[(size_t)rem[i]] == rem[(size_t)last]) moved[i] = 0;
+      }
+      std::vector<int> rest2;
+      bool left_any = false;
+      for (size_t i = 0; i < rem.size(); ++i) {
+        if (!moved[i]) rest2.push_back(rem[i]);
+        left_any = left_any || moved[i];
+      }
+      if (left_any && moved != applied && choose_tile(n, m, c, gates, rest2) == S1) applied = moved;
+    }
     std::vector<int> now, later;
     for (size_t i = 0; i < rem.size(); ++i) (applied[i] ? now : later).push_back(rem[i]);
     std::vector<int> pos_in_now;  // gate index -> position in `now` (-1: not in this pass)
