@@ -195,7 +195,8 @@ bool build_plan(int n, const std::vector<Gate> &gates, const Options &opt, bool 
   std::vector<int> rem;
   for (size_t i = start; i < gates.size(); ++i) rem.push_back((int)i);
 
-  // Plans for the plain pipelined kernels: a T (or its adjoint) on a qubit of the tile
+  // Gate scheduling that uses the diagonal T and CZ (§2.3), one step further for T.  Plans
+  // for the plain pipelined kernels: a T (or its adjoint) on a qubit of the tile
   // waits for the next non-diagonal gate on its qubit (succ) and is placed in the same
   // pass and stage, right before it in the stage's ops, where the kernel applies both as
   // one step (its factor 1/sqrt2 rides on the gate's fused operations).  A phase commutes
