@@ -269,11 +269,13 @@ bool build_plan(int n, const std::vector<Gate> &gates, const Options &opt, bool 
         if (!applied[i]) rest.push_back(rem[i]);
       const uint64_t S1 = choose_tile(n, m, c, gates, rest);
       std::vector<char> moved = applied;
+      // position in rem of the last applied non-diagonal gate of each qubit (-1: none)
+      std::vector<int> last_nd(n, -1);
+      for (size_t i = 0; i < rem.size(); ++i)
+        if (moved[i] && !kind_is_diag(gates[rem[i]].kind)) last_nd[gates[rem[i]].q0] = (int)i;
       for (int q = 0; q < n; ++q) {
         if (!((S >> q) & 1ull) || !((S1 >> q) & 1ull)) continue;
-        int last = -1;  // position in rem of the last applied non-diagonal gate on q
-        for (size_t i = 0; i < rem.size(); ++i)
-          if (moved[i] && !kind_is_diag(gates[rem[i]].kind) && gates[rem[i]].q0 == q) last = (int)i;
+        const int last = last_nd[q];
         if (last < 0) continue;
         // what follows it on q here must be diagonal, and a CZ among it must have no
         // applied non-diagonal gate after it on its other qubit
@@ -285,15 +287,17 @@ bool build_plan(int n, const std::vector<Gate> &gates, const Options &opt, bool 
           const bool on_q = x.q0 == q || (kind_two_qubit(x.kind) && x.q1 == q);
           if (!on_q) continue;
           if (!kind_is_diag(x.kind)) { ok = false; break; }
-          if (kind_two_qubit(x.kind)) {
-            const int o = x.q0 == q ? x.q1 : x.q0;
-            for (size_t k = i + 1; k < rem.size(); ++k)
-              if (moved[k] && !kind_is_diag(gates[rem[k]].kind) && gates[rem[k]].q0 == o) { ok = false; break; }
-          }
+          if (kind_two_qubit(x.kind) && last_nd[x.q0 == q ? x.q1 : x.q0] > (int)i) { ok = false; break; }
           with.push_back(i);
         }
         if (!ok) continue;
         moved[(size_t)last] = 0;
+        last_nd[q] = -1;
+        for (int i = last - 1; i >= 0; --i)
+          if (moved[(size_t)i] && !kind_is_diag(gates[rem[(size_t)i]].kind) && gates[rem[(size_t)i]].q0 == q) {
+            last_nd[q] = i;
+            break;
+          }
         for (size_t i : with) moved[i] = 0;
         for (size_t i = 0; i < rem.size(); ++i)  // the T that waits for it
           if (moved[i] && lazy_phase(rem[i]) && succ[(size_t)rem[i]] == rem[(size_t)last]) moved[i] = 0;
